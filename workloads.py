@@ -1,0 +1,69 @@
+"""Seeded synthetic initial fields phi0 for the anisotropic Cahn-Hilliard runs.
+
+This module holds only input generation (the shapes of the paper's initial
+conditions, Eqs. 40-42, resized), none of the lattice Boltzmann arithmetic. Both
+the CUDA path and the FP64 oracle take the same float64 arrays from here, so no
+random number generator has to be matched between them.
+
+Every field is float64 with shape (ny, nx), row-major with x fastest; node (x, y)
+sits at integer coordinates.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def droplet(nx: int, ny: int, radius: float, width: float, cx: float | None = None,
+            cy: float | None = None) -> np.ndarray:
+    """phi0 = tanh((R - r) / width), r the distance from (cx, cy) (default the grid centre).
+
+    With width = D/2 this is the profile of Eq. 40, tanh(2(R - r)/D); with
+    width = sqrt(2) * 1.5 it is the 64x64 droplet workload's profile.
+    """
+    cx = nx / 2.0 if cx is None else cx
+    cy = ny / 2.0 if cy is None else cy
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64),
+                       indexing="ij")
+    r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2)
+    return np.tanh((radius - r) / width)
+
+
+def droplet_workload(n: int = 64) -> np.ndarray:
+    """n x n droplet, radius 20 (scaled 0.3125 n), profile tanh((R - r)/(sqrt(2) 1.5))."""
+    return droplet(n, n, radius=20.0 * n / 64.0, width=np.sqrt(2.0) * 1.5)
+
+
+def two_droplets(nx: int, ny: int, drops, width: float) -> np.ndarray:
+    """Eq. 41: sum_i tanh((R_i - r_i)/width) + 1, drops = [(R, x, y), ...]."""
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64),
+                       indexing="ij")
+    out = np.ones((ny, nx))
+    for (R, cx, cy) in drops:
+        out += np.tanh((R - np.sqrt((x - cx) ** 2 + (y - cy) ** 2)) / width)
+    return out
+
+
+def noise(nx: int, ny: int, amplitude: float, seed: int, mean: float = 0.0) -> np.ndarray:
+    """Spinodal initial field (Eq. 42 shape): mean + U[-amplitude, amplitude], i.i.d. per node."""
+    rng = np.random.default_rng(seed)
+    return mean + rng.uniform(-amplitude, amplitude, size=(ny, nx))
+
+
+def cosine_mode(nx: int, ny: int, mx: int, my: int, amplitude: float, mean: float) -> np.ndarray:
+    """mean + A cos(q . x + shift), q = 2 pi (mx/nx, my/ny).
+
+    The shift of half a node along the dominant axis (pi |m|/n) keeps every node off the
+    zeros of the gradient, so no node has grad phi = 0.
+    """
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64),
+                       indexing="ij")
+    m = max(abs(mx), abs(my))
+    n = nx if abs(mx) >= abs(my) else ny
+    shift = np.pi * m / n
+    return mean + amplitude * np.cos(2 * np.pi * (mx * x / nx + my * y / ny) + shift)
+
+
+def planar_bands(nx: int, ny: int, x_left: float, x_right: float, width: float) -> np.ndarray:
+    """+1 between two planar interfaces normal to x, -1 outside; tanh profiles of the given width."""
+    x = np.arange(nx, dtype=np.float64)[None, :].repeat(ny, axis=0)
+    return np.tanh((x - x_left) / width) - np.tanh((x - x_right) / width) - 1.0
