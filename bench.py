@@ -1,0 +1,378 @@
+"""Benchmark of the fused anisotropic Cahn-Hilliard MRT-LBM step on GB300.
+
+Workload: the 8192x8192 periodic spinodal field (phi0 = U[-0.05, 0.05], seed 0,
+alpha = 0.3, Eq. 39 parameters), FP32 arithmetic. One benchmark step = 100 lattice
+time steps (one fused kernel launch each) followed by the logged diagnostics, total
+mass and free energy (FP64 reductions on the GPU); --steps 20 covers the
+workload's 2000 time steps. Inputs (9 x 8192^2 populations, 2.4 GB per buffer)
+are far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line. The metric is MLUPS (million lattice-node updates per
+second), with the step kernel's HBM roofline fraction for FP32 storage and, as
+variants, the BF16- and FP16-deviation storages.
+
+--impl reference times the FP64 CPU oracle (the test suite's reference) on the
+host cores instead, on a 2048x2048 sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N = 8192
+ALPHA = 0.3
+SEED = 0
+NOISE = 0.05
+INNER = 100  # lattice steps per benchmark step
+WORKLOAD = "spinodal-8192x8192"
+METRIC = "MLUPS (lattice-node updates/s, 1e6)"
+STEP_KERNEL_SOURCES = ("paper_2501_03759_gb300/csrc/lbch_step.cuh",
+                       "paper_2501_03759_gb300/csrc/lbch_lattice.cuh")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N, help="grid edge (default: the 8192^2 workload)")
+    ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage variants")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(storage_name: str):
+    """DRAM bytes per node update of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_{storage_name}_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_node_update"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_storage(lbch, torch, phi0, n, storage, steps, warmup, with_launch_events=True):
+    """Runs warmup + timed benchmark steps on one storage; returns timings (seconds)."""
+    solver = lbch.Solver(lbch.make_params(n, n, alpha=ALPHA, storage=storage))
+    solver.init_field(phi0)
+    stream = solver.stream
+    mass, energy = [], []
+    for _ in range(warmup):
+        solver.step(INNER)
+        solver.mass()
+        solver.free_energy()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(steps):
+        ev[k][0].record(stream)
+        solver.step(INNER)
+        ev[k][1].record(stream)
+        mass.append(solver.mass())
+        energy.append(solver.free_energy())
+    stop.record(stream)
+    torch.cuda.synchronize()
+    total = start.elapsed_time(stop) / 1e3
+    step_kernels = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    solver.close()
+    del solver
+    torch.cuda.empty_cache()
+    return {"total_s": total, "kernel_s_per_launch": step_kernels / (steps * INNER),
+            "mass_first": mass[0], "mass_last": mass[-1], "energy_first": energy[0],
+            "energy_last": energy[-1]}
+
+
+def run_e2e(lbch, torch, phi0, n, steps, warmup):
+    """Same metric through the public API from pinned host buffers: every step copies phi0
+    in, runs INNER lattice steps, reads mass and energy, and copies phi back out."""
+    solver = lbch.Solver(lbch.make_params(n, n, alpha=ALPHA))
+    h_in = torch.from_numpy(phi0).pin_memory()
+    h_out = torch.empty((n, n), dtype=torch.float64).pin_memory()
+
+    def one():
+        solver.init_field(h_in)
+        solver.step(INNER)
+        solver.mass()
+        solver.free_energy()
+        solver.field(h_out)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    solver.close()
+    return {"lu": steps * INNER * n * n, "unit": "MLUPS",
+            "h2d_bytes_per_step": int(h_in.numel() * 8), "d2h_bytes_per_step": int(h_out.numel() * 8 + 16),
+            "wall_s": dt}
+
+
+def cpu_oracle_rate(target_s: float = 12.0, n_sample: int = 2048):
+    """The FP64 oracle, as it stands, on the host cores: MLUPS on an n_sample^2 spinodal
+    sample of the workload (alpha 0.3, noise 0.05, seed 0)."""
+    import oracle
+    import workloads
+
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    p = oracle.Params(n_sample, n_sample, alpha=ALPHA)
+    f = oracle.init(p, workloads.noise(n_sample, n_sample, NOISE, SEED))
+    t0 = time.perf_counter()
+    f = oracle.step(p, f, 1)
+    one = time.perf_counter() - t0
+    k = max(1, int(target_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    oracle.step(p, f, k)
+    dt = time.perf_counter() - t0
+    return {"value": k * n_sample * n_sample / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{k} FP64 oracle steps on a {n_sample}x{n_sample} spinodal field "
+                      f"(alpha {ALPHA}, noise {NOISE}, seed {SEED}), OpenMP over rows",
+            "seconds": dt}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    import workloads
+
+    n_sample = 2048
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    p = oracle.Params(n_sample, n_sample, alpha=ALPHA)
+    f = oracle.init(p, workloads.noise(n_sample, n_sample, NOISE, SEED))
+    for _ in range(args.warmup):
+        f = oracle.step(p, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle.step(p, f, 1)
+    dt = time.perf_counter() - t0
+    value = args.steps * n_sample * n_sample / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{n_sample}x{n_sample}", "alpha": ALPHA, "noise": NOISE,
+                   "seed": SEED, "lattice_steps_per_step": 1, "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"each step: 1 FP64 oracle step on a {n_sample}x{n_sample} spinodal field"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+
+    from paper_2501_03759_gb300 import lbch
+    import workloads
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+
+        dist.init_process_group("gloo")
+    n = args.n
+    phi0 = workloads.noise(n, n, NOISE, SEED)
+    lbch.load()
+
+    props = torch.cuda.get_device_properties(local)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else None
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    barrier()
+    with ClockSampler(gpu_id) as clk:
+        r32 = time_storage(lbch, torch, phi0, n, lbch.STORE_F32, args.steps, args.warmup)
+    barrier()
+    total = max_over_ranks(r32["total_s"])
+    per_launch = max_over_ranks(r32["kernel_s_per_launch"])
+    lu_per_rank = args.steps * INNER * n * n
+    value = world * lu_per_rank / total / 1e6
+
+    peak, peak_kind = measured_peaks()
+    bpl = lbch.ALGORITHMIC_BYTES_PER_LU[lbch.STORE_F32]
+    achieved = bpl * n * n / per_launch / 1e9
+    traffic = profiled_traffic("f32")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None if traffic is None else traffic * n * n,
+                "peak_kind": peak_kind, "kernel": "lbch::step_kernel<F32, vec>",
+                "algorithmic_bytes_per_launch": bpl * n * n, "launch_ms": per_launch * 1e3}
+
+    variants = {}
+    if not args.no_variants:
+        for name, st in (("bf16_dev", lbch.STORE_BF16_DEV), ("f16_dev", lbch.STORE_F16_DEV)):
+            r = time_storage(lbch, torch, phi0, n, st, args.steps, args.warmup)
+            pl = max_over_ranks(r["kernel_s_per_launch"])
+            b = lbch.ALGORITHMIC_BYTES_PER_LU[st]
+            ach = b * n * n / pl / 1e9
+            variants[name] = {"value": world * lu_per_rank / max_over_ranks(r["total_s"]) / 1e6,
+                              "unit": "MLUPS", "launch_ms": pl * 1e3,
+                              "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                           "frac": ach / peak, "traffic": None if profiled_traffic(name) is None
+                                           else profiled_traffic(name) * n * n, "peak_kind": peak_kind},
+                              "kernel_only_mlups": n * n / pl / 1e6 * world,
+                              "mass_drift_rel": abs(r["mass_last"] - r["mass_first"]) / max(1e-300, abs(r["mass_first"]))}
+
+    e2e = None
+    if not args.no_e2e:
+        e = run_e2e(lbch, torch, phi0, n, max(1, min(args.steps, 5)), 1)
+        barrier()
+        e2e = {"value": world * e["lu"] / max_over_ranks(e["wall_s"]) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": e["h2d_bytes_per_step"], "d2h_bytes_per_step": e["d2h_bytes_per_step"],
+               "lattice_steps_per_step": INNER}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if n == N else f"spinodal-{n}x{n}", "nx": n, "ny": n, "alpha": ALPHA,
+                       "noise": NOISE, "seed": SEED, "storage": "f32", "lattice_steps_per_step": INNER,
+                       "diagnostics_per_step": ["mass", "free_energy"],
+                       "l2": "inputs larger than L2 (2.4 GB per population buffer), no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline,
+            "kernel_only_mlups": world * n * n / per_launch / 1e6,
+            "variants": variants,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps * (INNER + 5),
+            "mass_drift_rel": abs(r32["mass_last"] - r32["mass_first"]) / max(1e-300, abs(r32["mass_first"])),
+            "energy_first_last": [r32["energy_first"], r32["energy_last"]],
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

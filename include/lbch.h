@@ -1,0 +1,144 @@
+/*
+ * lbch: one time step of the multiple-relaxation-time lattice Boltzmann scheme for
+ * the anisotropic Cahn-Hilliard equation (Liu, Wang, Liu, arXiv 2501.03759,
+ * Sections 2-3), on a periodic 2D grid, on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The problem (Section 2): an order parameter phi(x, t) on a periodic N_x x N_y
+ * lattice evolves by the Cahn-Hilliard equation d phi/dt = div(M grad mu) (Eq. 10)
+ * with the chemical potential of Eq. 13 (Willmore regularisation, Eq. 9), the
+ * fourfold anisotropy gamma(n) = 1 + alpha cos 4 theta (Eq. 6) and the vector field
+ * Q of Eq. 15. The scheme (Section 3) splits mu = mu_alpha + mu_beta (Eq. 16) and
+ * evolves D2Q9 populations f_i (Eq. 20) by the MRT update of Eq. 17 with the
+ * equilibrium of Eq. 18, the source of Eq. 19, the moment matrix of Eq. 23 and the
+ * isotropic stencils of Eq. 26; phi = sum_i f_i (Eq. 22). Lattice units: dx = dt =
+ * c = 1, c_s^2 = 1/3.
+ *
+ * Readings the library takes where the paper is silent or garbled (flags select
+ * the alternatives):
+ *   - Eq. 15 is used with the factor k that Eq. 14 carries on its second term:
+ *     Q = gamma k grad phi + k |grad phi| P grad_n gamma.  LBCH_Q_LITERAL drops it.
+ *   - mu_beta = mu - mu_alpha with the isotropic k lap phi cancelled analytically:
+ *     mu_beta = (gamma-1) f - div((gamma-1) k grad phi + k|grad phi| P grad_n gamma)
+ *               + eps (lap w - f'(phi) w),  w = lap phi - f(phi).
+ *     LBCH_MU_NESTED takes mu - mu_alpha with the full Q instead.
+ *   - Where |grad phi|^2 < 1e-24 a node takes n = 0, gamma = 1, P grad_n gamma = 0.
+ *   - grad_n gamma = 16 alpha (n_1^3, n_2^3), the gradient of Eq. 6 in R^2.
+ *   - s_3 = s_5 = 1/(M/c_s^2 + 1/2) (from M = c_s^2 (1/s_{3,5} - 1/2) dt, after
+ *     Eq. 38) unless LBCH_S35_EXPLICIT; the other rates are inputs (default 1).
+ *   - Initial populations: f = f^eq(phi0, mu_alpha(phi0)), Eq. 18 with Eq. 16.
+ *   - Free energy: sum over nodes of gamma(n)(k/2 |grad phi|^2 + F(phi))
+ *     + eps/2 G(phi), with the stencils of Eq. 26 (Eqs. 1, 4, 7, 8, 9).
+ *
+ * Threading and streams: a context is used by one host thread at a time. All GPU
+ * work of a context goes to the CUDA stream given at creation, in call order.
+ *
+ * Errors: every call returns an lbch_status and never aborts or throws. After a
+ * CUDA error the context is failed: every later call except lbch_destroy and
+ * lbch_last_error returns LBCH_ESTATE.
+ */
+#ifndef LBCH_H
+#define LBCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbch_ctx lbch_ctx; /* opaque; created by lbch_create, freed by lbch_destroy */
+
+typedef enum {
+  LBCH_OK = 0,
+  LBCH_EINVAL = -1,      /* bad argument, parameter, size or call order */
+  LBCH_ECUDA = -2,       /* a CUDA call failed; the context is now failed */
+  LBCH_ENOMEM = -3,      /* the caller's workspace is too small or misaligned */
+  LBCH_ENONFINITE = -4,  /* NaN or Inf in an input field or in a reduced result */
+  LBCH_ESTATE = -5       /* the context failed earlier */
+} lbch_status;
+
+/* How the populations are stored between steps; arithmetic is FP32 in all cases. */
+typedef enum {
+  LBCH_STORE_F32 = 0,       /* 9 FP32 planes: 72 bytes read+written per node update */
+  LBCH_STORE_BF16_DEV = 1,  /* FP32 rest population and mu_alpha anchor, plus the 8 moving
+                               populations as BF16 deviations from omega_i mu_alpha: 48 bytes */
+  LBCH_STORE_F16_DEV = 2    /* as above with FP16 deviations scaled by 2^12: 48 bytes */
+} lbch_storage;
+
+enum {
+  LBCH_Q_LITERAL = 1u,    /* Eq. 15 exactly as printed (no k on its second term) */
+  LBCH_MU_NESTED = 2u,    /* mu_beta = mu - mu_alpha with the full Q of Eq. 15 */
+  LBCH_S35_EXPLICIT = 4u  /* use s[3], s[5] as given instead of deriving them from M */
+};
+
+enum { LBCH_REG_NONE = 0, LBCH_REG_WILLMORE = 1, LBCH_REG_LINEAR = 2 };
+
+typedef struct {
+  int32_t nx, ny;      /* periodic grid, x fastest; 1 <= nx, ny <= 65536 */
+  double M;            /* mobility (Eq. 10), > 0; sets s_3 = s_5 */
+  double sigma, D;     /* surface tension and interface thickness (Eq. 5), > 0 */
+  double eps;          /* regularisation strength epsilon (Eq. 7), >= 0 */
+  double alpha;        /* anisotropy strength (Eq. 6), 0 <= alpha < 1 */
+  double s[9];         /* relaxation rates s_0..s_8 of S (Eq. 25); each of s_1..s_8 in (0, 2) */
+  int32_t storage;       /* lbch_storage */
+  int32_t regularization;/* LBCH_REG_*: none, Willmore (Eq. 9, Eq. 13, the paper's choice),
+                            linear (Eq. 8, Eq. 12) */
+  uint32_t flags;        /* LBCH_Q_LITERAL | LBCH_MU_NESTED | LBCH_S35_EXPLICIT */
+} lbch_params;
+
+/* Device workspace a context needs for these parameters (population buffers,
+ * one FP64 staging plane of nx*ny, a small reduction area); 0 if the parameters
+ * are invalid. */
+size_t lbch_workspace_bytes(const lbch_params* p);
+
+/* Creates a context on the current CUDA device.
+ *   d_workspace: device memory of at least lbch_workspace_bytes(p) bytes, 256-byte
+ *                aligned, owned by the caller; it must outlive the context. The
+ *                library never allocates or frees device memory.
+ *   cuda_stream: a cudaStream_t (NULL for the legacy default stream).
+ * Returns LBCH_EINVAL for bad parameters, LBCH_ENOMEM if the workspace is too small
+ * or misaligned, LBCH_ECUDA if the device cannot run the kernels. *out is set only
+ * on LBCH_OK. */
+lbch_status lbch_create(const lbch_params* p, void* d_workspace, size_t bytes,
+                        void* cuda_stream, lbch_ctx** out);
+
+/* Sets the state to f = f^eq(phi0, mu_alpha(phi0)) (Eq. 18, Eq. 16, Eq. 26b) at t = 0.
+ *   h_phi0: host array of nx*ny doubles, row-major (x fastest), read before return.
+ * Synchronises the stream. LBCH_ENONFINITE (state left unset) if phi0 holds NaN/Inf. */
+lbch_status lbch_init_field(lbch_ctx* ctx, const double* h_phi0);
+
+/* Advances the state n >= 0 time steps of Eq. 17. Asynchronous: enqueues n kernel
+ * launches on the stream and returns. LBCH_EINVAL before any init/set_state. */
+lbch_status lbch_step(lbch_ctx* ctx, int64_t n);
+
+/* Total mass sum_x phi(x) (Eq. 22), accumulated in FP64 on the GPU. Synchronises. */
+lbch_status lbch_mass(lbch_ctx* ctx, double* out);
+
+/* Discrete free energy (Eq. 7 with G of Eq. 9 or Eq. 8), densities in FP32, sum in
+ * FP64 on the GPU. Synchronises. LBCH_ENONFINITE if the result is NaN/Inf. */
+lbch_status lbch_free_energy(lbch_ctx* ctx, double* out);
+
+/* Copies phi(x, t) = sum_i f_i(x, t) (Eq. 22) to h_phi (nx*ny doubles). Synchronises. */
+lbch_status lbch_get_field(lbch_ctx* ctx, double* h_phi);
+
+/* Copies the post-streaming populations f_i(x, t) of Eq. 17 to h_f9: 9 planes of
+ * nx*ny doubles, plane i in the D2Q9 order of Eq. 20a. Synchronises. */
+lbch_status lbch_get_state(lbch_ctx* ctx, double* h_f9);
+
+/* Replaces the state with h_f9 (same layout as lbch_get_state); checkpoint/resume.
+ * Synchronises. LBCH_ENONFINITE (state left unset) if h_f9 holds NaN/Inf. */
+lbch_status lbch_set_state(lbch_ctx* ctx, const double* h_f9);
+
+/* Number of time steps taken since the last lbch_init_field / lbch_set_state. */
+int64_t lbch_steps_taken(const lbch_ctx* ctx);
+
+/* Human-readable description of the last error on this context ("" if none). */
+const char* lbch_last_error(const lbch_ctx* ctx);
+
+/* Frees the host-side context. Never touches the workspace. NULL is ignored. */
+void lbch_destroy(lbch_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

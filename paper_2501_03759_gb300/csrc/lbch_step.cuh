@@ -1,0 +1,451 @@
+// Fused time step of the MRT lattice Boltzmann scheme for the anisotropic
+// Cahn-Hilliard equation (arXiv 2501.03759, Section 3), one kernel per step.
+//
+// What one launch computes, for every node x of the periodic grid:
+//   f_in,i(x)  = f*_i(x - c_i)                      pull streaming of the previous step
+//   phi        = sum_i f_in,i                       Eq. 22
+//   grad phi, lap phi                               Eq. 26a, 26b
+//   n, gamma(n), P grad_n gamma, Q, f, f', w, mu_a  Eqs. 2, 6, 15, 9, 13, 16
+//   mu_beta = (gamma-1) f - div Q + eps(lap w - f' w)   Eqs. 13, 16 (split reading)
+//   g = grad mu_beta, F_m = M F                     Eqs. 26a, 19, 25
+//   m* = m - S(m - m^eq) + (I - S/2) F_m, f* = M^-1 m*   Eqs. 17, 23, 25
+// and stores f* (the state before streaming) in the other buffer.
+//
+// Work decomposition (GB300): one warp owns a strip of 128 consecutive columns
+// (4 per lane, so rows move as 16-byte vectors) and sweeps a segment of rows top to
+// bottom. phi is needed up to 3 nodes away from an output node, so each warp keeps
+// a rolling three-row window of every stencil in registers: when the phi row r
+// arrives it completes grad/lap phi of row r-1, mu_beta of row r-2 and
+// grad mu_beta of row r-3, and collides row r-3. Left/right neighbours come from
+// warp shuffles; the 4 strip columns at each edge are halo, so a strip yields 120
+// output columns. The pulled populations of the last rows wait for their
+// collision in a per-warp shared-memory ring (each lane reads back only what it
+// wrote). No tensor cores: the 9x9 moment transform is a handful of adds with
+// constant +-1/+-2 entries.
+#pragma once
+
+#include "lbch_lattice.cuh"
+
+namespace lbch {
+
+constexpr int STRIP_W = 128;                 // columns per warp strip
+constexpr int HALO_W = 4;                    // halo columns on each side
+constexpr int OUT_W = STRIP_W - 2 * HALO_W;  // output columns per strip
+constexpr int STEP_WARPS = 4;                // warps per CTA
+constexpr int RING = 4;                      // rows of pulled populations in flight
+constexpr int RING_FLOAT4 = RING * 9 * 32;   // float4 per warp
+constexpr int STEP_SMEM = STEP_WARPS * RING_FLOAT4 * 16;
+
+struct StepArgs {
+  Buf src, dst;
+  long long ps;  // plane stride in elements
+  int nx, ny;
+  int n_strips, seg_len;
+  long long n_warps;
+  // Chemical potential constants.
+  float k;     // gradient energy coefficient (Eq. 5)
+  float kq;    // factor on |grad phi| P grad_n gamma in Q (k, or 1 for the literal Eq. 15)
+  float kiso;  // k times the isotropic part kept in Q (0 split, k nested)
+  float beta4, beta12;  // 4 beta and 12 beta (f and f')
+  float alpha, a16;     // alpha, 16 alpha
+  float eps;   // eps on lap w (0 without regularisation)
+  float cw;    // w = lap phi - cw f  (1 Willmore, 0 linear)
+  float cfp;   // eps on f' w (Willmore only)
+  float cnk;   // k lap phi added to mu_beta in nested form
+  // Collision: n_k = (m*_k)/|row k of M|^2 in terms of m_k, m^eq_k and g.
+  float c1a, c1b, c2a, c2b, c3a, c3g, c4a, c4g, c5a, c5g, c6a, c6g, c7, c8;
+};
+
+__device__ __forceinline__ int imod(int v, int n) {
+  int r = v % n;
+  return r < 0 ? r + n : r;
+}
+
+// Left/right neighbour sums and differences of a per-column quantity over the strip.
+__device__ __forceinline__ void neighbours(const float (&q)[4], float (&s)[4], float (&d)[4]) {
+  const float left = __shfl_up_sync(FULL, q[3], 1);
+  const float right = __shfl_down_sync(FULL, q[0], 1);
+  s[0] = left + q[1];
+  d[0] = q[1] - left;
+  s[1] = q[0] + q[2];
+  d[1] = q[2] - q[0];
+  s[2] = q[1] + q[3];
+  d[2] = q[3] - q[1];
+  s[3] = q[2] + right;
+  d[3] = right - q[2];
+}
+
+// Per-lane addressing of the strip.
+struct Cols {
+  long long c0;  // aligned first column (vector path)
+  int cs[6];     // columns xs + 4 lane + k - 1, k = 0..5 (scalar path), mod nx
+};
+
+// Post-collision value f*_i at the 4 columns of `base` (+ column offsets) of one row.
+template <int ST, bool VEC, int I>
+__device__ __forceinline__ void load_fstar(const StepArgs& a, long long ro, const Cols& cl,
+                                           float (&v)[4]) {
+  constexpr int SH = -cx(I);  // pull: f_in,i(x) = f*_i(x - c_i)
+  if constexpr (ST == ST_F32) {
+    const float* p = a.src.f32 + (long long)I * a.ps + ro;
+    if constexpr (VEC) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(p + cl.c0));
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = __ldg(p + cl.cs[j + SH + 1]);
+    }
+  } else {
+    using D = Dev<ST>;
+    if constexpr (I == 0) {
+      const float* p = a.src.f32 + ro;
+      if constexpr (VEC) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p + cl.c0));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = __ldg(p + cl.cs[j + 1]);
+      }
+    } else {
+      const float w = (float)wgt(I);
+      const float* pm = a.src.f32 + a.ps + ro;
+      const uint16_t* pd = a.src.dev + (long long)(I - 1) * a.ps + ro;
+      if constexpr (VEC) {
+        const float4 m = __ldg(reinterpret_cast<const float4*>(pm + cl.c0));
+        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(pd + cl.c0));
+        v[0] = fmaf(w, m.x, D::load(static_cast<uint16_t>(raw.x & 0xffffu)));
+        v[1] = fmaf(w, m.y, D::load(static_cast<uint16_t>(raw.x >> 16)));
+        v[2] = fmaf(w, m.z, D::load(static_cast<uint16_t>(raw.y & 0xffffu)));
+        v[3] = fmaf(w, m.w, D::load(static_cast<uint16_t>(raw.y >> 16)));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = cl.cs[j + SH + 1];
+          v[j] = fmaf(w, __ldg(pm + c), D::load(__ldg(pd + c)));
+        }
+      }
+    }
+  }
+  if constexpr (VEC) {
+    if constexpr (SH == -1) {  // c_x = +1: take the column to the left
+      const float prev = __shfl_up_sync(FULL, v[3], 1);
+      v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
+    } else if constexpr (SH == 1) {  // c_x = -1: take the column to the right
+      const float next = __shfl_down_sync(FULL, v[0], 1);
+      v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
+    }
+  }
+}
+
+// Pointwise part at one node: Q (Eq. 15 reading), w, mu_alpha (Eq. 16) and the
+// local part A of mu_beta (Eq. 13 minus Eq. 16's mu_alpha).
+__device__ __forceinline__ void pointwise(const StepArgs& a, float phi, float dx, float dy,
+                                          float lap, float& Qx, float& Qy, float& w, float& A,
+                                          float& mua) {
+  const float g2 = fmaf(dx, dx, dy * dy);
+  const bool ok = g2 >= 1e-24f;
+  const float rs = rsqrtf(ok ? g2 : 1.0f);
+  const float n1 = dx * rs, n2 = dy * rs;  // Eq. 2
+  const float n1s = n1 * n1, n2s = n2 * n2;
+  const float S4 = fmaf(n1s, n1s, n2s * n2s);
+  const float gm1 = ok ? a.alpha * fmaf(4.0f, S4, -3.0f) : 0.0f;  // gamma - 1, Eq. 6
+  // k_q |grad phi| P grad_n gamma with grad_n gamma = 16 alpha n^3, P = I - n n^T.
+  const float t = ok ? a.kq * a.a16 * (g2 * rs) : 0.0f;
+  const float kg = fmaf(a.k, gm1, a.kiso);
+  Qx = fmaf(kg, dx, t * (n1 * (n1s - S4)));
+  Qy = fmaf(kg, dy, t * (n2 * (n2s - S4)));
+  const float phi2 = phi * phi;
+  const float fb = a.beta4 * phi * (phi2 - 1.0f);  // f = F'(phi), Eq. 9
+  const float fp = fmaf(a.beta12, phi2, -a.beta4); // f'(phi), Eq. 13
+  w = fmaf(-a.cw, fb, lap);
+  mua = fmaf(-a.k, lap, fb);
+  A = fmaf(gm1, fb, fmaf(-a.cfp * fp, w, a.cnk * lap));
+}
+
+// Eq. 17 at one node in moment space (Eqs. 23, 25) with the closed forms
+// m^eq = (phi, -4 phi + 2 mu_a, 4 phi - 3 mu_a, 0, ...) and
+// M F = (0, 0, 0, -g_x/3, g_x/3, -g_y/3, g_y/3, 0, 0), and M^-1 = M^T diag(1/|row|^2).
+__device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], float mua,
+                                        float gx, float gy, float (&o)[9], float& phi_out) {
+  const float ab = f[1] + f[3], bb = f[2] + f[4];
+  const float Sa = ab + bb;
+  const float e = f[5] + f[7], h = f[6] + f[8];
+  const float Sd = e + h;
+  const float phi = f[0] + Sa + Sd;
+  const float x1 = f[1] - f[3], y1 = f[2] - f[4];
+  const float p = f[5] - f[7], q = f[6] - f[8];
+  const float pm = p - q, pp = p + q;
+  const float m1 = fmaf(-4.0f, f[0], fmaf(2.0f, Sd, -Sa));
+  const float m2 = fmaf(4.0f, f[0], fmaf(-2.0f, Sa, Sd));
+  const float m3 = x1 + pm, m4 = fmaf(-2.0f, x1, pm);
+  const float m5 = y1 + pp, m6 = fmaf(-2.0f, y1, pp);
+  const float m7 = ab - bb, m8 = e - h;
+  const float n0 = phi * (1.0f / 9.0f);
+  const float n1 = fmaf(a.c1a, m1, a.c1b * fmaf(2.0f, mua, -4.0f * phi));
+  const float n2 = fmaf(a.c2a, m2, a.c2b * fmaf(-3.0f, mua, 4.0f * phi));
+  const float n3 = fmaf(a.c3a, m3, a.c3g * gx);
+  const float n4 = fmaf(a.c4a, m4, a.c4g * gx);
+  const float n5 = fmaf(a.c5a, m5, a.c5g * gy);
+  const float n6 = fmaf(a.c6a, m6, a.c6g * gy);
+  const float n7 = a.c7 * m7, n8 = a.c8 * m8;
+  o[0] = fmaf(4.0f, n2 - n1, n0);
+  const float A0 = fmaf(-2.0f, n2, n0 - n1);
+  const float B = A0 + n7, C = A0 - n7;
+  const float X = fmaf(-2.0f, n4, n3), Y = fmaf(-2.0f, n6, n5);
+  o[1] = B + X;
+  o[3] = B - X;
+  o[2] = C + Y;
+  o[4] = C - Y;
+  const float D0 = fmaf(2.0f, n1, n0 + n2);
+  const float E = D0 + n8, G = D0 - n8;
+  const float U = n3 + n4, V = n5 + n6;
+  const float P = U + V, Mv = U - V;
+  o[5] = E + P;
+  o[7] = E - P;
+  o[6] = G - Mv;
+  o[8] = G + Mv;
+  phi_out = phi;
+}
+
+template <int ST, bool VEC>
+__device__ __forceinline__ void store_row(const StepArgs& a, long long ro, long long col,
+                                          const float (&o)[9][4], const float (&mua)[4],
+                                          const float (&phi)[4]) {
+  if constexpr (ST == ST_F32) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      float* p = a.dst.f32 + (long long)i * a.ps + ro + col;
+      if constexpr (VEC) {
+        *reinterpret_cast<float4*>(p) = make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) p[j] = o[i][j];
+      }
+    }
+  } else {
+    using D = Dev<ST>;
+    float rest[4];
+    uint16_t d[8][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float sum = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const float wm = (float)wgt(i) * mua[j];
+        d[i - 1][j] = D::store(o[i][j] - wm);
+        sum += fmaf((float)wgt(i), mua[j], D::load(d[i - 1][j]));  // f*_i as a reader rebuilds it
+      }
+      rest[j] = phi[j] - sum;  // keeps sum_i f*_i = phi: mass conserved to FP32 rounding
+    }
+    float* p0 = a.dst.f32 + ro + col;
+    float* pm = a.dst.f32 + a.ps + ro + col;
+    if constexpr (VEC) {
+      *reinterpret_cast<float4*>(p0) = make_float4(rest[0], rest[1], rest[2], rest[3]);
+      *reinterpret_cast<float4*>(pm) = make_float4(mua[0], mua[1], mua[2], mua[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        p0[j] = rest[j];
+        pm[j] = mua[j];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      uint16_t* pd = a.dst.dev + (long long)i * a.ps + ro + col;
+      if constexpr (VEC) {
+        *reinterpret_cast<uint2*>(pd) =
+            make_uint2(static_cast<uint32_t>(d[i][0]) | (static_cast<uint32_t>(d[i][1]) << 16),
+                       static_cast<uint32_t>(d[i][2]) | (static_cast<uint32_t>(d[i][3]) << 16));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pd[j] = d[i][j];
+      }
+    }
+  }
+}
+
+// Scalar-path store for columns that may be partly out of range (not 4-aligned grids).
+template <int ST>
+__device__ __forceinline__ void store_row_masked(const StepArgs& a, long long ro, int col0, int nvalid,
+                                                 const float (&o)[9][4], const float (&mua)[4],
+                                                 const float (&phi)[4]) {
+  if (nvalid >= 4) {
+    store_row<ST, false>(a, ro, col0, o, mua, phi);
+    return;
+  }
+  // Fewer than 4 valid columns: write them one at a time.
+  if constexpr (ST == ST_F32) {
+    for (int j = 0; j < nvalid; ++j)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) a.dst.f32[(long long)i * a.ps + ro + col0 + j] = o[i][j];
+  } else {
+    using D = Dev<ST>;
+    for (int j = 0; j < nvalid; ++j) {
+      float sum = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const uint16_t d = D::store(o[i][j] - (float)wgt(i) * mua[j]);
+        sum += fmaf((float)wgt(i), mua[j], D::load(d));
+        a.dst.dev[(long long)(i - 1) * a.ps + ro + col0 + j] = d;
+      }
+      a.dst.f32[ro + col0 + j] = phi[j] - sum;
+      a.dst.f32[a.ps + ro + col0 + j] = mua[j];
+    }
+  }
+}
+
+template <int ST, bool VEC>
+__global__ void __launch_bounds__(STEP_WARPS * 32, 3) step_kernel(const __grid_constant__ StepArgs a) {
+  extern __shared__ float4 smem_ring[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const long long warp = (long long)blockIdx.x * STEP_WARPS + wib;
+  if (warp >= a.n_warps) return;  // whole warps only: shuffles below see all 32 lanes
+  const int strip = (int)(warp % a.n_strips);
+  const int seg = (int)(warp / a.n_strips);
+  const int y0 = seg * a.seg_len;
+  const int y1 = min(y0 + a.seg_len, a.ny);
+  const int xs = strip * OUT_W - HALO_W;  // strip start column (before wrap)
+  float4* ring = smem_ring + wib * RING_FLOAT4 + lane;
+
+  Cols cl;
+  cl.c0 = imod(xs + 4 * lane, a.nx);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) cl.cs[k] = imod(xs + 4 * lane + k - 1, a.nx);
+
+  // Output columns of this lane: strip columns 4 lane + j in [HALO_W, STRIP_W - HALO_W).
+  const int ocol0 = strip * OUT_W + 4 * lane - HALO_W;  // global column of element 0
+  const bool lane_out = lane >= 1 && lane <= 30 && ocol0 < a.nx;
+  const int nvalid = min(4, a.nx - ocol0);
+
+  // Rolling accumulators (see the header comment): index 1 = row completing next, 0 = row after.
+  float Ax1[4], Ay1[4], Al1[4], Ax0[4], Ay0[4], Al0[4], php[4];
+  float T1[4], T0[4];
+  float Gx1[4], Gy1[4], Gx0[4], Gy0[4];
+  float mu1[4], mu2[4];  // mu_alpha of rows r-2 and r-3
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    Ax1[j] = Ay1[j] = Al1[j] = Ax0[j] = Ay0[j] = Al0[j] = php[j] = 0.0f;
+    T1[j] = T0[j] = Gx1[j] = Gy1[j] = Gx0[j] = Gy0[j] = mu1[j] = mu2[j] = 0.0f;
+  }
+
+  const int n_it = (y1 - y0) + 6;
+  int rm = imod(y0 - 4, a.ny);  // row r - 1 (mod ny) for the first iteration
+  int r0 = imod(y0 - 3, a.ny);
+  int rp = imod(y0 - 2, a.ny);
+  for (int it = 0; it < n_it; ++it) {
+    const long long ro_m = (long long)rm * a.nx, ro_0 = (long long)r0 * a.nx,
+                    ro_p = (long long)rp * a.nx;
+    // 1. Pull row r of f_in, stash it for its collision, and sum phi (Eq. 22).
+    float ph[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    float4* slot = ring + (it & (RING - 1)) * (9 * 32);
+    {
+      float v[4];
+#define LBCH_PULL(I)                                                              \
+  load_fstar<ST, VEC, I>(a, cy(I) == 1 ? ro_m : (cy(I) == -1 ? ro_p : ro_0), cl, v); \
+  slot[(I) * 32] = make_float4(v[0], v[1], v[2], v[3]);                            \
+  ph[0] += v[0]; ph[1] += v[1]; ph[2] += v[2]; ph[3] += v[3];
+      LBCH_PULL(0) LBCH_PULL(1) LBCH_PULL(2) LBCH_PULL(3) LBCH_PULL(4)
+      LBCH_PULL(5) LBCH_PULL(6) LBCH_PULL(7) LBCH_PULL(8)
+#undef LBCH_PULL
+    }
+    // 2. grad phi and lap phi of row r-1 (Eq. 26a, 26b), rolling over rows.
+    float dx[4], dy[4], lp[4];
+    {
+      float s[4], d[4];
+      neighbours(ph, s, d);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float e = d[j] * (1.0f / 12.0f);
+        const float u = fmaf(s[j], 1.0f / 12.0f, ph[j] * (1.0f / 3.0f));
+        const float t = fmaf(s[j], 1.0f / 6.0f, ph[j] * (2.0f / 3.0f));
+        dx[j] = Ax1[j] + e;
+        dy[j] = Ay1[j] + u;
+        lp[j] = Al1[j] + t;
+        Ax1[j] = fmaf(4.0f, e, Ax0[j]);
+        Ay1[j] = Ay0[j];
+        Al1[j] = Al0[j] + fmaf(s[j], 2.0f / 3.0f, ph[j] * (-10.0f / 3.0f));
+        Ax0[j] = e;
+        Ay0[j] = -u;
+        Al0[j] = t;
+      }
+    }
+    // 3. Pointwise at row r-1.
+    float Qx[4], Qy[4], w[4], Aq[4], mun[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) pointwise(a, php[j], dx[j], dy[j], lp[j], Qx[j], Qy[j], w[j], Aq[j], mun[j]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) php[j] = ph[j];
+    // 4. mu_beta of row r-2: A - div Q + eps lap w (Eq. 26 on Q and w).
+    float mub[4];
+    {
+      float sx[4], dqx[4], sqy[4], dqy[4], sw[4], dw[4];
+      neighbours(Qx, sx, dqx);
+      neighbours(Qy, sqy, dqy);
+      neighbours(w, sw, dw);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float aa = dqx[j] * (1.0f / 12.0f);
+        const float bb = fmaf(sqy[j], 1.0f / 12.0f, Qy[j] * (1.0f / 3.0f));
+        const float cc = a.eps * fmaf(sw[j], 1.0f / 6.0f, w[j] * (2.0f / 3.0f));
+        mub[j] = T1[j] + (cc - aa - bb);
+        T1[j] = T0[j] + (fmaf(-4.0f, aa, Aq[j]) +
+                         a.eps * fmaf(sw[j], 2.0f / 3.0f, w[j] * (-10.0f / 3.0f)));
+        T0[j] = (bb - aa) + cc;
+      }
+    }
+    // 5. grad mu_beta of row r-3 (Eq. 26a).
+    float gx[4], gy[4];
+    {
+      float s[4], d[4];
+      neighbours(mub, s, d);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float e = d[j] * (1.0f / 12.0f);
+        const float u = fmaf(s[j], 1.0f / 12.0f, mub[j] * (1.0f / 3.0f));
+        gx[j] = Gx1[j] + e;
+        gy[j] = Gy1[j] + u;
+        Gx1[j] = fmaf(4.0f, e, Gx0[j]);
+        Gy1[j] = Gy0[j];
+        Gx0[j] = e;
+        Gy0[j] = -u;
+      }
+    }
+    // 6. Collide row r-3 and store it.
+    if (it >= 6) {
+      const float4* rs = ring + ((it + 1) & (RING - 1)) * (9 * 32);
+      float4 fr[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fr[i] = rs[i * 32];
+      float o[9][4], phic[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float f[9], oj[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          f[i] = j == 0 ? fr[i].x : (j == 1 ? fr[i].y : (j == 2 ? fr[i].z : fr[i].w));
+        collide(a, f, mu2[j], gx[j], gy[j], oj, phic[j]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) o[i][j] = oj[i];
+      }
+      if (lane_out) {
+        const long long ro = (long long)(y0 + it - 6) * a.nx;
+        if constexpr (VEC) {
+          store_row<ST, true>(a, ro, ocol0, o, mu2, phic);
+        } else {
+          store_row_masked<ST>(a, ro, ocol0, nvalid, o, mu2, phic);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      mu2[j] = mu1[j];
+      mu1[j] = mun[j];
+    }
+    rm = r0;
+    r0 = rp;
+    rp = rp + 1 == a.ny ? 0 : rp + 1;
+  }
+}
+
+}  // namespace lbch

@@ -1,0 +1,270 @@
+"""ctypes binding of liblbch.so (the C-ABI declared in include/lbch.h).
+
+The functions keep the C names and only marshal arguments: host arrays become
+pointers, device memory and the stream come from PyTorch. Every computation runs
+in the library's CUDA kernels; there is no Python or CPU fallback. A missing
+library raises ``LbchUnavailable``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+STORE_F32, STORE_BF16_DEV, STORE_F16_DEV = 0, 1, 2
+Q_LITERAL, MU_NESTED, S35_EXPLICIT = 1, 2, 4
+REG_NONE, REG_WILLMORE, REG_LINEAR = 0, 1, 2
+
+OK, EINVAL, ECUDA, ENOMEM, ENONFINITE, ESTATE = 0, -1, -2, -3, -4, -5
+_STATUS = {OK: "LBCH_OK", EINVAL: "LBCH_EINVAL", ECUDA: "LBCH_ECUDA", ENOMEM: "LBCH_ENOMEM",
+           ENONFINITE: "LBCH_ENONFINITE", ESTATE: "LBCH_ESTATE"}
+
+# Bytes moved per node update by one step, by storage (9 populations read and written).
+ALGORITHMIC_BYTES_PER_LU = {STORE_F32: 72, STORE_BF16_DEV: 48, STORE_F16_DEV: 48}
+
+
+class LbchUnavailable(RuntimeError):
+    """The CUDA library is not built or cannot be loaded."""
+
+
+class LbchError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {_STATUS.get(status, status)}" + (f" ({detail})" if detail else ""))
+
+
+class lbch_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("M", ctypes.c_double), ("sigma", ctypes.c_double), ("D", ctypes.c_double),
+        ("eps", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("s", ctypes.c_double * 9),
+        ("storage", ctypes.c_int32), ("regularization", ctypes.c_int32), ("flags", ctypes.c_uint32),
+    ]
+
+
+def make_params(nx: int, ny: int, *, M=0.1, sigma=0.01, D=5.0, eps=0.03, alpha=0.0, s=None,
+                storage=STORE_F32, regularization=REG_WILLMORE, flags=0) -> lbch_params:
+    """lbch_params with the defaults of Eq. 39 (M, eps, D, sigma) and Willmore G."""
+    p = lbch_params()
+    p.nx, p.ny = int(nx), int(ny)
+    p.M, p.sigma, p.D, p.eps, p.alpha = float(M), float(sigma), float(D), float(eps), float(alpha)
+    rates = [1.0] * 9 if s is None else list(s)
+    for i in range(9):
+        p.s[i] = float(rates[i])
+    p.storage, p.regularization, p.flags = int(storage), int(regularization), int(flags)
+    return p
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads liblbch.so (raises LbchUnavailable if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise LbchUnavailable(
+                f"{path} is not built; run paper_2501_03759_gb300.build.build() (nvcc, sm_103a)")
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError as e:
+            raise LbchUnavailable(f"cannot load {path}: {e}") from e
+        P = ctypes.POINTER(lbch_params)
+        dp = ctypes.POINTER(ctypes.c_double)
+        vp = ctypes.c_void_p
+        lib.lbch_workspace_bytes.argtypes = [P]
+        lib.lbch_workspace_bytes.restype = ctypes.c_size_t
+        lib.lbch_create.argtypes = [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        lib.lbch_create.restype = ctypes.c_int
+        for name in ("lbch_init_field", "lbch_set_state"):
+            getattr(lib, name).argtypes = [vp, dp]
+            getattr(lib, name).restype = ctypes.c_int
+        for name in ("lbch_mass", "lbch_free_energy", "lbch_get_field", "lbch_get_state"):
+            getattr(lib, name).argtypes = [vp, dp]
+            getattr(lib, name).restype = ctypes.c_int
+        lib.lbch_step.argtypes = [vp, ctypes.c_int64]
+        lib.lbch_step.restype = ctypes.c_int
+        lib.lbch_steps_taken.argtypes = [vp]
+        lib.lbch_steps_taken.restype = ctypes.c_int64
+        lib.lbch_last_error.argtypes = [vp]
+        lib.lbch_last_error.restype = ctypes.c_char_p
+        lib.lbch_destroy.argtypes = [vp]
+        lib.lbch_destroy.restype = None
+        _lib = lib
+        return lib
+
+
+def _check(ctx, status: int, what: str):
+    if status != OK:
+        detail = ""
+        if ctx:
+            detail = (load().lbch_last_error(ctx) or b"").decode(errors="replace")
+        raise LbchError(status, what, detail)
+
+
+def _host_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _as_host_f64(a, n: int, what: str) -> np.ndarray:
+    if hasattr(a, "detach"):  # torch tensor (possibly pinned): use its memory directly
+        assert a.device.type == "cpu" and a.dtype.is_floating_point, what
+        a = a.detach().numpy()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"{what}: expected {n} values, got {a.size}")
+    return a
+
+
+# ---------------------------------------------------------------- C-ABI, same names
+
+def lbch_workspace_bytes(p: lbch_params) -> int:
+    return int(load().lbch_workspace_bytes(ctypes.byref(p)))
+
+
+def lbch_create(p: lbch_params, d_workspace: int, nbytes: int, cuda_stream: int | None):
+    ctx = ctypes.c_void_p()
+    st = load().lbch_create(ctypes.byref(p), ctypes.c_void_p(int(d_workspace)), int(nbytes),
+                            ctypes.c_void_p(int(cuda_stream or 0)), ctypes.byref(ctx))
+    _check(None, st, "lbch_create")
+    return ctx
+
+
+def lbch_init_field(ctx, phi0) -> None:
+    _check(ctx, load().lbch_init_field(ctx, _host_ptr(phi0)), "lbch_init_field")
+
+
+def lbch_step(ctx, n: int) -> None:
+    _check(ctx, load().lbch_step(ctx, int(n)), "lbch_step")
+
+
+def lbch_mass(ctx) -> float:
+    v = ctypes.c_double()
+    _check(ctx, load().lbch_mass(ctx, ctypes.byref(v)), "lbch_mass")
+    return v.value
+
+
+def lbch_free_energy(ctx) -> float:
+    v = ctypes.c_double()
+    _check(ctx, load().lbch_free_energy(ctx, ctypes.byref(v)), "lbch_free_energy")
+    return v.value
+
+
+def lbch_get_field(ctx, out: np.ndarray) -> np.ndarray:
+    _check(ctx, load().lbch_get_field(ctx, _host_ptr(out)), "lbch_get_field")
+    return out
+
+
+def lbch_get_state(ctx, out: np.ndarray) -> np.ndarray:
+    _check(ctx, load().lbch_get_state(ctx, _host_ptr(out)), "lbch_get_state")
+    return out
+
+
+def lbch_set_state(ctx, f9: np.ndarray) -> None:
+    _check(ctx, load().lbch_set_state(ctx, _host_ptr(f9)), "lbch_set_state")
+
+
+def lbch_steps_taken(ctx) -> int:
+    return int(load().lbch_steps_taken(ctx))
+
+
+def lbch_last_error(ctx) -> str:
+    return (load().lbch_last_error(ctx) or b"").decode(errors="replace")
+
+
+def lbch_destroy(ctx) -> None:
+    if ctx:
+        load().lbch_destroy(ctx)
+
+
+# ---------------------------------------------------------------- convenience owner
+
+class Solver:
+    """Owns a context and its device workspace (a torch uint8 tensor) on one stream.
+
+    Host inputs are float64 arrays of shape (ny, nx) (phi) or (9, ny, nx) (state);
+    pinned torch CPU tensors are accepted and used in place.
+    """
+
+    def __init__(self, params: lbch_params, device=None, stream=None):
+        import torch
+
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        nbytes = lbch_workspace_bytes(params)
+        if nbytes == 0:
+            raise LbchError(EINVAL, "lbch_workspace_bytes", "invalid parameters")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.ctx = lbch_create(params, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    def _on_device(self):
+        import torch
+        return torch.cuda.device(self.device)
+
+    def init_field(self, phi0) -> None:
+        a = _as_host_f64(phi0, self.nx * self.ny, "phi0")
+        with self._on_device():
+            lbch_init_field(self.ctx, a)
+
+    def step(self, n: int) -> None:
+        with self._on_device():
+            lbch_step(self.ctx, n)
+
+    def mass(self) -> float:
+        with self._on_device():
+            return lbch_mass(self.ctx)
+
+    def free_energy(self) -> float:
+        with self._on_device():
+            return lbch_free_energy(self.ctx)
+
+    def field(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.ny, self.nx), dtype=np.float64)
+        buf = out.detach().numpy() if hasattr(out, "detach") else out
+        assert buf.dtype == np.float64 and buf.flags.c_contiguous and buf.size == self.nx * self.ny
+        with self._on_device():
+            lbch_get_field(self.ctx, buf)
+        return out
+
+    def state(self) -> np.ndarray:
+        out = np.empty((9, self.ny, self.nx), dtype=np.float64)
+        with self._on_device():
+            lbch_get_state(self.ctx, out)
+        return out
+
+    def set_state(self, f9) -> None:
+        a = _as_host_f64(f9, 9 * self.nx * self.ny, "state")
+        with self._on_device():
+            lbch_set_state(self.ctx, a)
+
+    @property
+    def steps_taken(self) -> int:
+        return lbch_steps_taken(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            lbch_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+FP32 state: max |dphi| <= 1e-6 after 1 step and <= 1e-4 after 1000 steps on the
+64x64 droplet workload; the same 1e-6 bound for up to 10 steps on every other
+shape. Energies agree to 1e-5 relative; FP32 mass drifts by at most 1e-6
+relative over 2000 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2501_03759_gb300 import lbch  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    lbch.load()
+
+
+def solver(nx, ny, **kw):
+    return lbch.Solver(lbch.make_params(nx, ny, **kw))
+
+
+def oparams(nx, ny, **kw):
+    kw.pop("storage", None)
+    return oracle.Params(nx, ny, **kw)
+
+
+def both(nx, ny, phi0, checkpoints, **kw):
+    """phi from the GPU and from the oracle at each checkpoint (cumulative steps)."""
+    s = solver(nx, ny, **kw)
+    s.init_field(phi0)
+    p = oparams(nx, ny, **kw)
+    f = oracle.init(p, phi0)
+    out, done = [], 0
+    for t in checkpoints:
+        s.step(t - done)
+        f = oracle.step(p, f, t - done)
+        done = t
+        out.append((t, s.field(), oracle.phi(p, f), s, p, f))
+    return out
+
+
+def test_droplet_64_parity_over_time():
+    phi0 = W.droplet_workload(64)
+    bounds = {1: 1e-6, 10: 1e-6, 100: 1e-5, 1000: 1e-4, 2000: 1e-4}
+    res = both(64, 64, phi0, list(bounds), alpha=0.3)
+    for t, g, r, *_ in res:
+        err = np.abs(g - r).max()
+        print(f"droplet 64 alpha=0.3 step {t}: max|dphi| = {err:.3e}")
+        assert err <= bounds[t], (t, err)
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (9, 7), (13, 11), (4, 4), (1, 5), (7, 1), (100, 100),
+                                   (130, 67), (250, 33), (124, 9), (241, 19), (256, 40)])
+@pytest.mark.parametrize("alpha", [0.0, 0.3])
+def test_shapes_parity(shape, alpha):
+    nx, ny = shape
+    phi0 = W.noise(nx, ny, 0.6, 7)
+    for t, g, r, *_ in both(nx, ny, phi0, [1, 10], alpha=alpha):
+        err = np.abs(g - r).max()
+        assert err <= 1e-6, (shape, t, err)
+
+
+def test_spinodal_256_parity():
+    phi0 = W.noise(256, 256, 0.05, 0)
+    for t, g, r, *_ in both(256, 256, phi0, [1, 200], alpha=0.2):
+        err = np.abs(g - r).max()
+        print(f"spinodal 256 alpha=0.2 step {t}: max|dphi| = {err:.3e}")
+        assert err <= (1e-6 if t == 1 else 1e-5), (t, err)
+
+
+@pytest.mark.parametrize("variant", [
+    dict(flags=lbch.MU_NESTED), dict(flags=lbch.Q_LITERAL), dict(regularization=lbch.REG_LINEAR),
+    dict(regularization=lbch.REG_NONE), dict(eps=0.1),
+    dict(s=[1.0, 0.8, 1.3, 1.0, 1.6, 1.0, 0.7, 1.1, 1.5]),
+    dict(s=[1.0, 1.2, 1.2, 0.9, 1.2, 0.9, 1.2, 1.2, 1.2], flags=lbch.S35_EXPLICIT),
+])
+def test_variant_parity(variant):
+    kw = dict(alpha=0.3)
+    kw.update(variant)
+    oflags = kw.get("flags", 0)
+    phi0 = W.noise(64, 48, 0.5, 3)
+    s = solver(64, 48, **kw)
+    s.init_field(phi0)
+    okw = dict(kw)
+    okw["flags"] = oflags  # same bit values in both APIs
+    p = oparams(64, 48, **okw)
+    f = oracle.init(p, phi0)
+    s.step(10)
+    f = oracle.step(p, f, 10)
+    err = np.abs(s.field() - oracle.phi(p, f)).max()
+    assert err <= 1e-6, (variant, err)
+
+
+def test_state_matches_oracle_populations():
+    phi0 = W.droplet_workload(64)
+    s = solver(64, 64, alpha=0.3)
+    s.init_field(phi0)
+    p = oparams(64, 64, alpha=0.3)
+    f = oracle.init(p, phi0)
+    assert np.abs(s.state() - f).max() <= 1e-7
+    s.step(5)
+    f = oracle.step(p, f, 5)
+    assert np.abs(s.state() - f).max() <= 1e-7
+
+
+def test_checkpoint_resume_bitwise_f32():
+    phi0 = W.noise(96, 64, 0.5, 9)
+    a = solver(96, 64, alpha=0.3)
+    a.init_field(phi0)
+    a.step(13)
+    ckpt = a.state()
+    a.step(17)
+    b = solver(96, 64, alpha=0.3)
+    b.set_state(ckpt)
+    b.step(17)
+    assert np.array_equal(a.field(), b.field())
+    assert np.array_equal(a.state(), b.state())
+
+
+def test_mass_and_energy():
+    phi0 = W.droplet_workload(64)
+    s = solver(64, 64, alpha=0.3)
+    s.init_field(phi0)
+    p = oparams(64, 64, alpha=0.3)
+    f = oracle.init(p, phi0)
+    m0 = s.mass()
+    assert abs(m0 - oracle.mass(p, f)) <= 1e-9 * abs(m0)
+    done = 0
+    for t in (0, 10, 100, 1000, 2000):
+        s.step(t - done)
+        f = oracle.step(p, f, t - done)
+        done = t
+        e, e_ref = s.free_energy(), oracle.energy(p, f)
+        print(f"step {t}: energy {e:.10f} oracle {e_ref:.10f}")
+        assert abs(e - e_ref) <= 1e-5 * abs(e_ref), (t, e, e_ref)
+    assert abs(s.mass() - m0) <= 1e-6 * abs(m0)
+
+
+def test_energy_non_increasing_on_gpu():
+    s = solver(64, 64, alpha=0.3)
+    s.init_field(W.droplet_workload(64))
+    E = [s.free_energy()]
+    for _ in range(100):
+        s.step(10)
+        E.append(s.free_energy())
+    E = np.array(E)
+    assert np.all(np.diff(E) <= 1e-6 * np.abs(E[:-1]))
+
+
+def test_full_size_8192_sampled_windows():
+    """The 8192x8192 spinodal workload, in the launch shape the benchmark times."""
+    n, steps = 8192, 2
+    phi0 = W.noise(n, n, 0.05, 0)
+    s = solver(n, n, alpha=0.3)
+    s.init_field(phi0)
+    s.step(steps)
+    g = s.field()
+    p = oparams(n, n, alpha=0.3)
+    rng = np.random.default_rng(1)
+    corners = [(0, 0), (n - 16, n - 16), (n - 8, 0), (0, n - 8), (4000, 4090), (119, 7000)]
+    corners += [tuple(v) for v in rng.integers(0, n - 16, size=(6, 2))]
+    worst = 0.0
+    for (x0, y0) in corners:
+        ref = oracle.run_window(p, phi0, x0, y0, 16, 16, steps)
+        worst = max(worst, np.abs(g[y0:y0 + 16, x0:x0 + 16] - ref).max())
+    print(f"8192^2 sampled windows after {steps} steps: max|dphi| = {worst:.3e}")
+    assert worst <= 1e-6
+    assert np.isfinite(g).all()
+    s.close()
+
+
+def test_errors_on_gpu():
+    s = solver(32, 32, alpha=0.3)
+    with pytest.raises(lbch.LbchError) as e:
+        s.step(1)
+    assert e.value.status == lbch.EINVAL
+    bad = W.noise(32, 32, 0.5, 1)
+    bad[3, 4] = np.nan
+    with pytest.raises(lbch.LbchError) as e:
+        s.init_field(bad)
+    assert e.value.status == lbch.ENONFINITE
+    s.init_field(W.noise(32, 32, 0.5, 1))
+    with pytest.raises(lbch.LbchError) as e:
+        s.step(-1)
+    assert e.value.status == lbch.EINVAL
+    st = s.state()
+    st[2, 1, 1] = np.inf
+    with pytest.raises(lbch.LbchError) as e:
+        s.set_state(st)
+    assert e.value.status == lbch.ENONFINITE
+    s.init_field(W.noise(32, 32, 0.5, 1))
+    s.step(3)
+    assert s.steps_taken == 3
+
+
+@pytest.mark.parametrize("storage", [lbch.STORE_BF16_DEV, lbch.STORE_F16_DEV])
+def test_deviation_storage_reported(storage):
+    """16-bit deviation storage: error against the oracle is reported; gated loosely."""
+    phi0 = W.droplet_workload(64)
+    res = both(64, 64, phi0, [1, 100, 1000], alpha=0.3, storage=storage)
+    name = {lbch.STORE_BF16_DEV: "bf16-dev", lbch.STORE_F16_DEV: "f16-dev"}[storage]
+    for t, g, r, s, p, f in res:
+        err = np.abs(g - r).max()
+        print(f"{name} droplet 64 step {t}: max|dphi| = {err:.3e}")
+        assert err <= 1e-2, (t, err)
+    m0 = float(W.droplet_workload(64).sum())
+    drift = abs(res[-1][3].mass() - m0) / abs(m0)
+    print(f"{name} mass drift after 1000 steps: {drift:.3e}")
+    assert drift <= 1e-5
