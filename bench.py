@@ -89,6 +89,22 @@ def profiled_traffic(storage_name: str):
         return None
 
 
+def max_over_ranks(dist, v: float) -> float:
+    """Maximum of a per-rank scalar over the process group (identity without one)."""
+    if dist is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, max_seconds: float) -> float:
+    """Whole-job throughput of independent replicas: all units over the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -295,21 +311,14 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     barrier()
     with ClockSampler(gpu_id) as clk:
         r32 = time_storage(lbch, torch, phi0, n, lbch.STORE_F32, args.steps, args.warmup)
     barrier()
-    total = max_over_ranks(r32["total_s"])
-    per_launch = max_over_ranks(r32["kernel_s_per_launch"])
+    total = max_over_ranks(dist, r32["total_s"])
+    per_launch = max_over_ranks(dist, r32["kernel_s_per_launch"])
     lu_per_rank = args.steps * INNER * n * n
-    value = world * lu_per_rank / total / 1e6
+    value = job_rate(world, lu_per_rank, total) / 1e6
 
     peak, peak_kind = measured_peaks()
     bpl = lbch.ALGORITHMIC_BYTES_PER_LU[lbch.STORE_F32]
@@ -324,10 +333,10 @@ def main():
     if not args.no_variants:
         for name, st in (("bf16_dev", lbch.STORE_BF16_DEV), ("f16_dev", lbch.STORE_F16_DEV)):
             r = time_storage(lbch, torch, phi0, n, st, args.steps, args.warmup)
-            pl = max_over_ranks(r["kernel_s_per_launch"])
+            pl = max_over_ranks(dist, r["kernel_s_per_launch"])
             b = lbch.ALGORITHMIC_BYTES_PER_LU[st]
             ach = b * n * n / pl / 1e9
-            variants[name] = {"value": world * lu_per_rank / max_over_ranks(r["total_s"]) / 1e6,
+            variants[name] = {"value": job_rate(world, lu_per_rank, max_over_ranks(dist, r["total_s"])) / 1e6,
                               "unit": "MLUPS", "launch_ms": pl * 1e3,
                               "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                            "frac": ach / peak, "traffic": None if profiled_traffic(name) is None
@@ -339,7 +348,7 @@ def main():
     if not args.no_e2e:
         e = run_e2e(lbch, torch, phi0, n, max(1, min(args.steps, 5)), 1)
         barrier()
-        e2e = {"value": world * e["lu"] / max_over_ranks(e["wall_s"]) / 1e6, "unit": "MLUPS",
+        e2e = {"value": job_rate(world, e["lu"], max_over_ranks(dist, e["wall_s"])) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": e["h2d_bytes_per_step"], "d2h_bytes_per_step": e["d2h_bytes_per_step"],
                "lattice_steps_per_step": INNER}
 

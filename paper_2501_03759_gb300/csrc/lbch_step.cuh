@@ -188,7 +188,6 @@ __device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], 
   const float n5 = fmaf(a.c5a, m5, a.c5g * gy);
   const float n6 = fmaf(a.c6a, m6, a.c6g * gy);
   const float n7 = a.c7 * m7, n8 = a.c8 * m8;
-  o[0] = fmaf(4.0f, n2 - n1, n0);
   const float A0 = fmaf(-2.0f, n2, n0 - n1);
   const float B = A0 + n7, C = A0 - n7;
   const float X = fmaf(-2.0f, n4, n3), Y = fmaf(-2.0f, n6, n5);
@@ -204,6 +203,13 @@ __device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], 
   o[7] = E - P;
   o[6] = G - Mv;
   o[8] = G + Mv;
+  // Row 0 of M^-1 m* would be n0 - 4 n1 + 4 n2, but FP32 n0 = phi/9 carries a fixed
+  // relative bias. Since sum_i f*_i = sum_i f_i (m_0 is conserved, Eq. 34), the rest
+  // population takes what the moving ones gave up: f*_0 = f_0 + sum_{i>=1} (f_i - f*_i).
+  // The differences of nearby values are exact and small, so the only rounding at the
+  // scale of phi is the final add.
+  o[0] = f[0] + ((((f[1] - o[1]) + (f[2] - o[2])) + ((f[3] - o[3]) + (f[4] - o[4]))) +
+                 (((f[5] - o[5]) + (f[6] - o[6])) + ((f[7] - o[7]) + (f[8] - o[8]))));
   phi_out = phi;
 }
 

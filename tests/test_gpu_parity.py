@@ -106,10 +106,11 @@ def test_state_matches_oracle_populations():
     s.init_field(phi0)
     p = oparams(64, 64, alpha=0.3)
     f = oracle.init(p, phi0)
-    assert np.abs(s.state() - f).max() <= 1e-7
+    # Initial populations differ by their FP32 rounding only.
+    assert np.all(np.abs(s.state() - f) <= np.abs(f) * 2.0 ** -24 + 1e-30)
     s.step(5)
     f = oracle.step(p, f, 5)
-    assert np.abs(s.state() - f).max() <= 1e-7
+    assert np.abs(s.state() - f).max() <= 1e-6
 
 
 def test_checkpoint_resume_bitwise_f32():
@@ -133,7 +134,8 @@ def test_mass_and_energy():
     p = oparams(64, 64, alpha=0.3)
     f = oracle.init(p, phi0)
     m0 = s.mass()
-    assert abs(m0 - oracle.mass(p, f)) <= 1e-9 * abs(m0)
+    # The GPU sums FP32-rounded populations (in FP64): at most 2^-24 |f| per population.
+    assert abs(m0 - oracle.mass(p, f)) <= np.abs(f).sum() * 2.0 ** -24
     done = 0
     for t in (0, 10, 100, 1000, 2000):
         s.step(t - done)
@@ -166,7 +168,7 @@ def test_full_size_8192_sampled_windows():
     g = s.field()
     p = oparams(n, n, alpha=0.3)
     rng = np.random.default_rng(1)
-    corners = [(0, 0), (n - 16, n - 16), (n - 8, 0), (0, n - 8), (4000, 4090), (119, 7000)]
+    corners = [(0, 0), (n - 16, n - 16), (n - 16, 0), (0, n - 16), (4000, 4090), (116, 7000)]
     corners += [tuple(v) for v in rng.integers(0, n - 16, size=(6, 2))]
     worst = 0.0
     for (x0, y0) in corners:
@@ -208,11 +210,13 @@ def test_deviation_storage_reported(storage):
     phi0 = W.droplet_workload(64)
     res = both(64, 64, phi0, [1, 100, 1000], alpha=0.3, storage=storage)
     name = {lbch.STORE_BF16_DEV: "bf16-dev", lbch.STORE_F16_DEV: "f16-dev"}[storage]
+    bounds = {1: 2e-6, 100: 1e-5, 1000: 1e-4}  # regression guard at the FP32 bounds
     for t, g, r, s, p, f in res:
         err = np.abs(g - r).max()
         print(f"{name} droplet 64 step {t}: max|dphi| = {err:.3e}")
-        assert err <= 1e-2, (t, err)
-    m0 = float(W.droplet_workload(64).sum())
-    drift = abs(res[-1][3].mass() - m0) / abs(m0)
+        assert err <= bounds[t], (t, err)
+    t, g, r, s, p, f = res[-1]
+    m0 = oracle.mass(p, f)  # the oracle conserves mass to 1e-13
+    drift = abs(s.mass() - m0) / abs(m0)
     print(f"{name} mass drift after 1000 steps: {drift:.3e}")
     assert drift <= 1e-5
