@@ -138,6 +138,32 @@ const char* lbch_last_error(const lbch_ctx* ctx);
 /* Frees the host-side context. Never touches the workspace. NULL is ignored. */
 void lbch_destroy(lbch_ctx* ctx);
 
+/* Free energy of a state the caller holds in device memory, computed without any
+ * device allocation. This is a library convenience with no counterpart in the paper.
+ * It serves callers that cannot call cudaMalloc, or cannot hand this library an
+ * allocator: code whose device memory all comes from a pool fixed at start-up, or a
+ * host application that is only allowed to launch work on memory it already owns.
+ * It computes the same quantity as lbch_free_energy, without a context or workspace.
+ *   p:            scheme parameters (nx, ny, sigma, D, eps, alpha, regularization; the
+ *                 storage field is ignored).
+ *   d_f9:         device array of the post-streaming populations f_i(x, t) in FP32, 9
+ *                 planes, plane i starting at d_f9 + i * plane_stride, each row-major with
+ *                 x fastest (the layout of lbch_get_state, in FP32 on the device).
+ *   plane_stride: elements between planes, >= nx * ny.
+ *   d_out:        device pointer to one double that receives the energy.
+ *   cuda_stream:  stream for the work (NULL for the legacy default stream); the call
+ *                 returns without synchronising it.
+ * The scratch (phi in FP32 and the FP64 partial sums) lives in one file-scope
+ * __device__ array of 16,793,600 bytes that every GPU loading the library holds until
+ * the process exits. So nx * ny may be at most 4,194,304 (2048 x 2048); larger grids
+ * return LBCH_EINVAL. The first call on each device resolves that array's device
+ * address (cudaGetSymbolAddress) and the SM count; make that first call before any
+ * stream capture. All calls share the array and every call overwrites the parts it
+ * reads (nothing carries over between calls), so calls that overlap on the GPU race.
+ * Returns LBCH_EINVAL for bad arguments, LBCH_ECUDA if set-up or a launch fails. */
+lbch_status lbch_free_energy_static(const lbch_params* p, const float* d_f9, int64_t plane_stride,
+                                    double* d_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "lbch.h"
@@ -491,6 +492,96 @@ lbch_status lbch_set_state(lbch_ctx* c, const double* h_f9) {
 }
 
 int64_t lbch_steps_taken(const lbch_ctx* c) { return c ? c->steps : -1; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free free energy (lbch_free_energy_static): the same phi -> energy ->
+// fixed-order FP64 sum as lbch_free_energy, with its scratch in one static device array.
+
+namespace {
+
+constexpr long long STATIC_MAX_NODES = 1LL << 22;  // 2048 x 2048
+constexpr size_t STATIC_PARTIAL_BYTES = (size_t)MAX_RED_BLOCKS * sizeof(double);
+constexpr size_t STATIC_SCRATCH_BYTES = STATIC_PARTIAL_BYTES + (size_t)STATIC_MAX_NODES * sizeof(float);
+
+// FP64 partial sums (first MAX_RED_BLOCKS doubles), then phi in FP32.
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_static_mu;
+void* g_static_addr[MAX_DEVICES];  // device address of g_static_scratch, per device
+int g_static_sms[MAX_DEVICES];
+
+// phi = sum_i f_i (Eq. 22) of canonical FP32 populations, summed in FP64, stored in FP32.
+__global__ void phi_canonical_kernel(const float* __restrict__ f, long long ps, long long n,
+                                     float* __restrict__ phi) {
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+       id += (long long)gridDim.x * blockDim.x) {
+    double p = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) p += (double)f[(long long)i * ps + id];
+    phi[id] = (float)p;
+  }
+}
+
+// Resolves the scratch address and SM count of the current device once.
+cudaError_t static_setup(void** addr, int* sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_static_sms[dev] = n;
+    g_static_addr[dev] = p;
+  }
+  *addr = g_static_addr[dev];
+  *sms = g_static_sms[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbch_status lbch_free_energy_static(const lbch_params* p, const float* d_f9, int64_t plane_stride,
+                                    double* d_out, void* cuda_stream) {
+  if (check_params(p) || !d_f9 || !d_out) return LBCH_EINVAL;
+  const long long n = (long long)p->nx * p->ny;
+  if (plane_stride < n) return LBCH_EINVAL;
+  if (n > STATIC_MAX_NODES) return LBCH_EINVAL;  // beyond the static scratch
+  void* base = nullptr;
+  int sms = 0;
+  if (static_setup(&base, &sms) != cudaSuccess) return LBCH_ECUDA;
+  double* partial = reinterpret_cast<double*>(base);
+  float* phi = reinterpret_cast<float*>(static_cast<char*>(base) + STATIC_PARTIAL_BYTES);
+  long long blocks = (n + AUX_THREADS - 1) / AUX_THREADS;
+  const long long cap = (long long)sms * 8 < MAX_RED_BLOCKS ? (long long)sms * 8 : MAX_RED_BLOCKS;
+  if (blocks > cap) blocks = cap;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const double k = 3.0 * p->sigma * p->D / 8.0, beta = 3.0 * p->sigma / (4.0 * p->D);  // Eq. 5
+  const double eps = p->regularization == LBCH_REG_NONE ? 0.0 : p->eps;
+  EnergyConsts ec;
+  ec.k = (float)k;
+  ec.beta = (float)beta;
+  ec.beta4 = (float)(4.0 * beta);
+  ec.alpha = (float)p->alpha;
+  ec.half_eps = (float)(0.5 * eps);
+  ec.cw = p->regularization == LBCH_REG_LINEAR ? 0.0f : 1.0f;
+  // Every partial slot the final sum reads, and every phi value the energy kernel reads,
+  // is written earlier in this same call: nothing needs clearing.
+  phi_canonical_kernel<<<(int)blocks, AUX_THREADS, 0, st>>>(d_f9, plane_stride, n, phi);
+  energy_kernel<<<(int)blocks, AUX_THREADS, 0, st>>>(phi, Grid{p->nx, p->ny, plane_stride}, ec, partial);
+  final_sum_kernel<<<1, 1024, 0, st>>>(partial, (int)blocks, d_out);
+  return cudaGetLastError() == cudaSuccess ? LBCH_OK : LBCH_ECUDA;
+}
 
 const char* lbch_last_error(const lbch_ctx* c) { return c ? c->err : "context is NULL"; }
 

@@ -103,6 +103,8 @@ def load():
         lib.lbch_last_error.restype = ctypes.c_char_p
         lib.lbch_destroy.argtypes = [vp]
         lib.lbch_destroy.restype = None
+        lib.lbch_free_energy_static.argtypes = [P, vp, ctypes.c_int64, vp, vp]
+        lib.lbch_free_energy_static.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -188,6 +190,18 @@ def lbch_last_error(ctx) -> str:
 def lbch_destroy(ctx) -> None:
     if ctx:
         load().lbch_destroy(ctx)
+
+
+def lbch_free_energy_static(p: lbch_params, d_f9: int, plane_stride: int, d_out: int,
+                            cuda_stream: int | None) -> None:
+    """Free energy of caller-held FP32 populations on the device, without device allocation.
+
+    d_f9 and d_out are device addresses (e.g. ``tensor.data_ptr()``); the result lands in
+    the double at d_out, asynchronously on the stream.
+    """
+    st = load().lbch_free_energy_static(ctypes.byref(p), ctypes.c_void_p(int(d_f9)), int(plane_stride),
+                                        ctypes.c_void_p(int(d_out)), ctypes.c_void_p(int(cuda_stream or 0)))
+    _check(None, st, "lbch_free_energy_static")
 
 
 # ---------------------------------------------------------------- convenience owner
