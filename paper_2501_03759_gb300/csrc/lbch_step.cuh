@@ -18,10 +18,11 @@
 // arrives it completes grad/lap phi of row r-1, mu_beta of row r-2 and
 // grad mu_beta of row r-3, and collides row r-3. Left/right neighbours come from
 // warp shuffles; the 4 strip columns at each edge are halo, so a strip yields 120
-// output columns. The pulled populations of the last rows wait for their
-// collision in a per-warp shared-memory ring (each lane reads back only what it
-// wrote). No tensor cores: the 9x9 moment transform is a handful of adds with
-// constant +-1/+-2 entries.
+// output columns. Rows arrive by cp.async into a per-warp shared-memory ring of
+// landing slots, fetched PF_DIST rows ahead of use; a row stays in the ring until
+// its collision three rows later (each lane reads back only what it copied, so no
+// barrier is needed). No tensor cores: the 9x9 moment transform is a handful of
+// adds with constant +-1/+-2 entries.
 #pragma once
 
 #include "lbch_lattice.cuh"
@@ -32,9 +33,11 @@ constexpr int STRIP_W = 128;                 // columns per warp strip
 constexpr int HALO_W = 4;                    // halo columns on each side
 constexpr int OUT_W = STRIP_W - 2 * HALO_W;  // output columns per strip
 constexpr int STEP_WARPS = 4;                // warps per CTA
-constexpr int RING = 4;                      // rows of pulled populations in flight
-constexpr int RING_FLOAT4 = RING * 9 * 32;   // float4 per warp
-constexpr int STEP_SMEM = STEP_WARPS * RING_FLOAT4 * 16;
+constexpr int STEP_MIN_CTAS = 2;             // CTAs per SM the launch bounds plan for
+constexpr int PF_DIST = 1;                   // rows fetched ahead of the phi row
+constexpr int SLOTS = PF_DIST + 4;           // rows held per warp: r-3 (collision) .. r+PF_DIST
+constexpr int SLOT_F4 = 9 * 32;              // 16-byte units per slot (9 per lane)
+constexpr int STEP_SMEM = STEP_WARPS * SLOTS * SLOT_F4 * 16;
 
 struct StepArgs {
   Buf src, dst;
@@ -81,56 +84,90 @@ struct Cols {
   int cs[6];     // columns xs + 4 lane + k - 1, k = 0..5 (scalar path), mod nx
 };
 
-// Post-collision value f*_i at the 4 columns of `base` (+ column offsets) of one row.
-template <int ST, bool VEC, int I>
-__device__ __forceinline__ void load_fstar(const StepArgs& a, long long ro, const Cols& cl,
-                                           float (&v)[4]) {
-  constexpr int SH = -cx(I);  // pull: f_in,i(x) = f*_i(x - c_i)
-  if constexpr (ST == ST_F32) {
-    const float* p = a.src.f32 + (long long)I * a.ps + ro;
-    if constexpr (VEC) {
-      const float4 t = __ldg(reinterpret_cast<const float4*>(p + cl.c0));
-      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-    } else {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One warp's landing slot for one phi row r, as 16-byte units [q][lane]:
+//   vector F32:  q = i holds plane i of row r - c_iy at the strip's aligned columns (raw f*);
+//   vector DEV:  q = 0 the rest plane of row r, q = 1..3 the anchor plane of rows r-1, r, r+1,
+//                then (as 8-byte units [k][lane]) the deviation plane k+1 of row r - c_(k+1)y;
+//   scalar path: q = i holds f_in,i itself (pulled and rebuilt when it was fetched).
+// Fetches phi row r (rows ro_m = r-1, ro_0 = r, ro_p = r+1) into a slot; the vector path
+// copies asynchronously (cp.async), the scalar path loads and stores synchronously.
+template <int ST, bool VEC>
+__device__ __forceinline__ void issue_row(const StepArgs& a, float4* slot, int lane, long long ro_m,
+                                          long long ro_0, long long ro_p, const Cols& cl) {
+#define LBCH_RO(I) (cy(I) == 1 ? ro_m : (cy(I) == -1 ? ro_p : ro_0))
+  if constexpr (VEC) {
+    if constexpr (ST == ST_F32) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = __ldg(p + cl.cs[j + SH + 1]);
+      for (int i = 0; i < 9; ++i)
+        cp_async16(slot + i * 32 + lane, a.src.f32 + (long long)i * a.ps + LBCH_RO(i) + cl.c0);
+    } else {
+      cp_async16(slot + lane, a.src.f32 + ro_0 + cl.c0);
+      cp_async16(slot + 32 + lane, a.src.f32 + a.ps + ro_m + cl.c0);
+      cp_async16(slot + 64 + lane, a.src.f32 + a.ps + ro_0 + cl.c0);
+      cp_async16(slot + 96 + lane, a.src.f32 + a.ps + ro_p + cl.c0);
+      uint2* ds = reinterpret_cast<uint2*>(slot + 128);
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        cp_async8(ds + (i - 1) * 32 + lane, a.src.dev + (long long)(i - 1) * a.ps + LBCH_RO(i) + cl.c0);
     }
   } else {
-    using D = Dev<ST>;
-    if constexpr (I == 0) {
-      const float* p = a.src.f32 + ro;
-      if constexpr (VEC) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(p + cl.c0));
-        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-      } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = __ldg(p + cl.cs[j + 1]);
-      }
-    } else {
-      const float w = (float)wgt(I);
-      const float* pm = a.src.f32 + a.ps + ro;
-      const uint16_t* pd = a.src.dev + (long long)(I - 1) * a.ps + ro;
-      if constexpr (VEC) {
-        const float4 m = __ldg(reinterpret_cast<const float4*>(pm + cl.c0));
-        const uint2 raw = __ldg(reinterpret_cast<const uint2*>(pd + cl.c0));
-        v[0] = fmaf(w, m.x, D::load(static_cast<uint16_t>(raw.x & 0xffffu)));
-        v[1] = fmaf(w, m.y, D::load(static_cast<uint16_t>(raw.x >> 16)));
-        v[2] = fmaf(w, m.z, D::load(static_cast<uint16_t>(raw.y & 0xffffu)));
-        v[3] = fmaf(w, m.w, D::load(static_cast<uint16_t>(raw.y >> 16)));
-      } else {
+    for (int i = 0; i < 9; ++i) {
+      float v[4];
+      const long long ro = LBCH_RO(i);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = cl.cs[j + SH + 1];
-          v[j] = fmaf(w, __ldg(pm + c), D::load(__ldg(pd + c)));
+      for (int j = 0; j < 4; ++j) {
+        const int c = cl.cs[j - cx(i) + 1];  // pull: f_in,i(x) = f*_i(x - c_i)
+        if constexpr (ST == ST_F32) {
+          v[j] = __ldg(a.src.f32 + (long long)i * a.ps + ro + c);
+        } else if (i == 0) {
+          v[j] = __ldg(a.src.f32 + ro + c);
+        } else {
+          v[j] = fmaf((float)wgt(i), __ldg(a.src.f32 + a.ps + ro + c),
+                      Dev<ST>::load(__ldg(a.src.dev + (long long)(i - 1) * a.ps + ro + c)));
         }
       }
+      slot[i * 32 + lane] = make_float4(v[0], v[1], v[2], v[3]);
     }
   }
-  if constexpr (VEC) {
-    if constexpr (SH == -1) {  // c_x = +1: take the column to the left
+#undef LBCH_RO
+}
+
+// f_in,I at this lane's 4 columns from a landed slot.
+template <int ST, bool VEC, int I>
+__device__ __forceinline__ void read_row(const float4* slot, int lane, float (&v)[4]) {
+  if constexpr (!VEC || ST == ST_F32 || I == 0) {
+    const float4 t = slot[I * 32 + lane];
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    // Rebuild f*_I = w_I anchor + deviation at the source node (row r - c_Iy).
+    const float w = (float)wgt(I);
+    const float4 m = slot[(2 - cy(I)) * 32 + lane];
+    const uint2 raw = reinterpret_cast<const uint2*>(slot + 128)[(I - 1) * 32 + lane];
+    v[0] = fmaf(w, m.x, Dev<ST>::load(static_cast<uint16_t>(raw.x & 0xffffu)));
+    v[1] = fmaf(w, m.y, Dev<ST>::load(static_cast<uint16_t>(raw.x >> 16)));
+    v[2] = fmaf(w, m.z, Dev<ST>::load(static_cast<uint16_t>(raw.y & 0xffffu)));
+    v[3] = fmaf(w, m.w, Dev<ST>::load(static_cast<uint16_t>(raw.y >> 16)));
+  }
+  if constexpr (VEC) {  // the pull shift along x happens here, one shuffle per plane
+    if constexpr (cx(I) == 1) {  // take the column to the left
       const float prev = __shfl_up_sync(FULL, v[3], 1);
       v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
-    } else if constexpr (SH == 1) {  // c_x = -1: take the column to the right
+    } else if constexpr (cx(I) == -1) {  // take the column to the right
       const float next = __shfl_down_sync(FULL, v[0], 1);
       v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
     }
@@ -301,8 +338,9 @@ __device__ __forceinline__ void store_row_masked(const StepArgs& a, long long ro
 }
 
 template <int ST, bool VEC>
-__global__ void __launch_bounds__(STEP_WARPS * 32, 3) step_kernel(const __grid_constant__ StepArgs a) {
-  extern __shared__ float4 smem_ring[];
+__global__ void __launch_bounds__(STEP_WARPS * 32, STEP_MIN_CTAS)
+    step_kernel(const __grid_constant__ StepArgs a) {
+  extern __shared__ float4 smem_slots[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const long long warp = (long long)blockIdx.x * STEP_WARPS + wib;
@@ -312,7 +350,7 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, 3) step_kernel(const __grid_c
   const int y0 = seg * a.seg_len;
   const int y1 = min(y0 + a.seg_len, a.ny);
   const int xs = strip * OUT_W - HALO_W;  // strip start column (before wrap)
-  float4* ring = smem_ring + wib * RING_FLOAT4 + lane;
+  float4* slots = smem_slots + wib * (SLOTS * SLOT_F4);  // this warp's landing slots
 
   Cols cl;
   cl.c0 = imod(xs + 4 * lane, a.nx);
@@ -336,20 +374,31 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, 3) step_kernel(const __grid_c
   }
 
   const int n_it = (y1 - y0) + 6;
-  int rm = imod(y0 - 4, a.ny);  // row r - 1 (mod ny) for the first iteration
-  int r0 = imod(y0 - 3, a.ny);
-  int rp = imod(y0 - 2, a.ny);
+  // Rows r-1, r, r+1 (mod ny) of the next phi row to fetch; phi rows start at y0 - 3.
+  int fm = imod(y0 - 4, a.ny), f0 = imod(y0 - 3, a.ny), fp = imod(y0 - 2, a.ny);
+  auto fetch_next = [&](float4* slot) {
+    issue_row<ST, VEC>(a, slot, lane, (long long)fm * a.nx, (long long)f0 * a.nx, (long long)fp * a.nx, cl);
+    fm = f0;
+    f0 = fp;
+    fp = fp + 1 == a.ny ? 0 : fp + 1;
+  };
+#pragma unroll
+  for (int d = 0; d < PF_DIST; ++d) {
+    if (d < n_it) fetch_next(slots + d * SLOT_F4);
+    cp_async_commit();
+  }
+  int s_cur = 0, s_pf = PF_DIST, s_col = SLOTS - 3;  // slots of rows r, r + PF_DIST, r - 3
   for (int it = 0; it < n_it; ++it) {
-    const long long ro_m = (long long)rm * a.nx, ro_0 = (long long)r0 * a.nx,
-                    ro_p = (long long)rp * a.nx;
-    // 1. Pull row r of f_in, stash it for its collision, and sum phi (Eq. 22).
+    // 1. Fetch row r + PF_DIST; wait for row r; pull it and sum phi (Eq. 22).
+    if (it + PF_DIST < n_it) fetch_next(slots + s_pf * SLOT_F4);
+    cp_async_commit();
+    cp_async_wait<PF_DIST>();
     float ph[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float4* slot = ring + (it & (RING - 1)) * (9 * 32);
     {
+      const float4* slot = slots + s_cur * SLOT_F4;
       float v[4];
-#define LBCH_PULL(I)                                                              \
-  load_fstar<ST, VEC, I>(a, cy(I) == 1 ? ro_m : (cy(I) == -1 ? ro_p : ro_0), cl, v); \
-  slot[(I) * 32] = make_float4(v[0], v[1], v[2], v[3]);                            \
+#define LBCH_PULL(I)                    \
+  read_row<ST, VEC, I>(slot, lane, v); \
   ph[0] += v[0]; ph[1] += v[1]; ph[2] += v[2]; ph[3] += v[3];
       LBCH_PULL(0) LBCH_PULL(1) LBCH_PULL(2) LBCH_PULL(3) LBCH_PULL(4)
       LBCH_PULL(5) LBCH_PULL(6) LBCH_PULL(7) LBCH_PULL(8)
@@ -419,17 +468,23 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, 3) step_kernel(const __grid_c
     }
     // 6. Collide row r-3 and store it.
     if (it >= 6) {
-      const float4* rs = ring + ((it + 1) & (RING - 1)) * (9 * 32);
-      float4 fr[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) fr[i] = rs[i * 32];
+      const float4* slot = slots + s_col * SLOT_F4;
+      float fr[9][4];
+      read_row<ST, VEC, 0>(slot, lane, fr[0]);
+      read_row<ST, VEC, 1>(slot, lane, fr[1]);
+      read_row<ST, VEC, 2>(slot, lane, fr[2]);
+      read_row<ST, VEC, 3>(slot, lane, fr[3]);
+      read_row<ST, VEC, 4>(slot, lane, fr[4]);
+      read_row<ST, VEC, 5>(slot, lane, fr[5]);
+      read_row<ST, VEC, 6>(slot, lane, fr[6]);
+      read_row<ST, VEC, 7>(slot, lane, fr[7]);
+      read_row<ST, VEC, 8>(slot, lane, fr[8]);
       float o[9][4], phic[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         float f[9], oj[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-          f[i] = j == 0 ? fr[i].x : (j == 1 ? fr[i].y : (j == 2 ? fr[i].z : fr[i].w));
+        for (int i = 0; i < 9; ++i) f[i] = fr[i][j];
         collide(a, f, mu2[j], gx[j], gy[j], oj, phic[j]);
 #pragma unroll
         for (int i = 0; i < 9; ++i) o[i][j] = oj[i];
@@ -448,10 +503,11 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, 3) step_kernel(const __grid_c
       mu2[j] = mu1[j];
       mu1[j] = mun[j];
     }
-    rm = r0;
-    r0 = rp;
-    rp = rp + 1 == a.ny ? 0 : rp + 1;
+    s_cur = s_cur + 1 == SLOTS ? 0 : s_cur + 1;
+    s_pf = s_pf + 1 == SLOTS ? 0 : s_pf + 1;
+    s_col = s_col + 1 == SLOTS ? 0 : s_col + 1;
   }
+  cp_async_wait<0>();
 }
 
 }  // namespace lbch
