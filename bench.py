@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--storage", choices=["f32", "bf16_dev", "f16_dev"], default="f32",
+                    help="population storage of the main timed line")
     return ap.parse_args()
 
 
@@ -311,9 +313,11 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    storages = {"f32": lbch.STORE_F32, "bf16_dev": lbch.STORE_BF16_DEV, "f16_dev": lbch.STORE_F16_DEV}
+    main_st = storages[args.storage]
     barrier()
     with ClockSampler(gpu_id) as clk:
-        r32 = time_storage(lbch, torch, phi0, n, lbch.STORE_F32, args.steps, args.warmup)
+        r32 = time_storage(lbch, torch, phi0, n, main_st, args.steps, args.warmup)
     barrier()
     total = max_over_ranks(dist, r32["total_s"])
     per_launch = max_over_ranks(dist, r32["kernel_s_per_launch"])
@@ -321,17 +325,19 @@ def main():
     value = job_rate(world, lu_per_rank, total) / 1e6
 
     peak, peak_kind = measured_peaks()
-    bpl = lbch.ALGORITHMIC_BYTES_PER_LU[lbch.STORE_F32]
+    bpl = lbch.ALGORITHMIC_BYTES_PER_LU[main_st]
     achieved = bpl * n * n / per_launch / 1e9
-    traffic = profiled_traffic("f32")
+    traffic = profiled_traffic(args.storage)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None if traffic is None else traffic * n * n,
-                "peak_kind": peak_kind, "kernel": "lbch::step_kernel<F32, vec>",
+                "peak_kind": peak_kind, "kernel": f"lbch::step_kernel<{args.storage}, vec, fast rates>",
                 "algorithmic_bytes_per_launch": bpl * n * n, "launch_ms": per_launch * 1e3}
 
     variants = {}
     if not args.no_variants:
-        for name, st in (("bf16_dev", lbch.STORE_BF16_DEV), ("f16_dev", lbch.STORE_F16_DEV)):
+        for name, st in storages.items():
+            if st == main_st:
+                continue
             r = time_storage(lbch, torch, phi0, n, st, args.steps, args.warmup)
             pl = max_over_ranks(dist, r["kernel_s_per_launch"])
             b = lbch.ALGORITHMIC_BYTES_PER_LU[st]
@@ -362,7 +368,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD if n == N else f"spinodal-{n}x{n}", "nx": n, "ny": n, "alpha": ALPHA,
-                       "noise": NOISE, "seed": SEED, "storage": "f32", "lattice_steps_per_step": INNER,
+                       "noise": NOISE, "seed": SEED, "storage": args.storage, "lattice_steps_per_step": INNER,
                        "diagnostics_per_step": ["mass", "free_energy"],
                        "l2": "inputs larger than L2 (2.4 GB per population buffer), no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

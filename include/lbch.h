@@ -60,8 +60,9 @@ typedef enum {
 /* How the populations are stored between steps; arithmetic is FP32 in all cases. */
 typedef enum {
   LBCH_STORE_F32 = 0,       /* 9 FP32 planes: 72 bytes read+written per node update */
-  LBCH_STORE_BF16_DEV = 1,  /* FP32 rest population and mu_alpha anchor, plus the 8 moving
-                               populations as BF16 deviations from omega_i mu_alpha: 48 bytes */
+  LBCH_STORE_BF16_DEV = 1,  /* FP32 rest population and mu_alpha anchor per node, plus the 8
+                               moving populations as BF16 deviations from omega_i times the
+                               anchor of the node they stream to: 48 bytes */
   LBCH_STORE_F16_DEV = 2    /* as above with FP16 deviations scaled by 2^12: 48 bytes */
 } lbch_storage;
 

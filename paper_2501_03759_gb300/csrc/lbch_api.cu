@@ -39,6 +39,7 @@ struct lbch_ctx {
   // Launch shapes.
   StepArgs sa;
   bool vec;
+  bool fast;  // s_1 = s_2 = s_4 = s_6 = s_7 = s_8 = 1: reduced collision
   int step_blocks;
   int aux_blocks;
   bool failed;
@@ -110,28 +111,41 @@ lbch_status precheck(lbch_ctx* c, bool need_state) {
 
 Grid grid_of(const lbch_ctx* c) { return Grid{c->p.nx, c->p.ny, c->ps}; }
 
+// The step kernel instantiation for a context: storage, 16-byte rows (nx % 4 == 0), and
+// whether the relaxation rates allow the reduced collision.
+template <int ST>
+const void* step_entry(bool vec, bool fast) {
+  if (vec) return fast ? (const void*)step_kernel<ST, true, true> : (const void*)step_kernel<ST, true, false>;
+  return fast ? (const void*)step_kernel<ST, false, true> : (const void*)step_kernel<ST, false, false>;
+}
+
 template <int ST>
 void launch_step(lbch_ctx* c, const StepArgs& a) {
-  if (c->vec)
-    step_kernel<ST, true><<<c->step_blocks, STEP_WARPS * 32, STEP_SMEM, c->stream>>>(a);
-  else
-    step_kernel<ST, false><<<c->step_blocks, STEP_WARPS * 32, STEP_SMEM, c->stream>>>(a);
+  const dim3 g(c->step_blocks), b(STEP_WARPS * 32);
+  if (c->vec) {
+    if (c->fast)
+      step_kernel<ST, true, true><<<g, b, step_smem<ST, true>(), c->stream>>>(a);
+    else
+      step_kernel<ST, true, false><<<g, b, step_smem<ST, true>(), c->stream>>>(a);
+  } else {
+    if (c->fast)
+      step_kernel<ST, false, true><<<g, b, step_smem<ST, false>(), c->stream>>>(a);
+    else
+      step_kernel<ST, false, false><<<g, b, step_smem<ST, false>(), c->stream>>>(a);
+  }
 }
 
 template <int ST>
-cudaError_t configure_step_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(step_kernel<ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, STEP_SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(step_kernel<ST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, STEP_SMEM);
+cudaError_t configure_step_kernel(bool vec, bool fast) {
+  return cudaFuncSetAttribute(step_entry<ST>(vec, fast), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              vec ? step_smem<ST, true>() : step_smem<ST, false>());
 }
 
 template <int ST>
-int step_occupancy(bool vec) {
+int step_occupancy(bool vec, bool fast) {
   int nb = 0;
-  if (vec)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<ST, true>, STEP_WARPS * 32, STEP_SMEM);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_kernel<ST, false>, STEP_WARPS * 32, STEP_SMEM);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, step_entry<ST>(vec, fast), STEP_WARPS * 32,
+                                                vec ? step_smem<ST, true>() : step_smem<ST, false>());
   return nb;
 }
 
@@ -177,13 +191,24 @@ void launch_init(lbch_ctx* c, Buf b) {
 }
 
 template <int ST>
-void launch_phi(lbch_ctx* c, double* phi_d, float* phi_f, double* partial) {
-  phi_kernel<ST><<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->buf[c->cur], grid_of(c), phi_d, phi_f, partial);
+void launch_phi(lbch_ctx* c, double* phi_d, float* phi_f) {
+  phi_kernel<ST><<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->buf[c->cur], grid_of(c), phi_d, phi_f);
+}
+
+template <int ST>
+void launch_mass(lbch_ctx* c, double* partial) {
+  mass_kernel<ST><<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->buf[c->cur], grid_of(c), partial);
 }
 
 template <int ST>
 void launch_get_plane(lbch_ctx* c, int i) {
   get_plane_kernel<ST><<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->buf[c->cur], grid_of(c), i, c->stage0);
+}
+
+template <int ST>
+void launch_close_rest(lbch_ctx* c) {
+  if constexpr (ST != ST_F32)
+    close_rest_kernel<ST><<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->stage1, c->buf[c->cur], grid_of(c));
 }
 
 template <int ST>
@@ -268,11 +293,14 @@ lbch_status lbch_create(const lbch_params* p, void* d_workspace, size_t bytes, v
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  c->vec = (p->nx % 4) == 0;
+  c->fast = c->s[1] == 1.0 && c->s[2] == 1.0 && c->s[4] == 1.0 && c->s[6] == 1.0 && c->s[7] == 1.0 &&
+            c->s[8] == 1.0;
   if (e == cudaSuccess) {
     switch (p->storage) {
-      case LBCH_STORE_F32: e = configure_step_kernels<ST_F32>(); break;
-      case LBCH_STORE_BF16_DEV: e = configure_step_kernels<ST_BF16>(); break;
-      default: e = configure_step_kernels<ST_F16>(); break;
+      case LBCH_STORE_F32: e = configure_step_kernel<ST_F32>(c->vec, c->fast); break;
+      case LBCH_STORE_BF16_DEV: e = configure_step_kernel<ST_BF16>(c->vec, c->fast); break;
+      default: e = configure_step_kernel<ST_F16>(c->vec, c->fast); break;
     }
   }
   if (e != cudaSuccess) {
@@ -280,12 +308,11 @@ lbch_status lbch_create(const lbch_params* p, void* d_workspace, size_t bytes, v
     return LBCH_ECUDA;
   }
   c->device = dev;
-  c->vec = (p->nx % 4) == 0;
   int per_sm = 0;
   switch (p->storage) {
-    case LBCH_STORE_F32: per_sm = step_occupancy<ST_F32>(c->vec); break;
-    case LBCH_STORE_BF16_DEV: per_sm = step_occupancy<ST_BF16>(c->vec); break;
-    default: per_sm = step_occupancy<ST_F16>(c->vec); break;
+    case LBCH_STORE_F32: per_sm = step_occupancy<ST_F32>(c->vec, c->fast); break;
+    case LBCH_STORE_BF16_DEV: per_sm = step_occupancy<ST_BF16>(c->vec, c->fast); break;
+    default: per_sm = step_occupancy<ST_F16>(c->vec, c->fast); break;
   }
   if (per_sm < 1) {
     delete c;
@@ -364,7 +391,7 @@ lbch_status lbch_mass(lbch_ctx* c, double* out) {
   lbch_status st = precheck(c, true);
   if (st != LBCH_OK) return st;
   if (!out) return LBCH_EINVAL;
-  DISPATCH(c->p.storage, launch_phi, c, nullptr, nullptr, c->partial);
+  DISPATCH(c->p.storage, launch_mass, c, c->partial);
   final_sum_kernel<<<1, 1024, 0, c->stream>>>(c->partial, c->aux_blocks, c->result);
   if ((st = finish(c, "mass: launch")) != LBCH_OK) return st;
   double v = 0.0;
@@ -384,7 +411,7 @@ lbch_status lbch_free_energy(lbch_ctx* c, double* out) {
   if (st != LBCH_OK) return st;
   if (!out) return LBCH_EINVAL;
   float* phi_f = reinterpret_cast<float*>(c->stage1);
-  DISPATCH(c->p.storage, launch_phi, c, nullptr, phi_f, nullptr);
+  DISPATCH(c->p.storage, launch_phi, c, nullptr, phi_f);
   EnergyConsts ec;
   const double eps = c->p.regularization == LBCH_REG_NONE ? 0.0 : c->p.eps;
   ec.k = (float)c->k;
@@ -414,7 +441,7 @@ lbch_status lbch_get_field(lbch_ctx* c, double* h_phi) {
   if (st != LBCH_OK) return st;
   if (!h_phi) return LBCH_EINVAL;
   const size_t n = (size_t)c->p.nx * c->p.ny;
-  DISPATCH(c->p.storage, launch_phi, c, c->stage0, nullptr, nullptr);
+  DISPATCH(c->p.storage, launch_phi, c, c->stage0, nullptr);
   if ((st = finish(c, "get_field: launch")) != LBCH_OK) return st;
   if (cuda_failed(c, cudaMemcpyAsync(h_phi, c->stage0, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                   "get_field: copy"))
@@ -471,13 +498,14 @@ lbch_status lbch_set_state(lbch_ctx* c, const double* h_f9) {
     mu_alpha_kernel<<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->stage1, c->stage0, g, c->k, 4.0 * c->beta,
                                                                   c->flags);
     anchor_kernel<<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->stage0, c->buf[0], g);
-    for (int i = 0; i < 9; ++i) {
+    for (int i = 1; i < 9; ++i) {
       if (cuda_failed(c, cudaMemcpyAsync(c->stage0, h_f9 + i * n, n * sizeof(double), cudaMemcpyHostToDevice,
                                          c->stream),
                       "set_state: copy"))
         return LBCH_ECUDA;
       DISPATCH(c->p.storage, launch_set_dev, c, i);
     }
+    DISPATCH(c->p.storage, launch_close_rest, c);  // rest = phi - rebuilt moving populations
   }
   if ((st = finish(c, "set_state: launch")) != LBCH_OK) return st;
   int bad = 0;

@@ -32,7 +32,9 @@ __device__ __forceinline__ double pulled(const Buf& b, const Grid& g, int i, int
     return (double)b.f32[(long long)i * g.ps + s];
   } else {
     if (i == 0) return (double)b.f32[s];
-    return (double)fmaf((float)wgt(i), b.f32[g.ps + s], Dev<ST>::load(b.dev[(long long)(i - 1) * g.ps + s]));
+    // w_i times this node's anchor plus the deviation stored at the source node.
+    const long long own = (long long)y * g.nx + x;
+    return (double)fmaf((float)wgt(i), b.f32[g.ps + own], Dev<ST>::load(b.dev[(long long)(i - 1) * g.ps + s]));
   }
 }
 
@@ -70,15 +72,12 @@ __global__ void init_state_kernel(const double* __restrict__ phi0, const double*
       for (int i = 1; i < 9; ++i)  // f*_i(y) must stream to f_i(y + c_i) = w_i mu_alpha(y + c_i)
         b.f32[(long long)i * g.ps + id] = (float)(wgt(i) * mua[wrapped(g, x + cx(i), y + cy(i))]);
     } else {
+      // A reader at y + c_i rebuilds w_i anchor(y + c_i) + d_i(y) = w_i mu_alpha(y + c_i),
+      // exactly f^eq_i there, with every deviation zero.
       b.f32[id] = (float)rest;
       b.f32[g.ps + id] = (float)m;
-      const float mf = (float)m;
 #pragma unroll
-      for (int i = 1; i < 9; ++i) {
-        // Reader rebuilds w_i anchor(y) + d_i(y); it must give w_i mu_alpha(y + c_i).
-        const float want = (float)(wgt(i) * mua[wrapped(g, x + cx(i), y + cy(i))]);
-        b.dev[(long long)(i - 1) * g.ps + id] = Dev<ST>::store(want - (float)wgt(i) * mf);
-      }
+      for (int i = 1; i < 9; ++i) b.dev[(long long)(i - 1) * g.ps + id] = Dev<ST>::store(0.0f);
     }
   }
 }
@@ -117,8 +116,9 @@ __global__ void accumulate_kernel(const double* __restrict__ in, double* __restr
   }
 }
 
-// Deviation storage from one canonical plane: rest population as is; moving
-// populations as deviations from w_i times the anchor already in plane 1.
+// Deviation storage from one canonical plane: rest population as is; a moving
+// population as its deviation from w_i times the anchor (plane 1, already set) of
+// the node it streams to.
 template <int ST>
 __global__ void set_plane_dev_kernel(const double* __restrict__ in, Buf b, Grid g, int i) {
   const long long n = (long long)g.nx * g.ny;
@@ -128,9 +128,26 @@ __global__ void set_plane_dev_kernel(const double* __restrict__ in, Buf b, Grid 
     if (i == 0) {
       b.f32[id] = (float)in[id];
     } else {
-      const float want = (float)in[wrapped(g, x + cx(i), y + cy(i))];
-      b.dev[(long long)(i - 1) * g.ps + id] = Dev<ST>::store(want - (float)wgt(i) * b.f32[g.ps + id]);
+      const long long dst = wrapped(g, x + cx(i), y + cy(i));
+      const float want = (float)in[dst];
+      b.dev[(long long)(i - 1) * g.ps + id] = Dev<ST>::store(want - (float)wgt(i) * b.f32[g.ps + dst]);
     }
+  }
+}
+
+// Deviation storage, last pass of a state transfer: the rest population takes phi
+// minus the moving populations as a reader rebuilds them, so the 16-bit rounding of
+// the deviations does not change the mass (sum_i f_i(y) = phi(y) to FP32 rounding).
+template <int ST>
+__global__ void close_rest_kernel(const double* __restrict__ phi, Buf b, Grid g) {
+  const long long n = (long long)g.nx * g.ny;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(id % g.nx), y = (int)(id / g.nx);
+    float moving = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) moving += (float)pulled<ST>(b, g, i, x, y);
+    b.f32[id] = (float)(phi[id] - (double)moving);
   }
 }
 
@@ -157,26 +174,80 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return v;  // valid in thread 0
 }
 
-// phi = sum_i f_i (Eq. 22) per node, summed in FP64; optionally written out as FP64
-// (phi_d) or FP32 (phi_f); block partial sums of phi go to partial[blockIdx.x].
+// phi = sum_i f_i (Eq. 22) per node into phi (FP64, for host transfer) or phi_f (FP32,
+// for the energy). Rows are spread over blocks and columns over threads.
 template <int ST>
-__global__ void phi_kernel(Buf b, Grid g, double* __restrict__ phi_d, float* __restrict__ phi_f,
-                           double* __restrict__ partial) {
+__global__ void phi_kernel(Buf b, Grid g, double* __restrict__ phi_d, float* __restrict__ phi_f) {
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      const long long id = (long long)y * g.nx + x;
+      if (phi_d) {
+        double p = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) p += pulled<ST>(b, g, i, x, y);
+        phi_d[id] = p;
+      } else {
+        float p = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) p += (float)pulled<ST>(b, g, i, x, y);
+        phi_f[id] = p;
+      }
+    }
+}
+
+// Compensated (Kahan) FP32 sum: the error stays at FP32 rounding of the total.
+struct KahanF32 {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Total mass sum_x phi(x). Streaming only permutes populations, so this is the sum of
+// every stored population, no pull needed: 9 FP32 planes, or for 16-bit deviations
+// sum_x [f*_0 + (1 - w_0) anchor + sum_i d_i] (w_i anchor(x) summed over i >= 1).
+// Per-thread compensated FP32 sums, FP64 block sums to partial[blockIdx.x].
+template <int ST>
+__global__ void mass_kernel(Buf b, Grid g, double* __restrict__ partial) {
   __shared__ double sh[AUX_THREADS / 32];
   const long long n = (long long)g.nx * g.ny;
-  double acc = 0.0;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(id % g.nx), y = (int)(id / g.nx);
-    double p = 0.0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) p += pulled<ST>(b, g, i, x, y);
-    if (phi_d) phi_d[id] = p;
-    if (phi_f) phi_f[id] = (float)p;
-    acc += p;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n4 = n / 4;  // float4 / 4-value chunks per plane (planes are 256-byte aligned)
+  KahanF32 main, anchor;
+  auto add_f32_plane = [&](const float* p, KahanF32& k) {
+    const float4* p4 = reinterpret_cast<const float4*>(p);
+    for (long long q = t0; q < n4; q += stride) {
+      const float4 v = __ldg(p4 + q);
+      k.add(v.x); k.add(v.y); k.add(v.z); k.add(v.w);
+    }
+    for (long long q = 4 * n4 + t0; q < n; q += stride) k.add(__ldg(p + q));
+  };
+  if constexpr (ST == ST_F32) {
+    for (int i = 0; i < 9; ++i) add_f32_plane(b.f32 + (long long)i * g.ps, main);
+  } else {
+    add_f32_plane(b.f32, main);
+    add_f32_plane(b.f32 + g.ps, anchor);
+    for (int i = 0; i < 8; ++i) {
+      const uint16_t* d = b.dev + (long long)i * g.ps;
+      const uint2* d4 = reinterpret_cast<const uint2*>(d);
+      for (long long q = t0; q < n4; q += stride) {
+        const uint2 v = __ldg(d4 + q);
+        main.add(Dev<ST>::load(static_cast<uint16_t>(v.x & 0xffffu)));
+        main.add(Dev<ST>::load(static_cast<uint16_t>(v.x >> 16)));
+        main.add(Dev<ST>::load(static_cast<uint16_t>(v.y & 0xffffu)));
+        main.add(Dev<ST>::load(static_cast<uint16_t>(v.y >> 16)));
+      }
+      for (long long q = 4 * n4 + t0; q < n; q += stride) main.add(Dev<ST>::load(__ldg(d + q)));
+    }
   }
+  double acc = main.value() + (1.0 - wgt(0)) * anchor.value();
   acc = block_sum(acc, sh);
-  if (threadIdx.x == 0 && partial) partial[blockIdx.x] = acc;
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
 struct EnergyConsts {
@@ -188,34 +259,35 @@ struct EnergyConsts {
 __global__ void energy_kernel(const float* __restrict__ phi, Grid g, EnergyConsts c,
                               double* __restrict__ partial) {
   __shared__ double sh[AUX_THREADS / 32];
-  const long long n = (long long)g.nx * g.ny;
   double acc = 0.0;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(id % g.nx), y = (int)(id / g.nx);
-    const float p0 = phi[id];
-    float gx = 0.0f, gy = 0.0f, lap = 0.0f;
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-      const float v = phi[wrapped(g, x + cx(i), y + cy(i))];
-      const float w3 = 3.0f * (float)wgt(i);
-      gx = fmaf(w3 * cx(i), v, gx);
-      gy = fmaf(w3 * cy(i), v, gy);
-      lap = fmaf(2.0f * w3, v - p0, lap);
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
+    const long long rm = (long long)(y == 0 ? g.ny - 1 : y - 1) * g.nx;
+    const long long r0 = (long long)y * g.nx;
+    const long long rp = (long long)(y + 1 == g.ny ? 0 : y + 1) * g.nx;
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 1 == g.nx ? 0 : x + 1;
+      const float p0 = phi[r0 + x];
+      const float E = phi[r0 + xp], Wv = phi[r0 + xm], N = phi[rp + x], S = phi[rm + x];
+      const float NE = phi[rp + xp], NW = phi[rp + xm], SW = phi[rm + xm], SE = phi[rm + xp];
+      // Eq. 26a, 26b with the D2Q9 weights.
+      const float gx = (E - Wv) * (1.0f / 3.0f) + ((NE - NW) + (SE - SW)) * (1.0f / 12.0f);
+      const float gy = (N - S) * (1.0f / 3.0f) + ((NE - SE) + (NW - SW)) * (1.0f / 12.0f);
+      const float lap = ((E + Wv) + (N + S)) * (2.0f / 3.0f) + ((NE + NW) + (SE + SW)) * (1.0f / 6.0f) -
+                        p0 * (10.0f / 3.0f);
+      const float g2 = fmaf(gx, gx, gy * gy);
+      float gamma = 1.0f;
+      if (g2 >= 1e-24f) {
+        const float rs = rsqrtf(g2);
+        const float n1 = gx * rs, n2 = gy * rs;
+        const float n1s = n1 * n1, n2s = n2 * n2;
+        gamma = fmaf(c.alpha, fmaf(4.0f, fmaf(n1s, n1s, n2s * n2s), -3.0f), 1.0f);
+      }
+      const float q = p0 * p0 - 1.0f;
+      const float F = c.beta * q * q;                        // Eq. 4
+      const float wv = fmaf(-c.cw, c.beta4 * p0 * q, lap);   // lap phi - f (Willmore) or lap phi
+      const float e = fmaf(gamma, fmaf(0.5f * c.k, g2, F), c.half_eps * wv * wv);
+      acc += (double)e;
     }
-    const float g2 = fmaf(gx, gx, gy * gy);
-    float gamma = 1.0f;
-    if (g2 >= 1e-24f) {
-      const float rs = rsqrtf(g2);
-      const float n1 = gx * rs, n2 = gy * rs;
-      const float n1s = n1 * n1, n2s = n2 * n2;
-      gamma = fmaf(c.alpha, fmaf(4.0f, fmaf(n1s, n1s, n2s * n2s), -3.0f), 1.0f);
-    }
-    const float q = p0 * p0 - 1.0f;
-    const float F = c.beta * q * q;              // Eq. 4
-    const float wv = fmaf(-c.cw, c.beta4 * p0 * q, lap);  // lap phi - f (Willmore) or lap phi
-    const float e = fmaf(gamma, fmaf(0.5f * c.k, g2, F), c.half_eps * wv * wv);
-    acc += (double)e;
   }
   acc = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;

@@ -55,8 +55,10 @@ struct Dev<ST_F16> {
 // Device view of one population buffer.
 //   F32:  plane i (0..8) at f32 + i*ps.
 //   DEV:  f32 + 0*ps holds the post-collision rest population f*_0, f32 + 1*ps holds the
-//         anchor mu_alpha of the node where the collision happened; plane i (1..8) of
-//         16-bit deviations d_i = f*_i - w_i mu_alpha sits at dev + (i-1)*ps.
+//         anchor mu_alpha of each node; plane i (1..8) of 16-bit deviations
+//         d_i(x) = f*_i(x) - w_i mu_alpha(x + c_i), relative to the anchor of the node the
+//         population streams to, sits at dev + (i-1)*ps. A reader at y rebuilds
+//         f*_i(y - c_i) = w_i anchor(y) + d_i(y - c_i) from its own anchor.
 struct Buf {
   float* f32;
   uint16_t* dev;

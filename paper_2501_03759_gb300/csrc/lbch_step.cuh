@@ -33,11 +33,24 @@ constexpr int STRIP_W = 128;                 // columns per warp strip
 constexpr int HALO_W = 4;                    // halo columns on each side
 constexpr int OUT_W = STRIP_W - 2 * HALO_W;  // output columns per strip
 constexpr int STEP_WARPS = 4;                // warps per CTA
-constexpr int STEP_MIN_CTAS = 2;             // CTAs per SM the launch bounds plan for
-constexpr int PF_DIST = 1;                   // rows fetched ahead of the phi row
-constexpr int SLOTS = PF_DIST + 4;           // rows held per warp: r-3 (collision) .. r+PF_DIST
-constexpr int SLOT_F4 = 9 * 32;              // 16-byte units per slot (9 per lane)
-constexpr int STEP_SMEM = STEP_WARPS * SLOTS * SLOT_F4 * 16;
+// Pipeline depth per storage (measured on GB300 at 8192^2). FP32 rows are bandwidth
+// bound: fetch one row ahead and collide row r-3 right after its grad mu_beta. The
+// 16-bit storages are latency bound: collide row r-4 first thing in the iteration, so
+// that work covers the wait for row r, fetch no further ahead, and keep 12 warps per SM
+// (their landing slots are smaller).
+template <int ST, bool VEC>
+struct Pipe {
+  static constexpr bool DEV16 = ST != ST_F32;
+  static constexpr int PF_DIST = DEV16 ? 0 : 1;         // rows fetched ahead of the phi row
+  static constexpr int LAG = DEV16 ? 4 : 3;             // phi row r collides row r - LAG
+  static constexpr int SLOTS = PF_DIST + 1 + LAG;       // rows held per warp: r-LAG .. r+PF_DIST
+  // 16-byte units per slot: 9 per lane for FP32 planes (or pulled values on the scalar
+  // path); rest + anchor + 8 half-width deviation planes = 6 per lane for vector DEV.
+  static constexpr int SLOT_F4 = (DEV16 && VEC ? 6 : 9) * 32;
+  static constexpr int MIN_CTAS = DEV16 && VEC ? 3 : 2;  // CTAs per SM the launch bounds plan for
+};
+template <int ST, bool VEC>
+constexpr int step_smem() { return STEP_WARPS * Pipe<ST, VEC>::SLOTS * Pipe<ST, VEC>::SLOT_F4 * 16; }
 
 struct StepArgs {
   Buf src, dst;
@@ -100,8 +113,8 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // One warp's landing slot for one phi row r, as 16-byte units [q][lane]:
 //   vector F32:  q = i holds plane i of row r - c_iy at the strip's aligned columns (raw f*);
-//   vector DEV:  q = 0 the rest plane of row r, q = 1..3 the anchor plane of rows r-1, r, r+1,
-//                then (as 8-byte units [k][lane]) the deviation plane k+1 of row r - c_(k+1)y;
+//   vector DEV:  q = 0 the rest plane of row r, q = 1 the anchor plane of row r, then (as
+//                8-byte units [k][lane]) the deviation plane k+1 of row r - c_(k+1)y;
 //   scalar path: q = i holds f_in,i itself (pulled and rebuilt when it was fetched).
 // Fetches phi row r (rows ro_m = r-1, ro_0 = r, ro_p = r+1) into a slot; the vector path
 // copies asynchronously (cp.async), the scalar path loads and stores synchronously.
@@ -116,10 +129,8 @@ __device__ __forceinline__ void issue_row(const StepArgs& a, float4* slot, int l
         cp_async16(slot + i * 32 + lane, a.src.f32 + (long long)i * a.ps + LBCH_RO(i) + cl.c0);
     } else {
       cp_async16(slot + lane, a.src.f32 + ro_0 + cl.c0);
-      cp_async16(slot + 32 + lane, a.src.f32 + a.ps + ro_m + cl.c0);
-      cp_async16(slot + 64 + lane, a.src.f32 + a.ps + ro_0 + cl.c0);
-      cp_async16(slot + 96 + lane, a.src.f32 + a.ps + ro_p + cl.c0);
-      uint2* ds = reinterpret_cast<uint2*>(slot + 128);
+      cp_async16(slot + 32 + lane, a.src.f32 + a.ps + ro_0 + cl.c0);
+      uint2* ds = reinterpret_cast<uint2*>(slot + 64);
 #pragma unroll
       for (int i = 1; i < 9; ++i)
         cp_async8(ds + (i - 1) * 32 + lane, a.src.dev + (long long)(i - 1) * a.ps + LBCH_RO(i) + cl.c0);
@@ -136,8 +147,8 @@ __device__ __forceinline__ void issue_row(const StepArgs& a, float4* slot, int l
           v[j] = __ldg(a.src.f32 + (long long)i * a.ps + ro + c);
         } else if (i == 0) {
           v[j] = __ldg(a.src.f32 + ro + c);
-        } else {
-          v[j] = fmaf((float)wgt(i), __ldg(a.src.f32 + a.ps + ro + c),
+        } else {  // w_i times the anchor of this node, plus the deviation from the source node
+          v[j] = fmaf((float)wgt(i), __ldg(a.src.f32 + a.ps + ro_0 + cl.cs[j + 1]),
                       Dev<ST>::load(__ldg(a.src.dev + (long long)(i - 1) * a.ps + ro + c)));
         }
       }
@@ -150,18 +161,16 @@ __device__ __forceinline__ void issue_row(const StepArgs& a, float4* slot, int l
 // f_in,I at this lane's 4 columns from a landed slot.
 template <int ST, bool VEC, int I>
 __device__ __forceinline__ void read_row(const float4* slot, int lane, float (&v)[4]) {
-  if constexpr (!VEC || ST == ST_F32 || I == 0) {
+  constexpr bool REBUILD = VEC && ST != ST_F32 && I != 0;
+  if constexpr (!REBUILD) {
     const float4 t = slot[I * 32 + lane];
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-  } else {
-    // Rebuild f*_I = w_I anchor + deviation at the source node (row r - c_Iy).
-    const float w = (float)wgt(I);
-    const float4 m = slot[(2 - cy(I)) * 32 + lane];
-    const uint2 raw = reinterpret_cast<const uint2*>(slot + 128)[(I - 1) * 32 + lane];
-    v[0] = fmaf(w, m.x, Dev<ST>::load(static_cast<uint16_t>(raw.x & 0xffffu)));
-    v[1] = fmaf(w, m.y, Dev<ST>::load(static_cast<uint16_t>(raw.x >> 16)));
-    v[2] = fmaf(w, m.z, Dev<ST>::load(static_cast<uint16_t>(raw.y & 0xffffu)));
-    v[3] = fmaf(w, m.w, Dev<ST>::load(static_cast<uint16_t>(raw.y >> 16)));
+  } else {  // deviations of the source nodes (row r - c_Iy), shifted below
+    const uint2 raw = reinterpret_cast<const uint2*>(slot + 64)[(I - 1) * 32 + lane];
+    v[0] = Dev<ST>::load(static_cast<uint16_t>(raw.x & 0xffffu));
+    v[1] = Dev<ST>::load(static_cast<uint16_t>(raw.x >> 16));
+    v[2] = Dev<ST>::load(static_cast<uint16_t>(raw.y & 0xffffu));
+    v[3] = Dev<ST>::load(static_cast<uint16_t>(raw.y >> 16));
   }
   if constexpr (VEC) {  // the pull shift along x happens here, one shuffle per plane
     if constexpr (cx(I) == 1) {  // take the column to the left
@@ -171,6 +180,14 @@ __device__ __forceinline__ void read_row(const float4* slot, int lane, float (&v
       const float next = __shfl_down_sync(FULL, v[0], 1);
       v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
     }
+  }
+  if constexpr (REBUILD) {  // f*_I(y - c_I) = w_I anchor(y) + d_I(y - c_I)
+    const float w = (float)wgt(I);
+    const float4 m = slot[32 + lane];
+    v[0] = fmaf(w, m.x, v[0]);
+    v[1] = fmaf(w, m.y, v[1]);
+    v[2] = fmaf(w, m.z, v[2]);
+    v[3] = fmaf(w, m.w, v[3]);
   }
 }
 
@@ -202,6 +219,10 @@ __device__ __forceinline__ void pointwise(const StepArgs& a, float phi, float dx
 // Eq. 17 at one node in moment space (Eqs. 23, 25) with the closed forms
 // m^eq = (phi, -4 phi + 2 mu_a, 4 phi - 3 mu_a, 0, ...) and
 // M F = (0, 0, 0, -g_x/3, g_x/3, -g_y/3, g_y/3, 0, 0), and M^-1 = M^T diag(1/|row|^2).
+// FAST: s_1 = s_2 = s_4 = s_6 = s_7 = s_8 = 1, so those moments take their (forced)
+// equilibrium and need not be formed; the result equals the general path's, whose
+// (1 - s_k) m_k terms are then exactly zero.
+template <bool FAST>
 __device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], float mua,
                                         float gx, float gy, float (&o)[9], float& phi_out) {
   const float ab = f[1] + f[3], bb = f[2] + f[4];
@@ -212,19 +233,30 @@ __device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], 
   const float x1 = f[1] - f[3], y1 = f[2] - f[4];
   const float p = f[5] - f[7], q = f[6] - f[8];
   const float pm = p - q, pp = p + q;
-  const float m1 = fmaf(-4.0f, f[0], fmaf(2.0f, Sd, -Sa));
-  const float m2 = fmaf(4.0f, f[0], fmaf(-2.0f, Sa, Sd));
-  const float m3 = x1 + pm, m4 = fmaf(-2.0f, x1, pm);
-  const float m5 = y1 + pp, m6 = fmaf(-2.0f, y1, pp);
-  const float m7 = ab - bb, m8 = e - h;
+  const float m3 = x1 + pm, m5 = y1 + pp;
   const float n0 = phi * (1.0f / 9.0f);
-  const float n1 = fmaf(a.c1a, m1, a.c1b * fmaf(2.0f, mua, -4.0f * phi));
-  const float n2 = fmaf(a.c2a, m2, a.c2b * fmaf(-3.0f, mua, 4.0f * phi));
+  float n1, n2, n4, n6, n7, n8;
+  if constexpr (FAST) {
+    n1 = a.c1b * fmaf(2.0f, mua, -4.0f * phi);
+    n2 = a.c2b * fmaf(-3.0f, mua, 4.0f * phi);
+    n4 = a.c4g * gx;
+    n6 = a.c6g * gy;
+    n7 = 0.0f;
+    n8 = 0.0f;
+  } else {
+    const float m1 = fmaf(-4.0f, f[0], fmaf(2.0f, Sd, -Sa));
+    const float m2 = fmaf(4.0f, f[0], fmaf(-2.0f, Sa, Sd));
+    const float m4 = fmaf(-2.0f, x1, pm), m6 = fmaf(-2.0f, y1, pp);
+    const float m7 = ab - bb, m8 = e - h;
+    n1 = fmaf(a.c1a, m1, a.c1b * fmaf(2.0f, mua, -4.0f * phi));
+    n2 = fmaf(a.c2a, m2, a.c2b * fmaf(-3.0f, mua, 4.0f * phi));
+    n4 = fmaf(a.c4a, m4, a.c4g * gx);
+    n6 = fmaf(a.c6a, m6, a.c6g * gy);
+    n7 = a.c7 * m7;
+    n8 = a.c8 * m8;
+  }
   const float n3 = fmaf(a.c3a, m3, a.c3g * gx);
-  const float n4 = fmaf(a.c4a, m4, a.c4g * gx);
   const float n5 = fmaf(a.c5a, m5, a.c5g * gy);
-  const float n6 = fmaf(a.c6a, m6, a.c6g * gy);
-  const float n7 = a.c7 * m7, n8 = a.c8 * m8;
   const float A0 = fmaf(-2.0f, n2, n0 - n1);
   const float B = A0 + n7, C = A0 - n7;
   const float X = fmaf(-2.0f, n4, n3), Y = fmaf(-2.0f, n6, n5);
@@ -250,10 +282,15 @@ __device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], 
   phi_out = phi;
 }
 
+// Stores one collided row. DEV storage keeps the rest population and this node's
+// anchor in FP32 and d_i = f*_i - w_i anchor(x + c_i) in 16 bits; the rest population
+// is closed on the values a reader will rebuild, so sum_i f*_i = phi holds (mass is
+// conserved to FP32 rounding, not 16-bit rounding). dmu[i-1][j] is the anchor of the
+// node population i of column j streams to.
 template <int ST, bool VEC>
 __device__ __forceinline__ void store_row(const StepArgs& a, long long ro, long long col,
                                           const float (&o)[9][4], const float (&mua)[4],
-                                          const float (&phi)[4]) {
+                                          const float (&dmu)[8][4], const float (&phi)[4]) {
   if constexpr (ST == ST_F32) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -274,11 +311,11 @@ __device__ __forceinline__ void store_row(const StepArgs& a, long long ro, long 
       float sum = 0.0f;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
-        const float wm = (float)wgt(i) * mua[j];
-        d[i - 1][j] = D::store(o[i][j] - wm);
-        sum += fmaf((float)wgt(i), mua[j], D::load(d[i - 1][j]));  // f*_i as a reader rebuilds it
+        const float w = (float)wgt(i);
+        d[i - 1][j] = D::store(o[i][j] - w * dmu[i - 1][j]);
+        sum += fmaf(w, dmu[i - 1][j], D::load(d[i - 1][j]));  // f*_i as its reader rebuilds it
       }
-      rest[j] = phi[j] - sum;  // keeps sum_i f*_i = phi: mass conserved to FP32 rounding
+      rest[j] = phi[j] - sum;
     }
     float* p0 = a.dst.f32 + ro + col;
     float* pm = a.dst.f32 + a.ps + ro + col;
@@ -311,9 +348,9 @@ __device__ __forceinline__ void store_row(const StepArgs& a, long long ro, long 
 template <int ST>
 __device__ __forceinline__ void store_row_masked(const StepArgs& a, long long ro, int col0, int nvalid,
                                                  const float (&o)[9][4], const float (&mua)[4],
-                                                 const float (&phi)[4]) {
+                                                 const float (&dmu)[8][4], const float (&phi)[4]) {
   if (nvalid >= 4) {
-    store_row<ST, false>(a, ro, col0, o, mua, phi);
+    store_row<ST, false>(a, ro, col0, o, mua, dmu, phi);
     return;
   }
   // Fewer than 4 valid columns: write them one at a time.
@@ -327,8 +364,9 @@ __device__ __forceinline__ void store_row_masked(const StepArgs& a, long long ro
       float sum = 0.0f;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
-        const uint16_t d = D::store(o[i][j] - (float)wgt(i) * mua[j]);
-        sum += fmaf((float)wgt(i), mua[j], D::load(d));
+        const float w = (float)wgt(i);
+        const uint16_t d = D::store(o[i][j] - w * dmu[i - 1][j]);
+        sum += fmaf(w, dmu[i - 1][j], D::load(d));
         a.dst.dev[(long long)(i - 1) * a.ps + ro + col0 + j] = d;
       }
       a.dst.f32[ro + col0 + j] = phi[j] - sum;
@@ -337,8 +375,63 @@ __device__ __forceinline__ void store_row_masked(const StepArgs& a, long long ro
   }
 }
 
-template <int ST, bool VEC>
-__global__ void __launch_bounds__(STEP_WARPS * 32, STEP_MIN_CTAS)
+// Collides row `row` of this warp's strip from its landing slot and stores it.
+// mu_m, mu_c, mu_p: mu_alpha of rows row-1, row, row+1 at this lane's columns.
+template <int ST, bool VEC, bool FAST>
+__device__ __forceinline__ void collide_row(const StepArgs& a, const float4* slot, int lane, int row,
+                                            bool store, int ocol0, int nvalid, const float (&mu_m)[4],
+                                            const float (&mu_c)[4], const float (&mu_p)[4],
+                                            const float (&gx)[4], const float (&gy)[4]) {
+  float fr[9][4];
+  read_row<ST, VEC, 0>(slot, lane, fr[0]);
+  read_row<ST, VEC, 1>(slot, lane, fr[1]);
+  read_row<ST, VEC, 2>(slot, lane, fr[2]);
+  read_row<ST, VEC, 3>(slot, lane, fr[3]);
+  read_row<ST, VEC, 4>(slot, lane, fr[4]);
+  read_row<ST, VEC, 5>(slot, lane, fr[5]);
+  read_row<ST, VEC, 6>(slot, lane, fr[6]);
+  read_row<ST, VEC, 7>(slot, lane, fr[7]);
+  read_row<ST, VEC, 8>(slot, lane, fr[8]);
+  float o[9][4], phic[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float f[9], oj[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = fr[i][j];
+    collide<FAST>(a, f, mu_c[j], gx[j], gy[j], oj, phic[j]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[i][j] = oj[i];
+  }
+  float dmu[8][4];
+  if constexpr (ST != ST_F32) {  // anchors of the destination nodes x + c_i
+    float ext[3][6];             // rows row-1, row, row+1; columns -1 .. 4 of this lane
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float(&m)[4] = k == 0 ? mu_m : (k == 1 ? mu_c : mu_p);
+      ext[k][0] = __shfl_up_sync(FULL, m[3], 1);
+      ext[k][1] = m[0];
+      ext[k][2] = m[1];
+      ext[k][3] = m[2];
+      ext[k][4] = m[3];
+      ext[k][5] = __shfl_down_sync(FULL, m[0], 1);
+    }
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) dmu[i - 1][j] = ext[1 + cy(i)][j + cx(i) + 1];
+  }
+  if (store) {
+    const long long ro = (long long)row * a.nx;
+    if constexpr (VEC) {
+      store_row<ST, true>(a, ro, ocol0, o, mu_c, dmu, phic);
+    } else {
+      store_row_masked<ST>(a, ro, ocol0, nvalid, o, mu_c, dmu, phic);
+    }
+  }
+}
+
+template <int ST, bool VEC, bool FAST>
+__global__ void __launch_bounds__(STEP_WARPS * 32, (Pipe<ST, VEC>::MIN_CTAS))
     step_kernel(const __grid_constant__ StepArgs a) {
   extern __shared__ float4 smem_slots[];
   const int lane = threadIdx.x & 31;
@@ -350,6 +443,8 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, STEP_MIN_CTAS)
   const int y0 = seg * a.seg_len;
   const int y1 = min(y0 + a.seg_len, a.ny);
   const int xs = strip * OUT_W - HALO_W;  // strip start column (before wrap)
+  using PP = Pipe<ST, VEC>;
+  constexpr int PF_DIST = PP::PF_DIST, COLLIDE_LAG = PP::LAG, SLOTS = PP::SLOTS, SLOT_F4 = PP::SLOT_F4;
   float4* slots = smem_slots + wib * (SLOTS * SLOT_F4);  // this warp's landing slots
 
   Cols cl;
@@ -366,15 +461,18 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, STEP_MIN_CTAS)
   float Ax1[4], Ay1[4], Al1[4], Ax0[4], Ay0[4], Al0[4], php[4];
   float T1[4], T0[4];
   float Gx1[4], Gy1[4], Gx0[4], Gy0[4];
-  float mu1[4], mu2[4];  // mu_alpha of rows r-2 and r-3
+  float mu1[4], mu2[4], mu3[4], mu4[4];  // mu_alpha of rows r-2, r-3, r-4, r-5
+  float gxc[4], gyc[4];          // grad mu_beta of row r-4 (computed one iteration earlier)
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     Ax1[j] = Ay1[j] = Al1[j] = Ax0[j] = Ay0[j] = Al0[j] = php[j] = 0.0f;
-    T1[j] = T0[j] = Gx1[j] = Gy1[j] = Gx0[j] = Gy0[j] = mu1[j] = mu2[j] = 0.0f;
+    T1[j] = T0[j] = Gx1[j] = Gy1[j] = Gx0[j] = Gy0[j] = 0.0f;
+    mu1[j] = mu2[j] = mu3[j] = mu4[j] = gxc[j] = gyc[j] = 0.0f;
   }
 
-  const int n_it = (y1 - y0) + 6;
-  // Rows r-1, r, r+1 (mod ny) of the next phi row to fetch; phi rows start at y0 - 3.
+  // phi rows y0-3 .. ; row y collides at phi row y + COLLIDE_LAG.
+  const int n_it = (y1 - y0) + 3 + COLLIDE_LAG;
+  // Rows r-1, r, r+1 (mod ny) of the next phi row to fetch.
   int fm = imod(y0 - 4, a.ny), f0 = imod(y0 - 3, a.ny), fp = imod(y0 - 2, a.ny);
   auto fetch_next = [&](float4* slot) {
     issue_row<ST, VEC>(a, slot, lane, (long long)fm * a.nx, (long long)f0 * a.nx, (long long)fp * a.nx, cl);
@@ -387,11 +485,19 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, STEP_MIN_CTAS)
     if (d < n_it) fetch_next(slots + d * SLOT_F4);
     cp_async_commit();
   }
-  int s_cur = 0, s_pf = PF_DIST, s_col = SLOTS - 3;  // slots of rows r, r + PF_DIST, r - 3
+  int s_cur = 0, s_pf = PF_DIST, s_col = SLOTS - COLLIDE_LAG;  // slots of rows r, r+PF_DIST, r-LAG
   for (int it = 0; it < n_it; ++it) {
-    // 1. Fetch row r + PF_DIST; wait for row r; pull it and sum phi (Eq. 22).
+    // 1. Fetch row r + PF_DIST.
     if (it + PF_DIST < n_it) fetch_next(slots + s_pf * SLOT_F4);
     cp_async_commit();
+    // 2. With a lag of 4, collide row r-4 now: its inputs were all ready last iteration,
+    //    so this work overlaps the wait for row r.
+    if constexpr (COLLIDE_LAG == 4) {
+      if (it >= 3 + COLLIDE_LAG)
+        collide_row<ST, VEC, FAST>(a, slots + s_col * SLOT_F4, lane, y0 + it - 3 - COLLIDE_LAG, lane_out,
+                                   ocol0, nvalid, mu4, mu3, mu2, gxc, gyc);
+    }
+    // 3. Wait for row r; pull it and sum phi (Eq. 22).
     cp_async_wait<PF_DIST>();
     float ph[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     {
@@ -404,7 +510,7 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, STEP_MIN_CTAS)
       LBCH_PULL(5) LBCH_PULL(6) LBCH_PULL(7) LBCH_PULL(8)
 #undef LBCH_PULL
     }
-    // 2. grad phi and lap phi of row r-1 (Eq. 26a, 26b), rolling over rows.
+    // 4. grad phi and lap phi of row r-1 (Eq. 26a, 26b), rolling over rows.
     float dx[4], dy[4], lp[4];
     {
       float s[4], d[4];
@@ -425,13 +531,13 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, STEP_MIN_CTAS)
         Al0[j] = t;
       }
     }
-    // 3. Pointwise at row r-1.
+    // 5. Pointwise at row r-1.
     float Qx[4], Qy[4], w[4], Aq[4], mun[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) pointwise(a, php[j], dx[j], dy[j], lp[j], Qx[j], Qy[j], w[j], Aq[j], mun[j]);
 #pragma unroll
     for (int j = 0; j < 4; ++j) php[j] = ph[j];
-    // 4. mu_beta of row r-2: A - div Q + eps lap w (Eq. 26 on Q and w).
+    // 6. mu_beta of row r-2: A - div Q + eps lap w (Eq. 26 on Q and w).
     float mub[4];
     {
       float sx[4], dqx[4], sqy[4], dqy[4], sw[4], dw[4];
@@ -449,7 +555,7 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, STEP_MIN_CTAS)
         T0[j] = (bb - aa) + cc;
       }
     }
-    // 5. grad mu_beta of row r-3 (Eq. 26a).
+    // 7. grad mu_beta of row r-3 (Eq. 26a).
     float gx[4], gy[4];
     {
       float s[4], d[4];
@@ -466,42 +572,20 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, STEP_MIN_CTAS)
         Gy0[j] = -u;
       }
     }
-    // 6. Collide row r-3 and store it.
-    if (it >= 6) {
-      const float4* slot = slots + s_col * SLOT_F4;
-      float fr[9][4];
-      read_row<ST, VEC, 0>(slot, lane, fr[0]);
-      read_row<ST, VEC, 1>(slot, lane, fr[1]);
-      read_row<ST, VEC, 2>(slot, lane, fr[2]);
-      read_row<ST, VEC, 3>(slot, lane, fr[3]);
-      read_row<ST, VEC, 4>(slot, lane, fr[4]);
-      read_row<ST, VEC, 5>(slot, lane, fr[5]);
-      read_row<ST, VEC, 6>(slot, lane, fr[6]);
-      read_row<ST, VEC, 7>(slot, lane, fr[7]);
-      read_row<ST, VEC, 8>(slot, lane, fr[8]);
-      float o[9][4], phic[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        float f[9], oj[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = fr[i][j];
-        collide(a, f, mu2[j], gx[j], gy[j], oj, phic[j]);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) o[i][j] = oj[i];
-      }
-      if (lane_out) {
-        const long long ro = (long long)(y0 + it - 6) * a.nx;
-        if constexpr (VEC) {
-          store_row<ST, true>(a, ro, ocol0, o, mu2, phic);
-        } else {
-          store_row_masked<ST>(a, ro, ocol0, nvalid, o, mu2, phic);
-        }
-      }
+    // 8. With a lag of 3, collide row r-3 here.
+    if constexpr (COLLIDE_LAG == 3) {
+      if (it >= 6)
+        collide_row<ST, VEC, FAST>(a, slots + s_col * SLOT_F4, lane, y0 + it - 6, lane_out, ocol0, nvalid,
+                                   mu3, mu2, mu1, gx, gy);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+      mu4[j] = mu3[j];
+      mu3[j] = mu2[j];
       mu2[j] = mu1[j];
       mu1[j] = mun[j];
+      gxc[j] = gx[j];
+      gyc[j] = gy[j];
     }
     s_cur = s_cur + 1 == SLOTS ? 0 : s_cur + 1;
     s_pf = s_pf + 1 == SLOTS ? 0 : s_pf + 1;

@@ -204,6 +204,58 @@ def test_errors_on_gpu():
     assert s.steps_taken == 3
 
 
+# 16-bit deviation storage keeps d_i = f*_i - w_i anchor(x + c_i) to a relative 2^-9 (BF16)
+# or 2^-12 (FP16, scaled). d_i is about (1/s) w_i c_i . grad mu_alpha, so its rounding grows
+# with the roughness of the field: smooth interfaces lose ~1e-6 per step, the deliberately
+# rough U[-0.6, 0.6] fields ~1e-4..3e-4 (BF16). Bounds: measured maxima with ~2x margin.
+DEV_ROUGH_TOL = {lbch.STORE_BF16_DEV: 5e-4, lbch.STORE_F16_DEV: 8e-5}
+DEV_NAME = {lbch.STORE_BF16_DEV: "bf16-dev", lbch.STORE_F16_DEV: "f16-dev"}
+
+
+@pytest.mark.parametrize("storage", [lbch.STORE_BF16_DEV, lbch.STORE_F16_DEV])
+def test_deviation_storage_state_and_resume(storage):
+    """The canonical state of 16-bit storage tracks the oracle's populations, and a
+    checkpoint taken with get_state resumes close to the uninterrupted run."""
+    phi0 = W.noise(96, 64, 0.5, 9)
+    a = solver(96, 64, alpha=0.3, storage=storage)
+    a.init_field(phi0)
+    p = oparams(96, 64, alpha=0.3)
+    f = oracle.init(p, phi0)
+    assert np.abs(a.state() - f).max() <= 1e-7  # initial deviations are exactly zero
+    a.step(13)
+    f = oracle.step(p, f, 13)
+    err = np.abs(a.state() - f).max()
+    print(f"{DEV_NAME[storage]} state after 13 steps (U[-0.5,0.5]): max|df| = {err:.3e}")
+    assert err <= DEV_ROUGH_TOL[storage]
+    ckpt = a.state()
+    a.step(17)
+    b = solver(96, 64, alpha=0.3, storage=storage)
+    b.set_state(ckpt)
+    b.step(17)
+    err = np.abs(a.field() - b.field()).max()
+    print(f"{DEV_NAME[storage]} resume vs uninterrupted after 17 steps: max|dphi| = {err:.3e}")
+    assert err <= DEV_ROUGH_TOL[storage]
+    # set_state closes the rest population on phi, so the resumed mass differs only by
+    # FP32 rounding of the rest populations (at most 2^-24 |phi| per node).
+    assert abs(a.mass() - b.mass()) <= 2.0 ** -24 * np.abs(a.field()).sum() * 2
+
+
+@pytest.mark.parametrize("storage", [lbch.STORE_BF16_DEV, lbch.STORE_F16_DEV])
+@pytest.mark.parametrize("shape", [(130, 67), (9, 7), (256, 40)])
+def test_deviation_storage_shapes(storage, shape):
+    nx, ny = shape
+    rough = W.noise(nx, ny, 0.6, 7)
+    for t, g, r, *_ in both(nx, ny, rough, [1, 10], alpha=0.3, storage=storage):
+        err = np.abs(g - r).max()
+        print(f"{DEV_NAME[storage]} {shape} U[-0.6,0.6] step {t}: max|dphi| = {err:.3e}")
+        assert err <= DEV_ROUGH_TOL[storage], (shape, t, err)
+    spin = W.noise(nx, ny, 0.05, 7)  # the spinodal workloads' amplitude
+    for t, g, r, *_ in both(nx, ny, spin, [1, 10], alpha=0.3, storage=storage):
+        err = np.abs(g - r).max()
+        print(f"{DEV_NAME[storage]} {shape} U[-0.05,0.05] step {t}: max|dphi| = {err:.3e}")
+        assert err <= DEV_ROUGH_TOL[storage] / 10, (shape, t, err)
+
+
 @pytest.mark.parametrize("storage", [lbch.STORE_BF16_DEV, lbch.STORE_F16_DEV])
 def test_deviation_storage_reported(storage):
     """16-bit deviation storage: error against the oracle is reported; gated loosely."""
