@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the 16-bit storage variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-field parameter-sweep batch")
+    ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--storage", choices=["f32", "bf16_dev", "f16_dev"], default="f32",
                     help="population storage of the main timed line")
     return ap.parse_args()
@@ -231,6 +233,32 @@ def run_e2e(lbch, torch, phi0, n, steps, warmup):
             "wall_s": dt}
 
 
+def run_batch_sweep(lbch, torch, steps: int, count: int = 512, seed: int = 0):
+    """The parameter-sweep workload: count fields (edges from {64, 128, 256, 512}, alpha in
+    [0, 0.5], droplets and spinodal fields) stepped together, FP32 storage."""
+    import workloads
+
+    specs = workloads.batch_sweep_specs(count, seed)
+    n = [sp["n"] for sp in specs]
+    sites = sum(v * v for v in n)
+    b = lbch.Batch(lbch.make_params(8, 8), n, n, [sp["alpha"] for sp in specs])
+    for i, sp in enumerate(specs):
+        b.init_field(i, workloads.batch_field(sp))
+    b.step(64)  # warm-up (one graph replay)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    out = {"value": steps * sites / sec / 1e6, "unit": "MLUPS", "fields": count, "nodes": sites,
+           "steps": steps, "ms_per_step": sec / steps * 1e3, "rows_per_warp": b.rows_target,
+           "storage": "f32", "launch": "one kernel per step for all fields, CUDA graphs of 64 steps"}
+    b.close()
+    return out
+
+
 def cpu_oracle_rate(target_s: float = 12.0, n_sample: int = 2048):
     """The FP64 oracle, as it stands, on the host cores: MLUPS on an n_sample^2 spinodal
     sample of the workload (alpha 0.3, noise 0.05, seed 0)."""
@@ -358,6 +386,13 @@ def main():
                "h2d_bytes_per_step": e["h2d_bytes_per_step"], "d2h_bytes_per_step": e["d2h_bytes_per_step"],
                "lattice_steps_per_step": INNER}
 
+    batch = None
+    if not args.no_batch:
+        batch = run_batch_sweep(lbch, torch, args.batch_steps)
+        peak_bw = measured_peaks()[0]
+        batch["roofline_frac"] = 72 * batch["value"] * 1e6 / (peak_bw * 1e9)
+        batch["value"] = job_rate(world, batch["value"], 1.0)  # replicas: rates add
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate()
@@ -375,6 +410,7 @@ def main():
             "roofline": roofline,
             "kernel_only_mlups": world * n * n / per_launch / 1e6,
             "variants": variants,
+            "batch_sweep": batch,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),

@@ -139,6 +139,56 @@ const char* lbch_last_error(const lbch_ctx* ctx);
 /* Frees the host-side context. Never touches the workspace. NULL is ignored. */
 void lbch_destroy(lbch_ctx* ctx);
 
+/* ---- Batches: many independent periodic fields stepped together --------------------
+ *
+ * A batch holds `count` fields that share the scheme parameters of `common` (M, sigma, D,
+ * eps, s, storage, regularization, flags) and differ in size nx[i] x ny[i] and anisotropy
+ * strength alpha[i] (Eq. 6). One kernel launch advances every field by one time step
+ * (Eq. 17), so many small problems (parameter sweeps) fill the GPU together.
+ * Initial conditions, fields and diagnostics are per field and mean exactly what they
+ * mean for a single context; each field evolves exactly as it would alone. */
+typedef struct lbch_batch lbch_batch; /* opaque; lbch_batch_create / lbch_batch_destroy */
+
+/* Device workspace for a batch (every field's population buffers, one shared scratch
+ * area, the work tables); 0 for invalid arguments. nx, ny: arrays of count sizes. */
+size_t lbch_batch_workspace_bytes(const lbch_params* common, int32_t count, const int32_t* nx,
+                                  const int32_t* ny);
+
+/* Creates a batch on the current device. alpha: count strengths (NULL: common->alpha for
+ * all). The workspace rules are those of lbch_create. Creation also tunes the work split:
+ * it times a few row-segment lengths on the zeroed buffers (about a hundred launches) and
+ * captures a CUDA graph of 64 steps, which holds driver resources until lbch_batch_destroy.
+ * Returns LBCH_EINVAL, LBCH_ENOMEM or LBCH_ECUDA as lbch_create does. */
+lbch_status lbch_batch_create(const lbch_params* common, int32_t count, const int32_t* nx,
+                              const int32_t* ny, const double* alpha, void* d_workspace,
+                              size_t bytes, void* cuda_stream, lbch_batch** out);
+
+/* lbch_init_field for field i (0 <= i < count). Fields may only be (re)initialised while
+ * the batch has taken an even number of steps; LBCH_EINVAL otherwise. */
+lbch_status lbch_batch_init_field(lbch_batch* b, int32_t i, const double* h_phi0);
+
+/* Advances every field n >= 0 time steps; asynchronous like lbch_step. LBCH_EINVAL until
+ * every field has been initialised. */
+lbch_status lbch_batch_step(lbch_batch* b, int64_t n);
+
+/* lbch_get_field, lbch_mass and lbch_free_energy for field i; each synchronises. The
+ * fields share one scratch area, so calls on one batch must not overlap. */
+lbch_status lbch_batch_get_field(lbch_batch* b, int32_t i, double* h_phi);
+lbch_status lbch_batch_mass(lbch_batch* b, int32_t i, double* out);
+lbch_status lbch_batch_free_energy(lbch_batch* b, int32_t i, double* out);
+
+/* Rows per warp the creation-time tuner chose (-1 for NULL). */
+int32_t lbch_batch_rows_target(const lbch_batch* b);
+
+/* Time steps taken since creation (-1 for NULL). */
+int64_t lbch_batch_steps_taken(const lbch_batch* b);
+
+/* Description of the last error on this batch ("" if none). */
+const char* lbch_batch_last_error(const lbch_batch* b);
+
+/* Frees the batch's host objects and its CUDA graph; never touches the workspace. */
+void lbch_batch_destroy(lbch_batch* b);
+
 /* Free energy of a state the caller holds in device memory, computed without any
  * device allocation. This is a library convenience with no counterpart in the paper.
  * It serves callers that cannot call cudaMalloc, or cannot hand this library an

@@ -37,7 +37,9 @@ struct lbch_ctx {
   double* result;   // 8 doubles
   int* flags;       // 16 ints
   // Launch shapes.
-  StepArgs sa;
+  StepArgs sa;      // constants of the scheme
+  Field fld;        // geometry and work split of the field (buffers set per launch)
+  long long n_warps;
   bool vec;
   bool fast;  // s_1 = s_2 = s_4 = s_6 = s_7 = s_8 = 1: reduced collision
   int step_blocks;
@@ -120,18 +122,19 @@ const void* step_entry(bool vec, bool fast) {
 }
 
 template <int ST>
-void launch_step(lbch_ctx* c, const StepArgs& a) {
+void launch_step(lbch_ctx* c, const Field& f) {
   const dim3 g(c->step_blocks), b(STEP_WARPS * 32);
+  const StepArgs& a = c->sa;
   if (c->vec) {
     if (c->fast)
-      step_kernel<ST, true, true><<<g, b, step_smem<ST, true>(), c->stream>>>(a);
+      step_kernel<ST, true, true><<<g, b, step_smem<ST, true>(), c->stream>>>(a, f, c->n_warps);
     else
-      step_kernel<ST, true, false><<<g, b, step_smem<ST, true>(), c->stream>>>(a);
+      step_kernel<ST, true, false><<<g, b, step_smem<ST, true>(), c->stream>>>(a, f, c->n_warps);
   } else {
     if (c->fast)
-      step_kernel<ST, false, true><<<g, b, step_smem<ST, false>(), c->stream>>>(a);
+      step_kernel<ST, false, true><<<g, b, step_smem<ST, false>(), c->stream>>>(a, f, c->n_warps);
     else
-      step_kernel<ST, false, false><<<g, b, step_smem<ST, false>(), c->stream>>>(a);
+      step_kernel<ST, false, false><<<g, b, step_smem<ST, false>(), c->stream>>>(a, f, c->n_warps);
   }
 }
 
@@ -159,8 +162,8 @@ void fill_step_consts(lbch_ctx* c) {
   a.kiso = (float)(nested ? c->k : 0.0);
   a.beta4 = (float)(4.0 * c->beta);
   a.beta12 = (float)(12.0 * c->beta);
-  a.alpha = (float)p.alpha;
-  a.a16 = (float)(16.0 * p.alpha);
+  c->fld.alpha = (float)p.alpha;
+  c->fld.a16 = (float)(16.0 * p.alpha);
   a.eps = (float)eps;
   a.cw = p.regularization == LBCH_REG_LINEAR ? 0.0f : 1.0f;
   a.cfp = p.regularization == LBCH_REG_WILLMORE ? (float)eps : 0.0f;
@@ -237,23 +240,16 @@ lbch_status sync_flag(lbch_ctx* c, int* host_flag, const char* what) {
   return LBCH_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-size_t lbch_workspace_bytes(const lbch_params* p) {
-  if (check_params(p)) return 0;
+// Staging planes, reduction partials, results and flags of one field.
+size_t scratch_bytes(const lbch_params* p) {
   const size_t n = (size_t)p->nx * p->ny;
-  return 2 * state_bytes(p) + 2 * align_up(n * sizeof(double)) +
-         align_up(MAX_RED_BLOCKS * sizeof(double)) + align_up(8 * sizeof(double)) + align_up(16 * sizeof(int));
+  return 2 * align_up(n * sizeof(double)) + align_up(MAX_RED_BLOCKS * sizeof(double)) +
+         align_up(8 * sizeof(double)) + align_up(16 * sizeof(int));
 }
 
-lbch_status lbch_create(const lbch_params* p, void* d_workspace, size_t bytes, void* cuda_stream,
-                        lbch_ctx** out) {
-  if (!out) return LBCH_EINVAL;
-  if (check_params(p)) return LBCH_EINVAL;
-  const size_t need = lbch_workspace_bytes(p);
-  if (!d_workspace || bytes < need || ((uintptr_t)d_workspace % ALIGN) != 0) return LBCH_ENOMEM;
+// Sets up a context whose two population buffers start at `state` and whose scratch
+// (scratch_bytes(p)) starts at `scratch`; both 256-byte aligned device addresses.
+lbch_status ctx_setup(const lbch_params* p, char* state, char* scratch, cudaStream_t stream, lbch_ctx** out) {
   lbch_ctx* c = new (std::nothrow) lbch_ctx();
   if (!c) return LBCH_ENOMEM;
   c->p = *p;
@@ -261,20 +257,20 @@ lbch_status lbch_create(const lbch_params* p, void* d_workspace, size_t bytes, v
   c->k = 3.0 * p->sigma * p->D / 8.0;
   for (int i = 0; i < 9; ++i) c->s[i] = p->s[i];
   if (!(p->flags & LBCH_S35_EXPLICIT)) c->s[3] = c->s[5] = 1.0 / (p->M * 3.0 + 0.5);  // after Eq. 38
-  c->stream = (cudaStream_t)cuda_stream;
-  c->ws = (char*)d_workspace;
-  c->ws_bytes = bytes;
+  c->stream = stream;
+  c->ws = state;
+  c->ws_bytes = 0;
   c->ps = plane_stride(p);
   const size_t sb = state_bytes(p);
   const size_t n = (size_t)p->nx * p->ny;
   for (int b = 0; b < 2; ++b) {
-    char* base = c->ws + b * sb;
+    char* base = state + b * sb;
     c->buf[b].f32 = (float*)base;
     c->buf[b].dev = p->storage == LBCH_STORE_F32
                         ? nullptr
                         : (uint16_t*)(base + align_up((size_t)c->ps * 2 * sizeof(float)));
   }
-  char* q = c->ws + 2 * sb;
+  char* q = scratch;
   c->stage0 = (double*)q;
   q += align_up(n * sizeof(double));
   c->stage1 = (double*)q;
@@ -320,26 +316,47 @@ lbch_status lbch_create(const lbch_params* p, void* d_workspace, size_t bytes, v
   }
   // Strips of 120 output columns; segments of rows sized so that all warps fit in one
   // resident wave when the grid allows (each warp pays 6 warm-up rows).
-  StepArgs& a = c->sa;
-  a.ps = c->ps;
-  a.nx = p->nx;
-  a.ny = p->ny;
-  a.n_strips = (p->nx + OUT_W - 1) / OUT_W;
+  Field& f = c->fld;
+  f.ps = c->ps;
+  f.nx = p->nx;
+  f.ny = p->ny;
+  f.n_strips = (p->nx + OUT_W - 1) / OUT_W;
   const long long resident = (long long)sms * per_sm * STEP_WARPS;
-  long long segs = resident / a.n_strips;
+  long long segs = resident / f.n_strips;
   if (segs < 1) segs = 1;
   const long long max_segs = (p->ny + 15) / 16;  // at least ~16 rows per warp
   if (segs > max_segs) segs = max_segs;
-  a.seg_len = (int)((p->ny + segs - 1) / segs);
-  segs = (p->ny + a.seg_len - 1) / a.seg_len;
-  a.n_warps = (long long)a.n_strips * segs;
-  c->step_blocks = (int)((a.n_warps + STEP_WARPS - 1) / STEP_WARPS);
+  f.seg_len = (int)((p->ny + segs - 1) / segs);
+  segs = (p->ny + f.seg_len - 1) / f.seg_len;
+  c->n_warps = (long long)f.n_strips * segs;
+  c->step_blocks = (int)((c->n_warps + STEP_WARPS - 1) / STEP_WARPS);
   fill_step_consts(c);
   long long ab = ((long long)n + AUX_THREADS - 1) / AUX_THREADS;
   const long long cap = (long long)sms * 8 < MAX_RED_BLOCKS ? (long long)sms * 8 : MAX_RED_BLOCKS;
   c->aux_blocks = (int)(ab < cap ? ab : cap);
   *out = c;
   return LBCH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbch_workspace_bytes(const lbch_params* p) {
+  if (check_params(p)) return 0;
+  return 2 * state_bytes(p) + scratch_bytes(p);
+}
+
+lbch_status lbch_create(const lbch_params* p, void* d_workspace, size_t bytes, void* cuda_stream,
+                        lbch_ctx** out) {
+  if (!out) return LBCH_EINVAL;
+  if (check_params(p)) return LBCH_EINVAL;
+  const size_t need = lbch_workspace_bytes(p);
+  if (!d_workspace || bytes < need || ((uintptr_t)d_workspace % ALIGN) != 0) return LBCH_ENOMEM;
+  char* ws = (char*)d_workspace;
+  lbch_status st = ctx_setup(p, ws, ws + 2 * state_bytes(p), (cudaStream_t)cuda_stream, out);
+  if (st == LBCH_OK) (*out)->ws_bytes = bytes;
+  return st;
 }
 
 lbch_status lbch_init_field(lbch_ctx* c, const double* h_phi0) {
@@ -377,10 +394,10 @@ lbch_status lbch_step(lbch_ctx* c, int64_t n) {
     return LBCH_EINVAL;
   }
   for (int64_t t = 0; t < n; ++t) {
-    StepArgs a = c->sa;
-    a.src = c->buf[c->cur];
-    a.dst = c->buf[c->cur ^ 1];
-    DISPATCH(c->p.storage, launch_step, c, a);
+    Field f = c->fld;
+    f.src = c->buf[c->cur];
+    f.dst = c->buf[c->cur ^ 1];
+    DISPATCH(c->p.storage, launch_step, c, f);
     c->cur ^= 1;
   }
   c->steps += n;
@@ -616,3 +633,5 @@ const char* lbch_last_error(const lbch_ctx* c) { return c ? c->err : "context is
 void lbch_destroy(lbch_ctx* c) { delete c; }
 
 }  // extern "C"
+
+#include "lbch_batch.cuh"

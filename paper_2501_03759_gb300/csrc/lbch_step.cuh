@@ -52,24 +52,28 @@ struct Pipe {
 template <int ST, bool VEC>
 constexpr int step_smem() { return STEP_WARPS * Pipe<ST, VEC>::SLOTS * Pipe<ST, VEC>::SLOT_F4 * 16; }
 
+// Constants shared by every field a launch steps.
 struct StepArgs {
-  Buf src, dst;
-  long long ps;  // plane stride in elements
-  int nx, ny;
-  int n_strips, seg_len;
-  long long n_warps;
   // Chemical potential constants.
   float k;     // gradient energy coefficient (Eq. 5)
   float kq;    // factor on |grad phi| P grad_n gamma in Q (k, or 1 for the literal Eq. 15)
   float kiso;  // k times the isotropic part kept in Q (0 split, k nested)
   float beta4, beta12;  // 4 beta and 12 beta (f and f')
-  float alpha, a16;     // alpha, 16 alpha
   float eps;   // eps on lap w (0 without regularisation)
   float cw;    // w = lap phi - cw f  (1 Willmore, 0 linear)
   float cfp;   // eps on f' w (Willmore only)
   float cnk;   // k lap phi added to mu_beta in nested form
   // Collision: n_k = (m*_k)/|row k of M|^2 in terms of m_k, m^eq_k and g.
   float c1a, c1b, c2a, c2b, c3a, c3g, c4a, c4g, c5a, c5g, c6a, c6g, c7, c8;
+};
+
+// One periodic field: its buffers, its size and work split, and its anisotropy.
+struct Field {
+  Buf src, dst;
+  long long ps;  // plane stride in elements
+  int nx, ny;
+  int n_strips, seg_len;
+  float alpha, a16;  // alpha and 16 alpha (Eq. 6)
 };
 
 __device__ __forceinline__ int imod(int v, int n) {
@@ -119,21 +123,21 @@ __device__ __forceinline__ void cp_async_wait() {
 // Fetches phi row r (rows ro_m = r-1, ro_0 = r, ro_p = r+1) into a slot; the vector path
 // copies asynchronously (cp.async), the scalar path loads and stores synchronously.
 template <int ST, bool VEC>
-__device__ __forceinline__ void issue_row(const StepArgs& a, float4* slot, int lane, long long ro_m,
+__device__ __forceinline__ void issue_row(const Field& fd, float4* slot, int lane, long long ro_m,
                                           long long ro_0, long long ro_p, const Cols& cl) {
 #define LBCH_RO(I) (cy(I) == 1 ? ro_m : (cy(I) == -1 ? ro_p : ro_0))
   if constexpr (VEC) {
     if constexpr (ST == ST_F32) {
 #pragma unroll
       for (int i = 0; i < 9; ++i)
-        cp_async16(slot + i * 32 + lane, a.src.f32 + (long long)i * a.ps + LBCH_RO(i) + cl.c0);
+        cp_async16(slot + i * 32 + lane, fd.src.f32 + (long long)i * fd.ps + LBCH_RO(i) + cl.c0);
     } else {
-      cp_async16(slot + lane, a.src.f32 + ro_0 + cl.c0);
-      cp_async16(slot + 32 + lane, a.src.f32 + a.ps + ro_0 + cl.c0);
+      cp_async16(slot + lane, fd.src.f32 + ro_0 + cl.c0);
+      cp_async16(slot + 32 + lane, fd.src.f32 + fd.ps + ro_0 + cl.c0);
       uint2* ds = reinterpret_cast<uint2*>(slot + 64);
 #pragma unroll
       for (int i = 1; i < 9; ++i)
-        cp_async8(ds + (i - 1) * 32 + lane, a.src.dev + (long long)(i - 1) * a.ps + LBCH_RO(i) + cl.c0);
+        cp_async8(ds + (i - 1) * 32 + lane, fd.src.dev + (long long)(i - 1) * fd.ps + LBCH_RO(i) + cl.c0);
     }
   } else {
 #pragma unroll
@@ -144,12 +148,12 @@ __device__ __forceinline__ void issue_row(const StepArgs& a, float4* slot, int l
       for (int j = 0; j < 4; ++j) {
         const int c = cl.cs[j - cx(i) + 1];  // pull: f_in,i(x) = f*_i(x - c_i)
         if constexpr (ST == ST_F32) {
-          v[j] = __ldg(a.src.f32 + (long long)i * a.ps + ro + c);
+          v[j] = __ldg(fd.src.f32 + (long long)i * fd.ps + ro + c);
         } else if (i == 0) {
-          v[j] = __ldg(a.src.f32 + ro + c);
+          v[j] = __ldg(fd.src.f32 + ro + c);
         } else {  // w_i times the anchor of this node, plus the deviation from the source node
-          v[j] = fmaf((float)wgt(i), __ldg(a.src.f32 + a.ps + ro_0 + cl.cs[j + 1]),
-                      Dev<ST>::load(__ldg(a.src.dev + (long long)(i - 1) * a.ps + ro + c)));
+          v[j] = fmaf((float)wgt(i), __ldg(fd.src.f32 + fd.ps + ro_0 + cl.cs[j + 1]),
+                      Dev<ST>::load(__ldg(fd.src.dev + (long long)(i - 1) * fd.ps + ro + c)));
         }
       }
       slot[i * 32 + lane] = make_float4(v[0], v[1], v[2], v[3]);
@@ -193,7 +197,7 @@ __device__ __forceinline__ void read_row(const float4* slot, int lane, float (&v
 
 // Pointwise part at one node: Q (Eq. 15 reading), w, mu_alpha (Eq. 16) and the
 // local part A of mu_beta (Eq. 13 minus Eq. 16's mu_alpha).
-__device__ __forceinline__ void pointwise(const StepArgs& a, float phi, float dx, float dy,
+__device__ __forceinline__ void pointwise(const StepArgs& a, const Field& fd, float phi, float dx, float dy,
                                           float lap, float& Qx, float& Qy, float& w, float& A,
                                           float& mua) {
   const float g2 = fmaf(dx, dx, dy * dy);
@@ -202,9 +206,9 @@ __device__ __forceinline__ void pointwise(const StepArgs& a, float phi, float dx
   const float n1 = dx * rs, n2 = dy * rs;  // Eq. 2
   const float n1s = n1 * n1, n2s = n2 * n2;
   const float S4 = fmaf(n1s, n1s, n2s * n2s);
-  const float gm1 = ok ? a.alpha * fmaf(4.0f, S4, -3.0f) : 0.0f;  // gamma - 1, Eq. 6
+  const float gm1 = ok ? fd.alpha * fmaf(4.0f, S4, -3.0f) : 0.0f;  // gamma - 1, Eq. 6
   // k_q |grad phi| P grad_n gamma with grad_n gamma = 16 alpha n^3, P = I - n n^T.
-  const float t = ok ? a.kq * a.a16 * (g2 * rs) : 0.0f;
+  const float t = ok ? a.kq * fd.a16 * (g2 * rs) : 0.0f;
   const float kg = fmaf(a.k, gm1, a.kiso);
   Qx = fmaf(kg, dx, t * (n1 * (n1s - S4)));
   Qy = fmaf(kg, dy, t * (n2 * (n2s - S4)));
@@ -288,13 +292,13 @@ __device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], 
 // conserved to FP32 rounding, not 16-bit rounding). dmu[i-1][j] is the anchor of the
 // node population i of column j streams to.
 template <int ST, bool VEC>
-__device__ __forceinline__ void store_row(const StepArgs& a, long long ro, long long col,
+__device__ __forceinline__ void store_row(const Field& fd, long long ro, long long col,
                                           const float (&o)[9][4], const float (&mua)[4],
                                           const float (&dmu)[8][4], const float (&phi)[4]) {
   if constexpr (ST == ST_F32) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      float* p = a.dst.f32 + (long long)i * a.ps + ro + col;
+      float* p = fd.dst.f32 + (long long)i * fd.ps + ro + col;
       if constexpr (VEC) {
         *reinterpret_cast<float4*>(p) = make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
       } else {
@@ -317,8 +321,8 @@ __device__ __forceinline__ void store_row(const StepArgs& a, long long ro, long 
       }
       rest[j] = phi[j] - sum;
     }
-    float* p0 = a.dst.f32 + ro + col;
-    float* pm = a.dst.f32 + a.ps + ro + col;
+    float* p0 = fd.dst.f32 + ro + col;
+    float* pm = fd.dst.f32 + fd.ps + ro + col;
     if constexpr (VEC) {
       *reinterpret_cast<float4*>(p0) = make_float4(rest[0], rest[1], rest[2], rest[3]);
       *reinterpret_cast<float4*>(pm) = make_float4(mua[0], mua[1], mua[2], mua[3]);
@@ -331,7 +335,7 @@ __device__ __forceinline__ void store_row(const StepArgs& a, long long ro, long 
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      uint16_t* pd = a.dst.dev + (long long)i * a.ps + ro + col;
+      uint16_t* pd = fd.dst.dev + (long long)i * fd.ps + ro + col;
       if constexpr (VEC) {
         *reinterpret_cast<uint2*>(pd) =
             make_uint2(static_cast<uint32_t>(d[i][0]) | (static_cast<uint32_t>(d[i][1]) << 16),
@@ -346,18 +350,18 @@ __device__ __forceinline__ void store_row(const StepArgs& a, long long ro, long 
 
 // Scalar-path store for columns that may be partly out of range (not 4-aligned grids).
 template <int ST>
-__device__ __forceinline__ void store_row_masked(const StepArgs& a, long long ro, int col0, int nvalid,
+__device__ __forceinline__ void store_row_masked(const Field& fd, long long ro, int col0, int nvalid,
                                                  const float (&o)[9][4], const float (&mua)[4],
                                                  const float (&dmu)[8][4], const float (&phi)[4]) {
   if (nvalid >= 4) {
-    store_row<ST, false>(a, ro, col0, o, mua, dmu, phi);
+    store_row<ST, false>(fd, ro, col0, o, mua, dmu, phi);
     return;
   }
   // Fewer than 4 valid columns: write them one at a time.
   if constexpr (ST == ST_F32) {
     for (int j = 0; j < nvalid; ++j)
 #pragma unroll
-      for (int i = 0; i < 9; ++i) a.dst.f32[(long long)i * a.ps + ro + col0 + j] = o[i][j];
+      for (int i = 0; i < 9; ++i) fd.dst.f32[(long long)i * fd.ps + ro + col0 + j] = o[i][j];
   } else {
     using D = Dev<ST>;
     for (int j = 0; j < nvalid; ++j) {
@@ -367,10 +371,10 @@ __device__ __forceinline__ void store_row_masked(const StepArgs& a, long long ro
         const float w = (float)wgt(i);
         const uint16_t d = D::store(o[i][j] - w * dmu[i - 1][j]);
         sum += fmaf(w, dmu[i - 1][j], D::load(d));
-        a.dst.dev[(long long)(i - 1) * a.ps + ro + col0 + j] = d;
+        fd.dst.dev[(long long)(i - 1) * fd.ps + ro + col0 + j] = d;
       }
-      a.dst.f32[ro + col0 + j] = phi[j] - sum;
-      a.dst.f32[a.ps + ro + col0 + j] = mua[j];
+      fd.dst.f32[ro + col0 + j] = phi[j] - sum;
+      fd.dst.f32[fd.ps + ro + col0 + j] = mua[j];
     }
   }
 }
@@ -378,7 +382,8 @@ __device__ __forceinline__ void store_row_masked(const StepArgs& a, long long ro
 // Collides row `row` of this warp's strip from its landing slot and stores it.
 // mu_m, mu_c, mu_p: mu_alpha of rows row-1, row, row+1 at this lane's columns.
 template <int ST, bool VEC, bool FAST>
-__device__ __forceinline__ void collide_row(const StepArgs& a, const float4* slot, int lane, int row,
+__device__ __forceinline__ void collide_row(const StepArgs& a, const Field& fd, const float4* slot, int lane,
+                                            int row,
                                             bool store, int ocol0, int nvalid, const float (&mu_m)[4],
                                             const float (&mu_c)[4], const float (&mu_p)[4],
                                             const float (&gx)[4], const float (&gy)[4]) {
@@ -421,41 +426,34 @@ __device__ __forceinline__ void collide_row(const StepArgs& a, const float4* slo
       for (int j = 0; j < 4; ++j) dmu[i - 1][j] = ext[1 + cy(i)][j + cx(i) + 1];
   }
   if (store) {
-    const long long ro = (long long)row * a.nx;
+    const long long ro = (long long)row * fd.nx;
     if constexpr (VEC) {
-      store_row<ST, true>(a, ro, ocol0, o, mu_c, dmu, phic);
+      store_row<ST, true>(fd, ro, ocol0, o, mu_c, dmu, phic);
     } else {
-      store_row_masked<ST>(a, ro, ocol0, nvalid, o, mu_c, dmu, phic);
+      store_row_masked<ST>(fd, ro, ocol0, nvalid, o, mu_c, dmu, phic);
     }
   }
 }
 
+// One warp's work: the rows [seg * seg_len, ...) of strip `strip` of field fd.
 template <int ST, bool VEC, bool FAST>
-__global__ void __launch_bounds__(STEP_WARPS * 32, (Pipe<ST, VEC>::MIN_CTAS))
-    step_kernel(const __grid_constant__ StepArgs a) {
-  extern __shared__ float4 smem_slots[];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const long long warp = (long long)blockIdx.x * STEP_WARPS + wib;
-  if (warp >= a.n_warps) return;  // whole warps only: shuffles below see all 32 lanes
-  const int strip = (int)(warp % a.n_strips);
-  const int seg = (int)(warp / a.n_strips);
-  const int y0 = seg * a.seg_len;
-  const int y1 = min(y0 + a.seg_len, a.ny);
-  const int xs = strip * OUT_W - HALO_W;  // strip start column (before wrap)
+__device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, int strip, int seg, float4* slots,
+                                          int lane) {
   using PP = Pipe<ST, VEC>;
   constexpr int PF_DIST = PP::PF_DIST, COLLIDE_LAG = PP::LAG, SLOTS = PP::SLOTS, SLOT_F4 = PP::SLOT_F4;
-  float4* slots = smem_slots + wib * (SLOTS * SLOT_F4);  // this warp's landing slots
+  const int y0 = seg * fd.seg_len;
+  const int y1 = min(y0 + fd.seg_len, fd.ny);
+  const int xs = strip * OUT_W - HALO_W;  // strip start column (before wrap)
 
   Cols cl;
-  cl.c0 = imod(xs + 4 * lane, a.nx);
+  cl.c0 = imod(xs + 4 * lane, fd.nx);
 #pragma unroll
-  for (int k = 0; k < 6; ++k) cl.cs[k] = imod(xs + 4 * lane + k - 1, a.nx);
+  for (int k = 0; k < 6; ++k) cl.cs[k] = imod(xs + 4 * lane + k - 1, fd.nx);
 
   // Output columns of this lane: strip columns 4 lane + j in [HALO_W, STRIP_W - HALO_W).
   const int ocol0 = strip * OUT_W + 4 * lane - HALO_W;  // global column of element 0
-  const bool lane_out = lane >= 1 && lane <= 30 && ocol0 < a.nx;
-  const int nvalid = min(4, a.nx - ocol0);
+  const bool lane_out = lane >= 1 && lane <= 30 && ocol0 < fd.nx;
+  const int nvalid = min(4, fd.nx - ocol0);
 
   // Rolling accumulators (see the header comment): index 1 = row completing next, 0 = row after.
   float Ax1[4], Ay1[4], Al1[4], Ax0[4], Ay0[4], Al0[4], php[4];
@@ -473,12 +471,12 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, (Pipe<ST, VEC>::MIN_CTAS))
   // phi rows y0-3 .. ; row y collides at phi row y + COLLIDE_LAG.
   const int n_it = (y1 - y0) + 3 + COLLIDE_LAG;
   // Rows r-1, r, r+1 (mod ny) of the next phi row to fetch.
-  int fm = imod(y0 - 4, a.ny), f0 = imod(y0 - 3, a.ny), fp = imod(y0 - 2, a.ny);
+  int fm = imod(y0 - 4, fd.ny), f0 = imod(y0 - 3, fd.ny), fp = imod(y0 - 2, fd.ny);
   auto fetch_next = [&](float4* slot) {
-    issue_row<ST, VEC>(a, slot, lane, (long long)fm * a.nx, (long long)f0 * a.nx, (long long)fp * a.nx, cl);
+    issue_row<ST, VEC>(fd, slot, lane, (long long)fm * fd.nx, (long long)f0 * fd.nx, (long long)fp * fd.nx, cl);
     fm = f0;
     f0 = fp;
-    fp = fp + 1 == a.ny ? 0 : fp + 1;
+    fp = fp + 1 == fd.ny ? 0 : fp + 1;
   };
 #pragma unroll
   for (int d = 0; d < PF_DIST; ++d) {
@@ -494,7 +492,7 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, (Pipe<ST, VEC>::MIN_CTAS))
     //    so this work overlaps the wait for row r.
     if constexpr (COLLIDE_LAG == 4) {
       if (it >= 3 + COLLIDE_LAG)
-        collide_row<ST, VEC, FAST>(a, slots + s_col * SLOT_F4, lane, y0 + it - 3 - COLLIDE_LAG, lane_out,
+        collide_row<ST, VEC, FAST>(a, fd, slots + s_col * SLOT_F4, lane, y0 + it - 3 - COLLIDE_LAG, lane_out,
                                    ocol0, nvalid, mu4, mu3, mu2, gxc, gyc);
     }
     // 3. Wait for row r; pull it and sum phi (Eq. 22).
@@ -534,7 +532,7 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, (Pipe<ST, VEC>::MIN_CTAS))
     // 5. Pointwise at row r-1.
     float Qx[4], Qy[4], w[4], Aq[4], mun[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) pointwise(a, php[j], dx[j], dy[j], lp[j], Qx[j], Qy[j], w[j], Aq[j], mun[j]);
+    for (int j = 0; j < 4; ++j) pointwise(a, fd, php[j], dx[j], dy[j], lp[j], Qx[j], Qy[j], w[j], Aq[j], mun[j]);
 #pragma unroll
     for (int j = 0; j < 4; ++j) php[j] = ph[j];
     // 6. mu_beta of row r-2: A - div Q + eps lap w (Eq. 26 on Q and w).
@@ -575,7 +573,7 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, (Pipe<ST, VEC>::MIN_CTAS))
     // 8. With a lag of 3, collide row r-3 here.
     if constexpr (COLLIDE_LAG == 3) {
       if (it >= 6)
-        collide_row<ST, VEC, FAST>(a, slots + s_col * SLOT_F4, lane, y0 + it - 6, lane_out, ocol0, nvalid,
+        collide_row<ST, VEC, FAST>(a, fd, slots + s_col * SLOT_F4, lane, y0 + it - 6, lane_out, ocol0, nvalid,
                                    mu3, mu2, mu1, gx, gy);
     }
 #pragma unroll
@@ -592,6 +590,20 @@ __global__ void __launch_bounds__(STEP_WARPS * 32, (Pipe<ST, VEC>::MIN_CTAS))
     s_col = s_col + 1 == SLOTS ? 0 : s_col + 1;
   }
   cp_async_wait<0>();
+}
+
+
+// Single field: warp w takes strip w % n_strips of segment w / n_strips.
+template <int ST, bool VEC, bool FAST>
+__global__ void __launch_bounds__(STEP_WARPS * 32, (Pipe<ST, VEC>::MIN_CTAS))
+    step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ Field fd, long long n_warps) {
+  extern __shared__ float4 smem_slots[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const long long warp = (long long)blockIdx.x * STEP_WARPS + wib;
+  if (warp >= n_warps) return;  // whole warps only: shuffles see all 32 lanes
+  float4* slots = smem_slots + wib * (Pipe<ST, VEC>::SLOTS * Pipe<ST, VEC>::SLOT_F4);
+  step_warp<ST, VEC, FAST>(a, fd, (int)(warp % fd.n_strips), (int)(warp / fd.n_strips), slots, lane);
 }
 
 }  // namespace lbch

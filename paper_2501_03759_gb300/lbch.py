@@ -105,6 +105,27 @@ def load():
         lib.lbch_destroy.restype = None
         lib.lbch_free_energy_static.argtypes = [P, vp, ctypes.c_int64, vp, vp]
         lib.lbch_free_energy_static.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int32)
+        lib.lbch_batch_workspace_bytes.argtypes = [P, ctypes.c_int32, ip, ip]
+        lib.lbch_batch_workspace_bytes.restype = ctypes.c_size_t
+        lib.lbch_batch_create.argtypes = [P, ctypes.c_int32, ip, ip, dp, vp, ctypes.c_size_t, vp,
+                                          ctypes.POINTER(vp)]
+        lib.lbch_batch_create.restype = ctypes.c_int
+        lib.lbch_batch_init_field.argtypes = [vp, ctypes.c_int32, dp]
+        lib.lbch_batch_init_field.restype = ctypes.c_int
+        lib.lbch_batch_step.argtypes = [vp, ctypes.c_int64]
+        lib.lbch_batch_step.restype = ctypes.c_int
+        for name in ("lbch_batch_get_field", "lbch_batch_mass", "lbch_batch_free_energy"):
+            getattr(lib, name).argtypes = [vp, ctypes.c_int32, dp]
+            getattr(lib, name).restype = ctypes.c_int
+        lib.lbch_batch_rows_target.argtypes = [vp]
+        lib.lbch_batch_rows_target.restype = ctypes.c_int32
+        lib.lbch_batch_steps_taken.argtypes = [vp]
+        lib.lbch_batch_steps_taken.restype = ctypes.c_int64
+        lib.lbch_batch_last_error.argtypes = [vp]
+        lib.lbch_batch_last_error.restype = ctypes.c_char_p
+        lib.lbch_batch_destroy.argtypes = [vp]
+        lib.lbch_batch_destroy.restype = None
         _lib = lib
         return lib
 
@@ -276,6 +297,144 @@ class Solver:
         if getattr(self, "ctx", None):
             lbch_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batches (C names)
+
+def _i32(v):
+    a = np.ascontiguousarray(v, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _batch_check(b, status: int, what: str):
+    if status != OK:
+        detail = (load().lbch_batch_last_error(b) or b"").decode(errors="replace") if b else ""
+        raise LbchError(status, what, detail)
+
+
+def lbch_batch_workspace_bytes(common: lbch_params, nx, ny) -> int:
+    (ax, px), (ay, py) = _i32(nx), _i32(ny)
+    return int(load().lbch_batch_workspace_bytes(ctypes.byref(common), len(ax), px, py))
+
+
+def lbch_batch_create(common: lbch_params, nx, ny, alpha, d_workspace: int, nbytes: int, cuda_stream):
+    (ax, px), (ay, py) = _i32(nx), _i32(ny)
+    al = None if alpha is None else np.ascontiguousarray(alpha, dtype=np.float64)
+    b = ctypes.c_void_p()
+    st = load().lbch_batch_create(ctypes.byref(common), len(ax), px, py, None if al is None else _host_ptr(al),
+                                  ctypes.c_void_p(int(d_workspace)), int(nbytes),
+                                  ctypes.c_void_p(int(cuda_stream or 0)), ctypes.byref(b))
+    _batch_check(None, st, "lbch_batch_create")
+    return b
+
+
+def lbch_batch_init_field(b, i: int, phi0) -> None:
+    _batch_check(b, load().lbch_batch_init_field(b, int(i), _host_ptr(phi0)), "lbch_batch_init_field")
+
+
+def lbch_batch_step(b, n: int) -> None:
+    _batch_check(b, load().lbch_batch_step(b, int(n)), "lbch_batch_step")
+
+
+def lbch_batch_get_field(b, i: int, out: np.ndarray) -> np.ndarray:
+    _batch_check(b, load().lbch_batch_get_field(b, int(i), _host_ptr(out)), "lbch_batch_get_field")
+    return out
+
+
+def lbch_batch_mass(b, i: int) -> float:
+    v = ctypes.c_double()
+    _batch_check(b, load().lbch_batch_mass(b, int(i), ctypes.byref(v)), "lbch_batch_mass")
+    return v.value
+
+
+def lbch_batch_free_energy(b, i: int) -> float:
+    v = ctypes.c_double()
+    _batch_check(b, load().lbch_batch_free_energy(b, int(i), ctypes.byref(v)), "lbch_batch_free_energy")
+    return v.value
+
+
+def lbch_batch_rows_target(b) -> int:
+    return int(load().lbch_batch_rows_target(b))
+
+
+def lbch_batch_steps_taken(b) -> int:
+    return int(load().lbch_batch_steps_taken(b))
+
+
+def lbch_batch_last_error(b) -> str:
+    return (load().lbch_batch_last_error(b) or b"").decode(errors="replace")
+
+
+def lbch_batch_destroy(b) -> None:
+    if b:
+        load().lbch_batch_destroy(b)
+
+
+class Batch:
+    """Owns a batch of periodic fields (sizes nx[i] x ny[i], strengths alpha[i]) and its
+    device workspace; the other parameters come from ``common``."""
+
+    def __init__(self, common: lbch_params, nx, ny, alpha=None, device=None, stream=None):
+        import torch
+
+        self.nx = [int(v) for v in nx]
+        self.ny = [int(v) for v in ny]
+        self.count = len(self.nx)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        nbytes = lbch_batch_workspace_bytes(common, self.nx, self.ny)
+        if nbytes == 0:
+            raise LbchError(EINVAL, "lbch_batch_workspace_bytes", "invalid arguments")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.handle = lbch_batch_create(common, self.nx, self.ny, alpha, self.workspace.data_ptr(), nbytes,
+                                            self.stream.cuda_stream)
+
+    def _on_device(self):
+        import torch
+        return torch.cuda.device(self.device)
+
+    def init_field(self, i: int, phi0) -> None:
+        a = _as_host_f64(phi0, self.nx[i] * self.ny[i], "phi0")
+        with self._on_device():
+            lbch_batch_init_field(self.handle, i, a)
+
+    def step(self, n: int) -> None:
+        with self._on_device():
+            lbch_batch_step(self.handle, n)
+
+    def field(self, i: int) -> np.ndarray:
+        out = np.empty((self.ny[i], self.nx[i]), dtype=np.float64)
+        with self._on_device():
+            lbch_batch_get_field(self.handle, i, out)
+        return out
+
+    def mass(self, i: int) -> float:
+        with self._on_device():
+            return lbch_batch_mass(self.handle, i)
+
+    def free_energy(self, i: int) -> float:
+        with self._on_device():
+            return lbch_batch_free_energy(self.handle, i)
+
+    @property
+    def rows_target(self) -> int:
+        return lbch_batch_rows_target(self.handle)
+
+    @property
+    def steps_taken(self) -> int:
+        return lbch_batch_steps_taken(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lbch_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

@@ -67,3 +67,24 @@ def planar_bands(nx: int, ny: int, x_left: float, x_right: float, width: float) 
     """+1 between two planar interfaces normal to x, -1 outside; tanh profiles of the given width."""
     x = np.arange(nx, dtype=np.float64)[None, :].repeat(ny, axis=0)
     return np.tanh((x - x_left) / width) - np.tanh((x - x_right) / width) - 1.0
+
+
+def batch_sweep_specs(count: int = 512, seed: int = 0):
+    """The parameter-sweep batch: count square fields with edges drawn uniformly from
+    {64, 128, 256, 512}, alpha ~ U[0, 0.5], alternating droplet (radius 0.3 L, profile
+    tanh((R - r)/(sqrt(2) 1.5))) and spinodal (U[-0.05, 0.05]) initial fields.
+
+    Returns a list of dicts (n, alpha, kind, seed); batch_field(spec) builds phi0."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.choice(np.array([64, 128, 256, 512]), size=count)
+    alphas = rng.uniform(0.0, 0.5, size=count)
+    field_seeds = rng.integers(0, 2**31 - 1, size=count)
+    return [{"n": int(sizes[i]), "alpha": float(alphas[i]), "kind": "droplet" if i % 2 == 0 else "spinodal",
+             "seed": int(field_seeds[i])} for i in range(count)]
+
+
+def batch_field(spec) -> np.ndarray:
+    n = spec["n"]
+    if spec["kind"] == "droplet":
+        return droplet(n, n, radius=0.3 * n, width=np.sqrt(2.0) * 1.5)
+    return noise(n, n, 0.05, spec["seed"])
