@@ -86,6 +86,42 @@ class Params:
         return p
 
 
+class _Params3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("M", ctypes.c_double), ("sigma", ctypes.c_double), ("D", ctypes.c_double),
+        ("eps", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("s", ctypes.c_double * 15),
+        ("regularization", ctypes.c_int32), ("flags", ctypes.c_uint32),
+    ]
+
+
+@dataclass
+class Params3:
+    """3D (D3Q15) scheme parameters; defaults as Params."""
+    nx: int
+    ny: int
+    nz: int
+    M: float = 0.1
+    sigma: float = 0.01
+    D: float = 5.0
+    eps: float = 0.03
+    alpha: float = 0.0
+    s: list = field(default_factory=lambda: [1.0] * 15)
+    regularization: int = WILLMORE
+    flags: int = 0
+
+    def c(self) -> _Params3:
+        p = _Params3()
+        p.nx, p.ny, p.nz = int(self.nx), int(self.ny), int(self.nz)
+        p.M, p.sigma, p.D, p.eps, p.alpha = self.M, self.sigma, self.D, self.eps, self.alpha
+        for i in range(15):
+            p.s[i] = float(self.s[i])
+        p.regularization = int(self.regularization)
+        p.flags = int(self.flags)
+        return p
+
+
 def _load():
     global _lib
     with _lock:
@@ -109,6 +145,19 @@ def _load():
             lib.orc_energy.restype = ctypes.c_double
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_set_threads.restype = ctypes.c_int
+            p3 = ctypes.POINTER(_Params3)
+            lib.orc3_matrices.argtypes = [dp, dp]
+            lib.orc3_equilibrium.argtypes = [ctypes.c_double, ctypes.c_double, dp]
+            lib.orc3_source.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+            lib.orc3_collide_site.argtypes = [p3, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, dp]
+            lib.orc3_init.argtypes = [p3, dp, dp]
+            lib.orc3_step.argtypes = [p3, dp, ctypes.c_int64]
+            lib.orc3_phi.argtypes = [p3, dp, dp]
+            lib.orc3_mass.argtypes = [p3, dp]
+            lib.orc3_mass.restype = ctypes.c_double
+            lib.orc3_energy.argtypes = [p3, dp]
+            lib.orc3_energy.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -225,3 +274,66 @@ def run_window(p: Params, phi0_full: np.ndarray, x0: int, y0: int, w: int, h: in
     q = Params(**{**p.__dict__, "nx": sub.shape[1], "ny": sub.shape[0]})
     out = run(q, sub, nsteps)
     return out[pad:pad + h, pad:pad + w]
+
+
+# ---------------------------------------------------------------- 3D (D3Q15)
+
+def matrices3():
+    """(M of Eq. 24 as built by the oracle, its Gauss-Jordan inverse), 15x15."""
+    M = np.zeros((15, 15))
+    Mi = np.zeros((15, 15))
+    _load().orc3_matrices(_ptr(M), _ptr(Mi))
+    return M, Mi
+
+
+def equilibrium3(phi: float, mu_alpha: float) -> np.ndarray:
+    out = np.zeros(15)
+    _load().orc3_equilibrium(phi, mu_alpha, _ptr(out))
+    return out
+
+
+def source3(gx: float, gy: float, gz: float) -> np.ndarray:
+    out = np.zeros(15)
+    _load().orc3_source(gx, gy, gz, _ptr(out))
+    return out
+
+
+def collide_site3(p: Params3, f15, phi, mu_alpha, gx, gy, gz) -> np.ndarray:
+    fi = np.ascontiguousarray(f15, dtype=np.float64)
+    out = np.zeros(15)
+    _load().orc3_collide_site(ctypes.byref(p.c()), _ptr(fi), phi, mu_alpha, gx, gy, gz, _ptr(out))
+    return out
+
+
+def init3(p: Params3, phi0: np.ndarray) -> np.ndarray:
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    assert phi0.shape == (p.nz, p.ny, p.nx)
+    f = np.zeros((15, p.nz, p.ny, p.nx))
+    _check(_load().orc3_init(ctypes.byref(p.c()), _ptr(phi0), _ptr(f)), "init3")
+    return f
+
+
+def step3(p: Params3, f: np.ndarray, nsteps: int) -> np.ndarray:
+    g = np.array(f, dtype=np.float64, order="C", copy=True)
+    assert g.shape == (15, p.nz, p.ny, p.nx)
+    _check(_load().orc3_step(ctypes.byref(p.c()), _ptr(g), int(nsteps)), "step3")
+    return g
+
+
+def phi3(p: Params3, f: np.ndarray) -> np.ndarray:
+    out = np.zeros((p.nz, p.ny, p.nx))
+    _check(_load().orc3_phi(ctypes.byref(p.c()), _ptr(np.ascontiguousarray(f)), _ptr(out)), "phi3")
+    return out
+
+
+def mass3(p: Params3, f: np.ndarray) -> float:
+    return float(_load().orc3_mass(ctypes.byref(p.c()), _ptr(np.ascontiguousarray(f))))
+
+
+def energy3(p: Params3, f: np.ndarray) -> float:
+    return float(_load().orc3_energy(ctypes.byref(p.c()), _ptr(np.ascontiguousarray(f))))
+
+
+def run3(p: Params3, phi0: np.ndarray, nsteps: int) -> np.ndarray:
+    """phi after nsteps 3D steps from f = f^eq(phi0)."""
+    return phi3(p, step3(p, init3(p, phi0), nsteps))

@@ -488,3 +488,405 @@ int orc_set_threads(int n) {
 }
 
 }  // extern "C"
+
+// ===================================================================================
+// 3D: D3Q15, the same scheme with d = 3 (Eqs. 3, 6, 17-19, 21, 22, 24, 26).
+// ===================================================================================
+
+namespace {
+
+// Eq. 21a (c = 1) and Eq. 21b.
+const int CX3[15] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, -1, 1};
+const int CY3[15] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1};
+const int CZ3[15] = {0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, 1, -1, 1, -1};
+const double W3[15] = {2.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
+                       1.0 / 9.0,  1.0 / 9.0,  1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0,
+                       1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0, 1.0 / 72.0};
+
+// Row k of Eq. 24 as the function of c it names, at velocity i.
+double m3_row(int k, int i) {
+  const double x = CX3[i], y = CY3[i], z = CZ3[i], c2 = x * x + y * y + z * z;
+  switch (k) {
+    case 0: return 1.0;                                      // rho
+    case 1: return c2 - 2.0;                                 // e
+    case 2: return (15.0 * c2 * c2 - 55.0 * c2 + 32.0) / 2;  // epsilon
+    case 3: return x;                                        // j_x
+    case 4: return (5.0 * c2 - 13.0) / 2.0 * x;              // q_x
+    case 5: return y;                                        // j_y
+    case 6: return (5.0 * c2 - 13.0) / 2.0 * y;              // q_y
+    case 7: return z;                                        // j_z
+    case 8: return (5.0 * c2 - 13.0) / 2.0 * z;              // q_z
+    case 9: return 3.0 * x * x - c2;                         // 3 p_xx
+    case 10: return y * y - z * z;                           // p_ww
+    case 11: return x * y;                                   // p_xy
+    case 12: return y * z;                                   // p_yz
+    case 13: return x * z;                                   // p_xz
+    default: return x * y * z;                               // m_xyz
+  }
+}
+
+// Gauss-Jordan inversion of an n x n row-major matrix (n <= 15).
+void invert_n(int n, const double* a_in, double* inv) {
+  double a[15][30];
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < 2 * n; ++c) a[r][c] = c < n ? a_in[r * n + c] : (c - n == r ? 1.0 : 0.0);
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(a[r][col]) > std::fabs(a[piv][col])) piv = r;
+    if (piv != col)
+      for (int c = 0; c < 2 * n; ++c) std::swap(a[col][c], a[piv][c]);
+    const double d = a[col][col];
+    for (int c = 0; c < 2 * n; ++c) a[col][c] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double m = a[r][col];
+      if (m == 0.0) continue;
+      for (int c = 0; c < 2 * n; ++c) a[r][c] -= m * a[col][c];
+    }
+  }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) inv[r * n + c] = a[r][c + n];
+}
+
+struct Scheme3 {
+  int nx, ny, nz;
+  double k, beta, eps, alpha;
+  int reg;
+  unsigned flags;
+  double s[15];
+  double M[15][15], Minv[15][15], A[15][15], B[15][15];
+};
+
+int make_scheme3(const orc3_params* p, Scheme3* sc) {
+  if (!p || p->nx < 1 || p->ny < 1 || p->nz < 1) return -1;
+  if (!(p->sigma > 0) || !(p->D > 0) || !(p->M > 0)) return -1;
+  sc->nx = p->nx;
+  sc->ny = p->ny;
+  sc->nz = p->nz;
+  sc->beta = 3.0 * p->sigma / (4.0 * p->D);  // Eq. 5, as in 2D
+  sc->k = sc->beta * p->D * p->D / 2.0;
+  sc->eps = p->eps;
+  sc->alpha = p->alpha;
+  sc->reg = p->regularization;
+  sc->flags = p->flags;
+  for (int i = 0; i < 15; ++i) sc->s[i] = p->s[i];
+  if (!(p->flags & ORC_S35_EXPLICIT)) {
+    const double sj = 1.0 / (p->M / CS2 + 0.5);  // the j moments carry the flux (after Eq. 38)
+    sc->s[3] = sc->s[5] = sc->s[7] = sj;
+  }
+  for (int i = 1; i < 15; ++i)
+    if (!(sc->s[i] > 0.0 && sc->s[i] < 2.0)) return -1;
+  double m[225], mi[225];
+  for (int r = 0; r < 15; ++r)
+    for (int c = 0; c < 15; ++c) m[r * 15 + c] = m3_row(r, c);
+  invert_n(15, m, mi);
+  for (int r = 0; r < 15; ++r)
+    for (int c = 0; c < 15; ++c) {
+      sc->M[r][c] = m[r * 15 + c];
+      sc->Minv[r][c] = mi[r * 15 + c];
+    }
+  for (int i = 0; i < 15; ++i)
+    for (int j = 0; j < 15; ++j) {
+      double a = 0.0, b = 0.0;
+      for (int q = 0; q < 15; ++q) {
+        a += sc->Minv[i][q] * sc->s[q] * sc->M[q][j];
+        b += sc->Minv[i][q] * (1.0 - sc->s[q] / 2.0) * sc->M[q][j];
+      }
+      sc->A[i][j] = a;
+      sc->B[i][j] = b;
+    }
+  return 0;
+}
+
+inline size_t idx3(const Scheme3& sc, int x, int y, int z) {
+  return (size_t(wrap(z, sc.nz)) * sc.ny + wrap(y, sc.ny)) * sc.nx + wrap(x, sc.nx);
+}
+
+// Eq. 26a in 3D.
+inline void grad3(const Scheme3& sc, const double* chi, int x, int y, int z, double g[3]) {
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < 15; ++i) {
+    const double v = chi[idx3(sc, x + CX3[i], y + CY3[i], z + CZ3[i])];
+    s[0] += W3[i] * CX3[i] * v;
+    s[1] += W3[i] * CY3[i] * v;
+    s[2] += W3[i] * CZ3[i] * v;
+  }
+  for (int d = 0; d < 3; ++d) g[d] = s[d] / CS2;
+}
+
+// Eq. 26b in 3D.
+inline double lap3(const Scheme3& sc, const double* chi, int x, int y, int z) {
+  const double c = chi[idx3(sc, x, y, z)];
+  double s = 0.0;
+  for (int i = 0; i < 15; ++i) s += 2.0 * W3[i] * (chi[idx3(sc, x + CX3[i], y + CY3[i], z + CZ3[i])] - c);
+  return s / CS2;
+}
+
+struct Aniso3 {
+  double gamma, Pg[3], gnorm;
+};
+
+// Eqs. 3, 6 and the projection after Eq. 14, with the n = 0 guard.
+inline Aniso3 anisotropy3(double alpha, const double g[3]) {
+  Aniso3 a;
+  const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  a.gnorm = std::sqrt(g2);
+  if (g2 < GUARD) {
+    a.gamma = 1.0;
+    a.Pg[0] = a.Pg[1] = a.Pg[2] = 0.0;
+    return a;
+  }
+  double n[3], gn[3], s4 = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    n[d] = g[d] / a.gnorm;
+    s4 += n[d] * n[d] * n[d] * n[d];
+    gn[d] = 16.0 * alpha * n[d] * n[d] * n[d];
+  }
+  a.gamma = 1.0 + alpha * (4.0 * s4 - 3.0);  // Eq. 6, d = 3
+  for (int d = 0; d < 3; ++d) {
+    double v = 0.0;
+    for (int e = 0; e < 3; ++e) v += ((d == e ? 1.0 : 0.0) - n[d] * n[e]) * gn[e];  // P = I - n n^T
+    a.Pg[d] = v;
+  }
+  return a;
+}
+
+struct Fields3 {
+  std::vector<double> phi, dx, dy, dz, lap, gamma, Qx, Qy, Qz, w, mua, mub, gx, gy, gz, lap2;
+  explicit Fields3(size_t n)
+      : phi(n), dx(n), dy(n), dz(n), lap(n), gamma(n), Qx(n), Qy(n), Qz(n), w(n), mua(n), mub(n), gx(n),
+        gy(n), gz(n), lap2(n) {}
+};
+
+void compute_fields3(const Scheme3& sc, const double* f, Fields3& F) {
+  const int nx = sc.nx, ny = sc.ny, nz = sc.nz;
+  const size_t N = size_t(nx) * ny * nz;
+  const bool literal_q = sc.flags & ORC_Q_LITERAL, nested = sc.flags & ORC_MU_NESTED;
+#pragma omp parallel for schedule(static)
+  for (long long id = 0; id < (long long)N; ++id) {
+    double s = 0.0;
+    for (int i = 0; i < 15; ++i) s += f[i * N + id];  // Eq. 22
+    F.phi[id] = s;
+  }
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const size_t id = idx3(sc, x, y, z);
+        double g[3];
+        grad3(sc, F.phi.data(), x, y, z, g);
+        F.dx[id] = g[0];
+        F.dy[id] = g[1];
+        F.dz[id] = g[2];
+        F.lap[id] = lap3(sc, F.phi.data(), x, y, z);
+        const Aniso3 a = anisotropy3(sc.alpha, g);
+        F.gamma[id] = a.gamma;
+        const double kq = literal_q ? 1.0 : sc.k;
+        const double iso = nested ? a.gamma : (a.gamma - 1.0);
+        F.Qx[id] = iso * sc.k * g[0] + kq * a.gnorm * a.Pg[0];  // Eq. 15
+        F.Qy[id] = iso * sc.k * g[1] + kq * a.gnorm * a.Pg[1];
+        F.Qz[id] = iso * sc.k * g[2] + kq * a.gnorm * a.Pg[2];
+        const double phi = F.phi[id];
+        const double fb = 4.0 * sc.beta * phi * (phi + 1.0) * (phi - 1.0);
+        F.w[id] = F.lap[id] - fb;
+        F.mua[id] = fb - sc.k * F.lap[id];  // Eq. 16
+      }
+  if (sc.reg == 2) {
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) F.lap2[idx3(sc, x, y, z)] = lap3(sc, F.lap.data(), x, y, z);
+  }
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const size_t id = idx3(sc, x, y, z);
+        double gxq[3], gyq[3], gzq[3];
+        grad3(sc, F.Qx.data(), x, y, z, gxq);
+        grad3(sc, F.Qy.data(), x, y, z, gyq);
+        grad3(sc, F.Qz.data(), x, y, z, gzq);
+        const double divQ = gxq[0] + gyq[1] + gzq[2];
+        const double phi = F.phi[id];
+        const double fb = 4.0 * sc.beta * phi * (phi + 1.0) * (phi - 1.0);
+        const double fp = 4.0 * sc.beta * (3.0 * phi * phi - 1.0);
+        double reg = 0.0;
+        if (sc.reg == 1) reg = sc.eps * (lap3(sc, F.w.data(), x, y, z) - fp * F.w[id]);  // Eq. 13
+        else if (sc.reg == 2) reg = sc.eps * F.lap2[id];                                  // Eq. 12
+        F.mub[id] = nested ? F.gamma[id] * fb - divQ + reg - F.mua[id] : (F.gamma[id] - 1.0) * fb - divQ + reg;
+      }
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const size_t id = idx3(sc, x, y, z);
+        double g[3];
+        grad3(sc, F.mub.data(), x, y, z, g);
+        F.gx[id] = g[0];
+        F.gy[id] = g[1];
+        F.gz[id] = g[2];
+      }
+}
+
+void equilibrium3(double phi, double mua, double feq[15]) {
+  for (int i = 0; i < 15; ++i) feq[i] = W3[i] * mua;  // Eq. 18
+  feq[0] = phi + (W3[0] - 1.0) * mua;
+}
+
+void source3(double gx, double gy, double gz, double F[15]) {
+  for (int i = 0; i < 15; ++i) F[i] = -W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);  // Eq. 19
+}
+
+void collide3(const Scheme3& sc, const double f[15], double phi, double mua, double gx, double gy, double gz,
+              double out[15]) {
+  double feq[15], F[15], neq[15];
+  equilibrium3(phi, mua, feq);
+  source3(gx, gy, gz, F);
+  for (int j = 0; j < 15; ++j) neq[j] = f[j] - feq[j];
+  for (int i = 0; i < 15; ++i) {  // Eq. 17, dt = 1
+    double relax = 0.0, force = 0.0;
+    for (int j = 0; j < 15; ++j) {
+      relax += sc.A[i][j] * neq[j];
+      force += sc.B[i][j] * F[j];
+    }
+    out[i] = f[i] - relax + force;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+void orc3_matrices(double* M225, double* Minv225) {
+  orc3_params p = {};
+  p.nx = p.ny = p.nz = 1;
+  p.M = 0.1;
+  p.sigma = 0.01;
+  p.D = 5.0;
+  for (int i = 0; i < 15; ++i) p.s[i] = 1.0;
+  Scheme3 sc;
+  make_scheme3(&p, &sc);
+  for (int r = 0; r < 15; ++r)
+    for (int c = 0; c < 15; ++c) {
+      if (M225) M225[r * 15 + c] = sc.M[r][c];
+      if (Minv225) Minv225[r * 15 + c] = sc.Minv[r][c];
+    }
+}
+
+void orc3_equilibrium(double phi, double mu_alpha, double feq[15]) { equilibrium3(phi, mu_alpha, feq); }
+
+void orc3_source(double gx, double gy, double gz, double F[15]) { source3(gx, gy, gz, F); }
+
+void orc3_collide_site(const orc3_params* p, const double f[15], double phi, double mu_alpha, double gx,
+                       double gy, double gz, double out[15]) {
+  Scheme3 sc;
+  if (make_scheme3(p, &sc) != 0) {
+    for (int i = 0; i < 15; ++i) out[i] = NAN;
+    return;
+  }
+  collide3(sc, f, phi, mu_alpha, gx, gy, gz, out);
+}
+
+int orc3_init(const orc3_params* p, const double* phi0, double* f) {
+  Scheme3 sc;
+  if (make_scheme3(p, &sc) != 0) return -1;
+  const size_t N = size_t(sc.nx) * sc.ny * sc.nz;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < sc.nz; ++z)
+    for (int y = 0; y < sc.ny; ++y)
+      for (int x = 0; x < sc.nx; ++x) {
+        const size_t id = idx3(sc, x, y, z);
+        const double ph = phi0[id];
+        const double mua = 4.0 * sc.beta * ph * (ph + 1.0) * (ph - 1.0) - sc.k * lap3(sc, phi0, x, y, z);
+        double feq[15];
+        equilibrium3(ph, mua, feq);
+        for (int i = 0; i < 15; ++i) f[i * N + id] = feq[i];
+      }
+  return 0;
+}
+
+int orc3_step(const orc3_params* p, double* f, int64_t nsteps) {
+  Scheme3 sc;
+  if (make_scheme3(p, &sc) != 0) return -1;
+  const int nx = sc.nx, ny = sc.ny, nz = sc.nz;
+  const size_t N = size_t(nx) * ny * nz;
+  Fields3 F(N);
+  std::vector<double> fstar(15 * N);
+  for (int64_t t = 0; t < nsteps; ++t) {
+    compute_fields3(sc, f, F);
+#pragma omp parallel for schedule(static)
+    for (long long id = 0; id < (long long)N; ++id) {
+      double fi[15], fo[15];
+      for (int i = 0; i < 15; ++i) fi[i] = f[i * N + id];
+      collide3(sc, fi, F.phi[id], F.mua[id], F.gx[id], F.gy[id], F.gz[id], fo);
+      for (int i = 0; i < 15; ++i) fstar[i * N + id] = fo[i];
+    }
+    // Streaming, periodic: f_i(x + c_i) = f*_i(x).
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < nz; ++z)
+      for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+          for (int i = 0; i < 15; ++i)
+            f[i * N + idx3(sc, x + CX3[i], y + CY3[i], z + CZ3[i])] = fstar[i * N + idx3(sc, x, y, z)];
+  }
+  return 0;
+}
+
+int orc3_phi(const orc3_params* p, const double* f, double* phi) {
+  Scheme3 sc;
+  if (make_scheme3(p, &sc) != 0) return -1;
+  const size_t N = size_t(sc.nx) * sc.ny * sc.nz;
+  for (size_t id = 0; id < N; ++id) {
+    double s = 0.0;
+    for (int i = 0; i < 15; ++i) s += f[i * N + id];
+    phi[id] = s;
+  }
+  return 0;
+}
+
+double orc3_mass(const orc3_params* p, const double* f) {
+  Scheme3 sc;
+  if (make_scheme3(p, &sc) != 0) return NAN;
+  const size_t N = size_t(sc.nx) * sc.ny * sc.nz;
+  double m = 0.0;
+  for (size_t id = 0; id < N; ++id)
+    for (int i = 0; i < 15; ++i) m += f[i * N + id];
+  return m;
+}
+
+double orc3_energy(const orc3_params* p, const double* f) {
+  Scheme3 sc;
+  if (make_scheme3(p, &sc) != 0) return NAN;
+  const int nx = sc.nx, ny = sc.ny, nz = sc.nz;
+  const size_t N = size_t(nx) * ny * nz;
+  std::vector<double> phi(N), plane(nz);
+  orc3_phi(p, f, phi.data());
+#pragma omp parallel for schedule(static)
+  for (int z = 0; z < nz; ++z) {
+    double acc = 0.0;
+    for (int y = 0; y < ny; ++y)
+      for (int x = 0; x < nx; ++x) {
+        const double ph = phi[idx3(sc, x, y, z)];
+        double g[3];
+        grad3(sc, phi.data(), x, y, z, g);
+        const double lap = lap3(sc, phi.data(), x, y, z);
+        const Aniso3 a = anisotropy3(sc.alpha, g);
+        const double F = sc.beta * (ph - 1.0) * (ph - 1.0) * (ph + 1.0) * (ph + 1.0);  // Eq. 4
+        double e = a.gamma * (0.5 * sc.k * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) + F);  // Eq. 7
+        if (sc.reg == 1) {
+          const double w = lap - 4.0 * sc.beta * ph * (ph + 1.0) * (ph - 1.0);  // Eq. 9
+          e += 0.5 * sc.eps * w * w;
+        } else if (sc.reg == 2) {
+          e += 0.5 * sc.eps * lap * lap;  // Eq. 8
+        }
+        acc += e;
+      }
+    plane[z] = acc;
+  }
+  double E = 0.0;
+  for (int z = 0; z < nz; ++z) E += plane[z];
+  return E;
+}
+
+}  // extern "C"

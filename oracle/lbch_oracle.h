@@ -93,6 +93,38 @@ double orc_energy(const orc_params* p, const double* f);
  * results do not depend on it). Returns the number now in use. */
 int orc_set_threads(int n);
 
+/* ---- 3D: D3Q15 (Eq. 21, Eq. 24), Section 3 with d = 3 ------------------------------
+ * State: 15 planes of nx*ny*nz doubles, plane i first, then z, then y, then x (x
+ * fastest), in the velocity order of Eq. 21a. Readings specific to 3D:
+ *   - Eq. 24 names the moments (rho, e, eps, j_x, q_x, j_y, q_y, j_z, q_z, 3p_xx, p_ww,
+ *     p_xy, p_yz, p_xz, m_xyz) but orders the eight diagonal velocities differently from
+ *     Eq. 21a, and its last row is not orthogonal to j_x; the oracle builds each row as
+ *     the function of c it names, evaluated at the velocities of Eq. 21a (last row
+ *     c_x c_y c_z).
+ *   - s_3 = s_5 = s_7 (the j moments) = 1/(M/c_s^2 + 1/2) unless ORC_S35_EXPLICIT.
+ * Pins: Eq. 21 and Eq. 24 printed values (with the two discrepancies named exactly),
+ * Eq. 27 moment constraints, orthogonality, single-relaxation reduction, mass
+ * conservation, energy decay, continuum linear dispersion along axis, face and body
+ * diagonals, cube rotation equivariance, and a separate NumPy route. */
+typedef struct {
+  int32_t nx, ny, nz;
+  double M, sigma, D, eps, alpha;
+  double s[15];
+  int32_t regularization;
+  uint32_t flags;
+} orc3_params;
+
+void orc3_matrices(double* M225, double* Minv225);
+void orc3_equilibrium(double phi, double mu_alpha, double feq[15]);
+void orc3_source(double gx, double gy, double gz, double F[15]);
+void orc3_collide_site(const orc3_params* p, const double f[15], double phi, double mu_alpha,
+                       double gx, double gy, double gz, double out[15]);
+int orc3_init(const orc3_params* p, const double* phi0, double* f);
+int orc3_step(const orc3_params* p, double* f, int64_t nsteps);
+int orc3_phi(const orc3_params* p, const double* f, double* phi);
+double orc3_mass(const orc3_params* p, const double* f);
+double orc3_energy(const orc3_params* p, const double* f);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,3 +31,18 @@ def moment_matrix():
 
 def parameters():
     return {k: float(v) for k, v in _rows("parameters_eq39.txt")}
+
+
+def lattice3():
+    """(c as (15, 3) int array, w as (15,) float array) from Eq. 21a, 21b."""
+    c, w = [], []
+    for i, (idx, cx, cy, cz, wt) in enumerate(_rows("d3q15_lattice.txt")):
+        assert int(idx) == i
+        c.append((int(cx), int(cy), int(cz)))
+        w.append(float(Fraction(wt)))
+    return np.array(c), np.array(w)
+
+
+def moment_matrix3():
+    """Eq. 24 as printed (15 x 15)."""
+    return np.array([[float(v) for v in r] for r in _rows("d3q15_moment_matrix.txt")])

@@ -1,0 +1,262 @@
+"""Pins of the 3D (D3Q15) oracle against things other than itself: the printed Eq. 21
+and Eq. 24 (with the print's two discrepancies named exactly), Eq. 27 moment
+constraints, orthogonality, the single-relaxation reduction, conservation, energy
+decay, the continuum linear dispersion along the three symmetry directions, cube
+rotation equivariance, and a separately written NumPy route."""
+import math
+
+import numpy as np
+import pytest
+
+import golden_io
+import oracle
+import workloads as W
+
+C3, W3 = golden_io.lattice3()
+M24 = golden_io.moment_matrix3()
+
+
+def P3(nx, ny, nz, **kw):
+    return oracle.Params3(nx, ny, nz, **kw)
+
+
+def droplet3(n, radius, width):
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=float),) * 3, indexing="ij")
+    r = np.sqrt((x - n / 2) ** 2 + (y - n / 2) ** 2 + (z - n / 2) ** 2)
+    return np.tanh((radius - r) / width)
+
+
+# ---------------------------------------------------------------- tables (Eqs. 21, 24)
+
+def test_lattice_tables_match_eq21():
+    feq = oracle.equilibrium3(0.0, 1.0)
+    assert np.array_equal(feq[1:], W3[1:]) and feq[0] == W3[0] - 1.0
+    for axis in range(3):
+        g = [0.0, 0.0, 0.0]
+        g[axis] = 1.0
+        assert np.array_equal(oracle.source3(*g), -W3 * C3[:, axis])
+
+
+def test_moment_matrix_against_printed_eq24():
+    """Rows j_x, j_y, j_z of the print fix which velocity each printed column stands for.
+    Relabelled that way, rows 0..13 of the oracle's M equal the print; the printed last row
+    differs from c_x c_y c_z in exactly two entries and is not orthogonal to j_x."""
+    M, _ = oracle.matrices3()
+    printed_vel = M24[[3, 5, 7]].T.astype(int)  # velocity of each printed column
+    perm = [next(i for i in range(15) if tuple(C3[i]) == tuple(v)) for v in printed_vel]
+    assert sorted(perm) == list(range(15))
+    relabelled = M[:, perm]
+    assert np.array_equal(relabelled[:14], M24[:14])
+    diff = np.nonzero(relabelled[14] != M24[14])[0]
+    assert list(diff) == [11, 12]
+    assert M24[14] @ M24[3] != 0  # the printed row is not orthogonal to j_x
+    assert np.array_equal(M[14], C3[:, 0] * C3[:, 1] * C3[:, 2])
+
+
+def test_moment_constraints_eq27_3d():
+    assert math.isclose(W3.sum(), 1.0, abs_tol=1e-15)
+    assert np.abs(W3 @ C3).max() <= 1e-16
+    assert np.abs(np.einsum("i,ia,ib->ab", W3, C3, C3) - np.eye(3) / 3).max() <= 1e-16
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        phi, mua, gx, gy, gz = rng.uniform(-1, 1, 5)
+        feq = oracle.equilibrium3(phi, mua)
+        F = oracle.source3(gx, gy, gz)
+        assert abs(feq.sum() - phi) <= 4e-16
+        assert np.abs(feq @ C3).max() <= 1e-16
+        assert np.abs(np.einsum("i,ia,ib->ab", feq, C3, C3) - mua * np.eye(3) / 3).max() <= 1e-15
+        assert abs(F.sum()) <= 1e-16
+        assert np.abs(F @ C3 + np.array([gx, gy, gz]) / 3).max() <= 1e-16
+
+
+def test_matrix_orthogonal_and_closed_forms_3d():
+    M, Mi = oracle.matrices3()
+    G = M @ M.T
+    assert np.array_equal(G, np.diag(np.diag(G)))
+    assert np.array_equal(np.diag(G), [15, 18, 360, 10, 40, 10, 40, 10, 40, 12, 4, 8, 8, 8, 8])
+    assert np.abs(Mi @ M - np.eye(15)).max() <= 1e-15
+    rng = np.random.default_rng(2)
+    phi, mua, gx, gy, gz = rng.uniform(-1, 1, 5)
+    meq = M @ oracle.equilibrium3(phi, mua)
+    want = np.zeros(15)
+    # e = c^2 - 2 and eps = (15 c^4 - 55 c^2 + 32)/2 summed against Eq. 18 with Eq. 21b weights.
+    want[0], want[1], want[2] = phi, -2 * phi + mua, 16 * phi - 15 * mua
+    assert np.abs(meq - want).max() <= 1e-14
+    Fm = M @ oracle.source3(gx, gy, gz)
+    want = np.zeros(15)
+    want[[3, 4, 5, 6, 7, 8]] = [-gx / 3, 7 * gx / 9, -gy / 3, 7 * gy / 9, -gz / 3, 7 * gz / 9]
+    assert np.abs(Fm - want).max() <= 1e-15
+
+
+@pytest.mark.parametrize("s", [0.7, 1.0, 1.6])
+def test_srt_reduction_3d(s):
+    p = P3(4, 4, 4, s=[s] * 15, flags=oracle.S35_EXPLICIT)
+    rng = np.random.default_rng(3)
+    f = rng.uniform(-0.1, 0.5, 15)
+    phi = f.sum()
+    mua, gx, gy, gz = rng.uniform(-0.1, 0.1, 4)
+    feq = W3 * mua
+    feq[0] = phi + (W3[0] - 1) * mua
+    F = -W3 * (C3 @ np.array([gx, gy, gz]))
+    bgk = f - s * (f - feq) + (1 - s / 2) * F
+    assert np.abs(oracle.collide_site3(p, f, phi, mua, gx, gy, gz) - bgk).max() <= 1e-14
+
+
+# ---------------------------------------------------------------- conservation, energy
+
+def test_mass_and_energy_droplet_3d():
+    n = 24
+    p = P3(n, n, n, alpha=0.3)
+    f = oracle.init3(p, droplet3(n, 8.0, 2.5))
+    # Exactly rounded sums: the plain sequential sum of 2e5 values is itself off by ~1e-10.
+    m0 = math.fsum(f.ravel())
+    E = [oracle.energy3(p, f)]
+    for _ in range(20):
+        f = oracle.step3(p, f, 10)
+        E.append(oracle.energy3(p, f))
+    assert abs(math.fsum(f.ravel()) - m0) <= 1e-13 * abs(m0)
+    E = np.array(E)
+    assert np.all(np.diff(E) <= 1e-12 * np.abs(E[:-1]))
+    assert E[-1] < E[0]
+
+
+# ---------------------------------------------------------------- linear dispersion
+
+def _rate3(p, m, phi0, T=300):
+    n = p.nx
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=float),) * 3, indexing="ij")
+    u = 2 * np.pi * (m[0] * x + m[1] * y + m[2] * z) / n + np.pi * max(m) / n
+    f = oracle.init3(p, phi0 + 1e-4 * np.cos(u))
+    zz = np.exp(-1j * u)
+
+    def amp(g):
+        return abs(((oracle.phi3(p, g) - phi0) * zz).sum())
+
+    f1 = oracle.step3(p, f, T)
+    f2 = oracle.step3(p, f1, T)
+    return math.log(amp(f2) / amp(f1)) / T
+
+
+def _continuum_rate3(n, mode, gamma_factor, phi0, alpha, eps=0.03):
+    """lambda = -M q^2 [gamma (f'(phi0) + k q^2) + eps (q^2 + f'(phi0))^2] with
+    gamma = 1 + alpha (4 sum n^4 - 3): 1 + alpha, 1 - alpha, 1 - 5 alpha/3 along the
+    axis, face and body diagonals, where P grad_n gamma = 0 (Eqs. 6, 10, 13, 15, 16)."""
+    beta, k = 3 * 0.01 / 20.0, 3 * 0.01 * 5.0 / 8.0
+    q2 = (2 * np.pi / n) ** 2 * sum(v * v for v in mode)
+    fp = 4 * beta * (3 * phi0 ** 2 - 1)
+    gam = 1 + alpha * gamma_factor
+    return -0.1 * q2 * (gam * (fp + k * q2) + eps * (q2 + fp) ** 2)
+
+
+@pytest.mark.parametrize("phi0", [-1.0, 0.0])
+def test_linear_dispersion_3d_axis(phi0):
+    n, alpha = 32, 0.3
+    want = _continuum_rate3(n, (1, 0, 0), 1.0, phi0, alpha)
+    lam = _rate3(P3(n, n, n, alpha=alpha), (1, 0, 0), phi0)
+    assert abs(lam - want) <= 1e-2 * abs(want), (lam, want)
+
+
+@pytest.mark.parametrize("mode,gamma_factor", [((1, 1, 0), -1.0), ((1, 1, 1), -5.0 / 3.0)])
+def test_linear_dispersion_3d_diagonals(mode, gamma_factor):
+    """Along the face and body diagonals D3Q15's lattice error is a few percent at
+    q = 2 pi sqrt(2|3)/32 (measured 1.1% and 3.3%, shrinking with n); a wrong gamma
+    (sign of alpha: 40-200%) or a dropped term falls far outside 6%."""
+    n, alpha = 32, 0.3
+    want = _continuum_rate3(n, mode, gamma_factor, -1.0, alpha)
+    lam = _rate3(P3(n, n, n, alpha=alpha), mode, -1.0)
+    assert abs(lam - want) <= 6e-2 * abs(want), (lam, want)
+
+
+@pytest.mark.parametrize("eps", [0.03, 0.3])
+def test_linear_dispersion_3d_willmore_visible(eps):
+    # n = 16 along the axis: with eps = 0.3 the Willmore term is ~30% of lambda.
+    n, alpha = 16, 0.3
+    want = _continuum_rate3(n, (1, 0, 0), 1.0, -1.0, alpha, eps=eps)
+    lam = _rate3(P3(n, n, n, alpha=alpha, eps=eps), (1, 0, 0), -1.0)
+    assert abs(lam - want) <= 3e-2 * abs(want), (lam, want)
+    assert abs(_continuum_rate3(n, (1, 0, 0), 1.0, -1.0, alpha, eps=0.0) - want) > 0.2 * abs(want) or eps < 0.1
+
+
+# ---------------------------------------------------------------- symmetry
+
+def _rot_z(a):
+    """a'(x, y, z) = a(y, -x, z): rotation by +90 degrees about z (arrays indexed [z, y, x])."""
+    n = a.shape[-1]
+    i = np.arange(n)
+    return a[:, (-i[None, :]) % n, i[:, None]]
+
+
+def _rot_state(f):
+    perm = []
+    for j in range(15):  # new population j comes from old i with R c_i = c_j, R(x, y, z) = (-y, x, z)
+        cx, cy, cz = C3[j]
+        src = (cy, -cx, cz)
+        perm.append(next(i for i in range(15) if tuple(C3[i]) == src))
+    return np.stack([_rot_z(f[perm[j]]) for j in range(15)])
+
+
+def test_rotation_equivariance_3d():
+    n = 12
+    p = P3(n, n, n, alpha=0.4)
+    rng = np.random.default_rng(5)
+    phi0 = rng.uniform(-0.5, 0.5, (n, n, n))
+    f0 = oracle.init3(p, phi0)
+    ref = oracle.step3(p, f0, 30)
+    rot = oracle.step3(p, _rot_state(f0), 30)
+    assert np.abs(rot - _rot_state(ref)).max() <= 1e-13
+
+
+# ---------------------------------------------------------------- second route
+
+def _numpy_step3(f, alpha, M=0.1, sigma=0.01, D=5.0, eps=0.03):
+    beta, k = 3 * sigma / (4 * D), 3 * sigma * D / 8
+    at = lambda a, c: np.roll(a, shift=(-c[2], -c[1], -c[0]), axis=(0, 1, 2))  # a(x + c)
+    grad = lambda a: [3 * sum(W3[i] * C3[i, d] * at(a, C3[i]) for i in range(15)) for d in range(3)]
+    lap = lambda a: 6 * sum(W3[i] * (at(a, C3[i]) - a) for i in range(15))
+    phi = f.sum(0)
+    g = np.stack(grad(phi))
+    L = lap(phi)
+    g2 = (g * g).sum(0)
+    ok = g2 >= 1e-24
+    nrm = np.sqrt(g2)
+    n = np.where(ok, g / np.where(ok, nrm, 1.0), 0.0)
+    gamma = np.where(ok, 1 + alpha * (4 * (n ** 4).sum(0) - 3), 1.0)
+    dg = 16 * alpha * n ** 3
+    pg = dg - n * (n * dg).sum(0)
+    Q = (gamma - 1) * k * g + k * nrm * pg
+    fb = 4 * beta * phi * (phi ** 2 - 1)
+    fp = 4 * beta * (3 * phi ** 2 - 1)
+    w = L - fb
+    mua = fb - k * L
+    divq = sum(grad(Q[d])[d] for d in range(3))
+    mub = (gamma - 1) * fb - divq + eps * (lap(w) - fp * w)
+    G = np.stack(grad(mub))
+    feq = W3[:, None, None, None] * mua[None]
+    feq[0] += phi - mua
+    F = -W3[:, None, None, None] * np.einsum("id,d...->i...", C3.astype(float), G)
+    # Eq. 24 relabelled to Eq. 21a's velocities, last row c_x c_y c_z (see the test above).
+    vel = M24[[3, 5, 7]].T.astype(int)
+    perm = [next(i for i in range(15) if tuple(C3[i]) == tuple(v)) for v in vel]
+    Mm = np.zeros((15, 15))
+    Mm[:, perm] = M24
+    Mm[14] = C3[:, 0] * C3[:, 1] * C3[:, 2]
+    s = np.ones(15)
+    s[[3, 5, 7]] = 1 / (3 * M + 0.5)
+    Mi = np.linalg.inv(Mm)
+    post = f - np.einsum("ij,j...->i...", Mi @ np.diag(s) @ Mm, f - feq) + \
+        np.einsum("ij,j...->i...", Mi @ np.diag(1 - s / 2) @ Mm, F)
+    return np.stack([at(post[i], -C3[i]) for i in range(15)])
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.35])
+def test_numpy_second_route_3d(alpha):
+    nx, ny, nz = 6, 5, 4
+    rng = np.random.default_rng(9)
+    phi0 = rng.uniform(-0.6, 0.6, (nz, ny, nx))
+    p = P3(nx, ny, nz, alpha=alpha)
+    f = oracle.init3(p, phi0)
+    g = f.copy()
+    for _ in range(8):
+        g = _numpy_step3(g, alpha)
+    f = oracle.step3(p, f, 8)
+    assert np.abs(f - g).max() <= 1e-13
