@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-field parameter-sweep batch")
     ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--no-3d", action="store_true", help="skip the D3Q15 measurement")
     ap.add_argument("--storage", choices=["f32", "bf16_dev", "f16_dev"], default="f32",
                     help="population storage of the main timed line")
     return ap.parse_args()
@@ -259,6 +260,28 @@ def run_batch_sweep(lbch, torch, steps: int, count: int = 512, seed: int = 0):
     return out
 
 
+def run_3d(lbch, torch, n: int, steps: int):
+    """The D3Q15 path on an n^3 periodic spinodal field (alpha 0.3, noise 0.05), FP32."""
+    rng = np.random.default_rng(SEED)
+    s = lbch.Solver3(lbch.make_params3(n, n, n, alpha=ALPHA))
+    s.init_field(rng.uniform(-NOISE, NOISE, (n, n, n)))
+    s.step(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    s.close()
+    mlups = steps * n ** 3 / sec / 1e6
+    peak_bw = measured_peaks()[0]
+    return {"value": mlups, "unit": "MLUPS", "workload": f"spinodal-{n}^3 D3Q15", "steps": steps,
+            "ms_per_step": sec / steps * 1e3, "algorithmic_bytes_per_lu": 120,
+            "roofline_frac_algorithmic": 120 * mlups * 1e6 / (peak_bw * 1e9),
+            "launch": "four kernels per step (phi; anisotropy; mu_beta; collide and store)"}
+
+
 def cpu_oracle_rate(target_s: float = 12.0, n_sample: int = 2048):
     """The FP64 oracle, as it stands, on the host cores: MLUPS on an n_sample^2 spinodal
     sample of the workload (alpha 0.3, noise 0.05, seed 0)."""
@@ -393,6 +416,11 @@ def main():
         batch["roofline_frac"] = 72 * batch["value"] * 1e6 / (peak_bw * 1e9)
         batch["value"] = job_rate(world, batch["value"], 1.0)  # replicas: rates add
 
+    d3 = None
+    if not args.no_3d:
+        d3 = run_3d(lbch, torch, 256, 50)
+        d3["paper_100"] = run_3d(lbch, torch, 100, 200)["value"]
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate()
@@ -411,6 +439,7 @@ def main():
             "kernel_only_mlups": world * n * n / per_launch / 1e6,
             "variants": variants,
             "batch_sweep": batch,
+            "d3q15": d3,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),

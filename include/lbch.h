@@ -21,7 +21,8 @@
  *     mu_beta = (gamma-1) f - div((gamma-1) k grad phi + k|grad phi| P grad_n gamma)
  *               + eps (lap w - f'(phi) w),  w = lap phi - f(phi).
  *     LBCH_MU_NESTED takes mu - mu_alpha with the full Q instead.
- *   - Where |grad phi|^2 < 1e-24 a node takes n = 0, gamma = 1, P grad_n gamma = 0.
+ *   - Where |grad phi|^2 < 1e-12 a node takes n = 0, gamma = 1, P grad_n gamma = 0
+ *     (FP32 rounding of a zero gradient stays below this, so it never picks a direction).
  *   - grad_n gamma = 16 alpha (n_1^3, n_2^3), the gradient of Eq. 6 in R^2.
  *   - s_3 = s_5 = 1/(M/c_s^2 + 1/2) (from M = c_s^2 (1/s_{3,5} - 1/2) dt, after
  *     Eq. 38) unless LBCH_S35_EXPLICIT; the other rates are inputs (default 1).

@@ -25,7 +25,8 @@
 //     isotropic reduction stated after Eq. 16). ORC_MU_NESTED takes mu - mu_alpha
 //     with the full Q and nested Eq. 26a stencils instead.
 //   - n = grad phi/|grad phi| is undefined where grad phi = 0: where
-//     |grad phi|^2 < 1e-24 the node takes n = 0, gamma = 1, P grad_n gamma = 0.
+//     |grad phi|^2 < 1e-12 the node takes n = 0, gamma = 1, P grad_n gamma = 0
+//     (a threshold an FP32 gradient can resolve: its rounding noise stays below 1e-14).
 //   - grad_n gamma is the R^2 gradient of Eq. 6 in n: 16 alpha (n_1^3, n_2^3).
 //   - Only s_3 = s_5 is fixed (by M = c_s^2 (1/s_3 - 1/2) dt after Eq. 38);
 //     the other rates are inputs.
@@ -51,7 +52,7 @@ const double WGT[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                        1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 // c_s = c / sqrt(3), c = dx/dt = 1 (text after Eq. 21); dt = dx = 1.
 const double CS2 = 1.0 / 3.0;
-const double GUARD = 1e-24;
+const double GUARD = 1e-12;
 
 // Eq. 23.
 const double MROWS[9][9] = {

@@ -9,8 +9,8 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "liblbch.so")
 SOURCES = [os.path.join(HERE, "csrc", "lbch_api.cu")]
 DEPENDS = SOURCES + [os.path.join(HERE, "csrc", n) for n in
-                     ("lbch_step.cuh", "lbch_aux.cuh", "lbch_lattice.cuh", "lbch_batch.cuh")] + [
-    os.path.join(ROOT, "include", "lbch.h")]
+                     ("lbch_step.cuh", "lbch_aux.cuh", "lbch_lattice.cuh", "lbch_batch.cuh", "lbch3.cuh")] + [
+    os.path.join(ROOT, "include", "lbch.h"), os.path.join(ROOT, "include", "lbch3.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]

@@ -12,6 +12,7 @@
 #include <new>
 
 #include "lbch.h"
+#include "lbch3.h"
 #include "lbch_aux.cuh"
 #include "lbch_step.cuh"
 
@@ -635,3 +636,4 @@ void lbch_destroy(lbch_ctx* c) { delete c; }
 }  // extern "C"
 
 #include "lbch_batch.cuh"
+#include "lbch3.cuh"

@@ -255,7 +255,7 @@ struct EnergyConsts {
 };
 
 // Free-energy density (Eq. 7 with Eq. 9 or Eq. 8; stencils of Eq. 26; the n = 0,
-// gamma = 1 guard where |grad phi|^2 < 1e-24) in FP32, block sums in FP64.
+// gamma = 1 guard where |grad phi|^2 < 1e-12) in FP32, block sums in FP64.
 __global__ void energy_kernel(const float* __restrict__ phi, Grid g, EnergyConsts c,
                               double* __restrict__ partial) {
   __shared__ double sh[AUX_THREADS / 32];
@@ -276,7 +276,7 @@ __global__ void energy_kernel(const float* __restrict__ phi, Grid g, EnergyConst
                         p0 * (10.0f / 3.0f);
       const float g2 = fmaf(gx, gx, gy * gy);
       float gamma = 1.0f;
-      if (g2 >= 1e-24f) {
+      if (g2 >= 1e-12f) {
         const float rs = rsqrtf(g2);
         const float n1 = gx * rs, n2 = gy * rs;
         const float n1s = n1 * n1, n2s = n2 * n2;

@@ -201,7 +201,7 @@ __device__ __forceinline__ void pointwise(const StepArgs& a, const Field& fd, fl
                                           float lap, float& Qx, float& Qy, float& w, float& A,
                                           float& mua) {
   const float g2 = fmaf(dx, dx, dy * dy);
-  const bool ok = g2 >= 1e-24f;
+  const bool ok = g2 >= 1e-12f;  // n = 0, gamma = 1 below this
   const float rs = rsqrtf(ok ? g2 : 1.0f);
   const float n1 = dx * rs, n2 = dy * rs;  // Eq. 2
   const float n1s = n1 * n1, n2s = n2 * n2;

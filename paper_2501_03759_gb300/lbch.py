@@ -47,6 +47,29 @@ class lbch_params(ctypes.Structure):
     ]
 
 
+class lbch3_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("M", ctypes.c_double), ("sigma", ctypes.c_double), ("D", ctypes.c_double),
+        ("eps", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("s", ctypes.c_double * 15),
+        ("regularization", ctypes.c_int32), ("flags", ctypes.c_uint32),
+    ]
+
+
+def make_params3(nx: int, ny: int, nz: int, *, M=0.1, sigma=0.01, D=5.0, eps=0.03, alpha=0.0, s=None,
+                 regularization=REG_WILLMORE, flags=0) -> lbch3_params:
+    """lbch3_params (D3Q15) with the defaults of Eq. 39 and Willmore G."""
+    p = lbch3_params()
+    p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+    p.M, p.sigma, p.D, p.eps, p.alpha = float(M), float(sigma), float(D), float(eps), float(alpha)
+    rates = [1.0] * 15 if s is None else list(s)
+    for i in range(15):
+        p.s[i] = float(rates[i])
+    p.regularization, p.flags = int(regularization), int(flags)
+    return p
+
+
 def make_params(nx: int, ny: int, *, M=0.1, sigma=0.01, D=5.0, eps=0.03, alpha=0.0, s=None,
                 storage=STORE_F32, regularization=REG_WILLMORE, flags=0) -> lbch_params:
     """lbch_params with the defaults of Eq. 39 (M, eps, D, sigma) and Willmore G."""
@@ -126,6 +149,20 @@ def load():
         lib.lbch_batch_last_error.restype = ctypes.c_char_p
         lib.lbch_batch_destroy.argtypes = [vp]
         lib.lbch_batch_destroy.restype = None
+        P3 = ctypes.POINTER(lbch3_params)
+        lib.lbch3_workspace_bytes.argtypes = [P3]
+        lib.lbch3_workspace_bytes.restype = ctypes.c_size_t
+        lib.lbch3_create.argtypes = [P3, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+        lib.lbch3_create.restype = ctypes.c_int
+        for name in ("lbch3_init_field", "lbch3_get_field", "lbch3_mass", "lbch3_free_energy"):
+            getattr(lib, name).argtypes = [vp, dp]
+            getattr(lib, name).restype = ctypes.c_int
+        lib.lbch3_step.argtypes = [vp, ctypes.c_int64]
+        lib.lbch3_step.restype = ctypes.c_int
+        lib.lbch3_last_error.argtypes = [vp]
+        lib.lbch3_last_error.restype = ctypes.c_char_p
+        lib.lbch3_destroy.argtypes = [vp]
+        lib.lbch3_destroy.restype = None
         _lib = lib
         return lib
 
@@ -435,6 +472,116 @@ class Batch:
         if getattr(self, "handle", None):
             lbch_batch_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- 3D (C names)
+
+def _check3(c, status: int, what: str):
+    if status != OK:
+        detail = (load().lbch3_last_error(c) or b"").decode(errors="replace") if c else ""
+        raise LbchError(status, what, detail)
+
+
+def lbch3_workspace_bytes(p: lbch3_params) -> int:
+    return int(load().lbch3_workspace_bytes(ctypes.byref(p)))
+
+
+def lbch3_create(p: lbch3_params, d_workspace: int, nbytes: int, cuda_stream):
+    c = ctypes.c_void_p()
+    st = load().lbch3_create(ctypes.byref(p), ctypes.c_void_p(int(d_workspace)), int(nbytes),
+                             ctypes.c_void_p(int(cuda_stream or 0)), ctypes.byref(c))
+    _check3(None, st, "lbch3_create")
+    return c
+
+
+def lbch3_init_field(c, phi0) -> None:
+    _check3(c, load().lbch3_init_field(c, _host_ptr(phi0)), "lbch3_init_field")
+
+
+def lbch3_step(c, n: int) -> None:
+    _check3(c, load().lbch3_step(c, int(n)), "lbch3_step")
+
+
+def lbch3_get_field(c, out: np.ndarray) -> np.ndarray:
+    _check3(c, load().lbch3_get_field(c, _host_ptr(out)), "lbch3_get_field")
+    return out
+
+
+def lbch3_mass(c) -> float:
+    v = ctypes.c_double()
+    _check3(c, load().lbch3_mass(c, ctypes.byref(v)), "lbch3_mass")
+    return v.value
+
+
+def lbch3_free_energy(c) -> float:
+    v = ctypes.c_double()
+    _check3(c, load().lbch3_free_energy(c, ctypes.byref(v)), "lbch3_free_energy")
+    return v.value
+
+
+def lbch3_last_error(c) -> str:
+    return (load().lbch3_last_error(c) or b"").decode(errors="replace")
+
+
+def lbch3_destroy(c) -> None:
+    if c:
+        load().lbch3_destroy(c)
+
+
+class Solver3:
+    """Owns a 3D (D3Q15) context and its workspace; fields are (nz, ny, nx) float64 arrays."""
+
+    def __init__(self, params: lbch3_params, device=None, stream=None):
+        import torch
+
+        self.params = params
+        self.shape = (params.nz, params.ny, params.nx)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        nbytes = lbch3_workspace_bytes(params)
+        if nbytes == 0:
+            raise LbchError(EINVAL, "lbch3_workspace_bytes", "invalid parameters")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.ctx = lbch3_create(params, self.workspace.data_ptr(), nbytes, self.stream.cuda_stream)
+
+    def _on_device(self):
+        import torch
+        return torch.cuda.device(self.device)
+
+    def init_field(self, phi0) -> None:
+        a = _as_host_f64(phi0, int(np.prod(self.shape)), "phi0")
+        with self._on_device():
+            lbch3_init_field(self.ctx, a)
+
+    def step(self, n: int) -> None:
+        with self._on_device():
+            lbch3_step(self.ctx, n)
+
+    def field(self) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float64)
+        with self._on_device():
+            lbch3_get_field(self.ctx, out)
+        return out
+
+    def mass(self) -> float:
+        with self._on_device():
+            return lbch3_mass(self.ctx)
+
+    def free_energy(self) -> float:
+        with self._on_device():
+            return lbch3_free_energy(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            lbch3_destroy(self.ctx)
+            self.ctx = None
 
     def __del__(self):
         try:

@@ -5,7 +5,7 @@ idioms: whole-array np.roll shifts, dense 9x9 operators from numpy.linalg.inv,
 einsum collisions). It takes its lattice tables from the golden fixtures of
 Eqs. 20 and 23 rather than from the oracle. Readings match the oracle's defaults:
 k on the second term of Eq. 15, split mu_beta, n = 0 and gamma = 1 where
-|grad phi|^2 < 1e-24, Willmore regularisation.
+|grad phi|^2 < 1e-12, Willmore regularisation.
 """
 import numpy as np
 
@@ -39,7 +39,7 @@ def step(f, M=0.1, sigma=0.01, D=5.0, eps=0.03, alpha=0.0, s=None):
     px, py = grad(phi)
     L = lap(phi)
     g2 = px * px + py * py
-    ok = g2 >= 1e-24
+    ok = g2 >= 1e-12
     nrm = np.sqrt(g2)
     safe = np.where(ok, nrm, 1.0)
     n = np.stack([np.where(ok, px / safe, 0.0), np.where(ok, py / safe, 0.0)])

@@ -77,3 +77,20 @@ def test_batch_writes_stay_in_workspace():
     finally:
         lbch.lbch_batch_destroy(b)
     assert bands_intact(buf, nbytes)
+
+
+def test_3d_context_writes_stay_in_workspace():
+    nx, ny, nz = 13, 11, 9
+    p = lbch.make_params3(nx, ny, nz, alpha=0.3)
+    nbytes = lbch.lbch3_workspace_bytes(p)
+    buf, ptr = guarded(nbytes)
+    ctx = lbch.lbch3_create(p, ptr, nbytes, torch.cuda.current_stream().cuda_stream)
+    try:
+        lbch.lbch3_init_field(ctx, np.ascontiguousarray(np.random.default_rng(1).uniform(-0.5, 0.5, (nz, ny, nx))))
+        lbch.lbch3_step(ctx, 7)
+        lbch.lbch3_mass(ctx)
+        lbch.lbch3_free_energy(ctx)
+        lbch.lbch3_get_field(ctx, np.empty((nz, ny, nx)))
+    finally:
+        lbch.lbch3_destroy(ctx)
+    assert bands_intact(buf, nbytes)

@@ -126,7 +126,7 @@ def _rate3(p, m, phi0, T=300):
     n = p.nx
     z, y, x = np.meshgrid(*(np.arange(n, dtype=float),) * 3, indexing="ij")
     u = 2 * np.pi * (m[0] * x + m[1] * y + m[2] * z) / n + np.pi * max(m) / n
-    f = oracle.init3(p, phi0 + 1e-4 * np.cos(u))
+    f = oracle.init3(p, phi0 + 1e-3 * np.cos(u))  # linear, and |grad phi|^2 > 1e-12 at every node
     zz = np.exp(-1j * u)
 
     def amp(g):
@@ -217,7 +217,7 @@ def _numpy_step3(f, alpha, M=0.1, sigma=0.01, D=5.0, eps=0.03):
     g = np.stack(grad(phi))
     L = lap(phi)
     g2 = (g * g).sum(0)
-    ok = g2 >= 1e-24
+    ok = g2 >= 1e-12
     nrm = np.sqrt(g2)
     n = np.where(ok, g / np.where(ok, nrm, 1.0), 0.0)
     gamma = np.where(ok, 1 + alpha * (4 * (n ** 4).sum(0) - 3), 1.0)
