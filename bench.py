@@ -279,7 +279,7 @@ def run_3d(lbch, torch, n: int, steps: int):
     return {"value": mlups, "unit": "MLUPS", "workload": f"spinodal-{n}^3 D3Q15", "steps": steps,
             "ms_per_step": sec / steps * 1e3, "algorithmic_bytes_per_lu": 120,
             "roofline_frac_algorithmic": 120 * mlups * 1e6 / (peak_bw * 1e9),
-            "launch": "four kernels per step (phi; anisotropy; mu_beta; collide and store)"}
+            "launch": "three kernels per step (phi; mu_alpha and mu_beta by a z-sweep; collide and store)"}
 
 
 def cpu_oracle_rate(target_s: float = 12.0, n_sample: int = 2048):

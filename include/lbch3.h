@@ -33,8 +33,8 @@ typedef struct {
   uint32_t flags;         /* LBCH_Q_LITERAL | LBCH_MU_NESTED | LBCH_S35_EXPLICIT (s_3, s_5, s_7) */
 } lbch3_params;
 
-/* Device workspace (two population buffers, one FP32 phi plane, six intermediate FP32
- * planes, one FP64 staging plane, a reduction area); 0 for invalid parameters. */
+/* Device workspace (two population buffers; FP32 planes of phi, mu_alpha and mu_beta;
+ * one FP64 staging plane; a reduction area); 0 for invalid parameters. */
 size_t lbch3_workspace_bytes(const lbch3_params* p);
 
 /* Creates a 3D context on the current device; same rules as lbch_create. */
@@ -45,7 +45,7 @@ lbch_status lbch3_create(const lbch3_params* p, void* d_workspace, size_t bytes,
  * Synchronises. LBCH_ENONFINITE if phi0 holds NaN/Inf. */
 lbch_status lbch3_init_field(lbch3_ctx* c, const double* h_phi0);
 
-/* Advances n >= 0 time steps (four kernel launches per step); asynchronous. */
+/* Advances n >= 0 time steps (three kernel launches per step); asynchronous. */
 lbch_status lbch3_step(lbch3_ctx* c, int64_t n);
 
 /* phi = sum_i f_i to h_phi (nx*ny*nz doubles). Synchronises. */
