@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-field parameter-sweep batch")
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--no-3d", action="store_true", help="skip the D3Q15 measurement")
+    ap.add_argument("--n3", type=int, default=256, help="edge of the D3Q15 spinodal cube (default 256)")
     ap.add_argument("--storage", choices=["f32", "bf16_dev", "f16_dev"], default="f32",
                     help="population storage of the main timed line")
     return ap.parse_args()
@@ -418,7 +419,7 @@ def main():
 
     d3 = None
     if not args.no_3d:
-        d3 = run_3d(lbch, torch, 256, 50)
+        d3 = run_3d(lbch, torch, args.n3, 50)
         d3["paper_100"] = run_3d(lbch, torch, 100, 200)["value"]
 
     cpu = None

@@ -109,6 +109,14 @@ lbch_status lbch_create(const lbch_params* p, void* d_workspace, size_t bytes,
  * Synchronises the stream. LBCH_ENONFINITE (state left unset) if phi0 holds NaN/Inf. */
 lbch_status lbch_init_field(lbch_ctx* ctx, const double* h_phi0);
 
+/* lbch_init_field from a device field: h_phi0 replaced by d_phi0, nx*ny FP32 values in
+ * device memory (x fastest). Asynchronous; it does not check for NaN/Inf. */
+lbch_status lbch_init_field_device(lbch_ctx* ctx, const float* d_phi0);
+
+/* Writes phi(x, t) = sum_i f_i(x, t) as FP32 to d_phi (nx*ny values, device memory).
+ * Asynchronous. */
+lbch_status lbch_get_phi_device(lbch_ctx* ctx, float* d_phi);
+
 /* Advances the state n >= 0 time steps of Eq. 17. Asynchronous: enqueues n kernel
  * launches on the stream and returns. LBCH_EINVAL before any init/set_state. */
 lbch_status lbch_step(lbch_ctx* ctx, int64_t n);
@@ -175,6 +183,8 @@ lbch_status lbch_batch_step(lbch_batch* b, int64_t n);
 /* lbch_get_field, lbch_mass and lbch_free_energy for field i; each synchronises. The
  * fields share one scratch area, so calls on one batch must not overlap. */
 lbch_status lbch_batch_get_field(lbch_batch* b, int32_t i, double* h_phi);
+/* lbch_get_phi_device for field i (asynchronous, on the batch's stream). */
+lbch_status lbch_batch_get_phi_device(lbch_batch* b, int32_t i, float* d_phi);
 lbch_status lbch_batch_mass(lbch_batch* b, int32_t i, double* out);
 lbch_status lbch_batch_free_energy(lbch_batch* b, int32_t i, double* out);
 

@@ -1,0 +1,123 @@
+/*
+ * lbnop: a learned leap for the anisotropic Cahn-Hilliard LBM of lbch.h.
+ *
+ * A periodic convolutional U-Net maps phi(t) on an H x W field to phi(t + K), K lattice
+ * steps later (the surrogate is not part of arXiv 2501.03759; the scheme of its Section 3
+ * generates its training data and judges it). The library holds the network, runs it
+ * forward, trains it (mean squared error, Adam), and alternates leaps with steps of an
+ * lbch context.
+ *
+ * Network (the flat parameter layout below follows this table, in this order):
+ *   phi (H x W, FP32) -> 4 x 4 space-to-depth -> 16 channels at level 0 (H/4 x W/4)
+ *   layer  c_in c_out level activation
+ *   e0a      16   32   0   SiLU  (its pre-activation also gets alpha v, alpha of Eq. 6)
+ *   e0b      32   32   0   SiLU  -> h0
+ *   e1a      32   64   1   SiLU  (input: 2 x 2 average pool of h0)
+ *   e1b      64   64   1   SiLU  -> h1
+ *   e2a      64   96   2   SiLU  (input: pool of h1)
+ *   e2b      96   96   2   SiLU  -> h2
+ *   m3a      96   96   3   SiLU  (input: pool of h2)
+ *   m3b      96   96   3   SiLU  -> h3
+ *   d2a      96   96   2   SiLU  (input: nearest 2x upsampling of h3, plus h2)
+ *   d2b      96   64   2   none
+ *   d1a      64   64   1   SiLU  (input: upsampled d2b output, plus h1)
+ *   d1b      64   32   1   none
+ *   d0a      32   32   0   SiLU  (input: upsampled d1b output, plus h0)
+ *   out      32   16   0   none  -> 4 x 4 depth-to-space -> D (H x W)
+ *   phi_out = phi + scale (D - mean D)  (mean over the field, so mass is conserved)
+ * Every layer is a 3 x 3 cross-correlation with periodic wrap plus a bias:
+ *   z(p) = sum_{(dy, dx) in {-1,0,1}^2} W[3 (dy + 1) + (dx + 1)] x(p + (dy, dx)) + b.
+ * Flat parameters (FP32, 581,520 values): for each layer in table order, W as
+ * [9][c_out][c_in], then b [c_out]; after e0a's bias, its conditioning vector v [c_out].
+ *
+ * Arithmetic: the convolutions are implicit GEMMs on BF16 tensor-core operands with FP32
+ * accumulation. Weights are kept in FP32 (master copy, Adam state) and rounded to BF16
+ * for the GEMMs; activations and gradients between layers are stored in BF16; the head
+ * (D, its mean, phi_out) and the loss are FP32 with FP64 sums.
+ *
+ * Ownership and errors follow lbch.h: the caller owns the device workspace (the library
+ * never allocates), all work goes to the caller's stream, and calls return lbch_status.
+ */
+#ifndef LBNOP_H
+#define LBNOP_H
+
+#include "lbch.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbnop_ctx lbnop_ctx;
+
+#define LBNOP_MAX_BATCH 64
+
+typedef struct {
+  int32_t H, W;          /* field size, multiples of 32, each in [32, 8192] */
+  int32_t max_batch;     /* fields per forward or training step, in [1, LBNOP_MAX_BATCH] */
+  double scale;          /* phi_out = phi + scale (D - mean D); > 0 */
+} lbnop_params;
+
+/* Number of FP32 parameters (581,520). */
+int64_t lbnop_param_count(void);
+
+/* Device workspace for these parameters (weights, Adam state, activations and gradients
+ * for max_batch fields); 0 if the parameters are invalid. */
+size_t lbnop_workspace_bytes(const lbnop_params* p);
+
+lbch_status lbnop_create(const lbnop_params* p, void* d_workspace, size_t bytes, void* cuda_stream,
+                         lbnop_ctx** out);
+
+/* Loads parameters from host FP32 (lbnop_param_count values, layout above) and resets the
+ * Adam state. Synchronises. LBCH_ENONFINITE if any value is NaN or Inf. */
+lbch_status lbnop_set_params(lbnop_ctx* c, const float* h_theta);
+lbch_status lbnop_get_params(lbnop_ctx* c, float* h_theta);   /* synchronises */
+
+/* phi_out = network(phi, alpha) for `batch` fields. d_phi, d_phi_out: device FP32,
+ * [batch][H][W] (they may be the same buffer); h_alpha: host, batch values (anisotropy
+ * strength per field). Asynchronous. */
+lbch_status lbnop_forward(lbnop_ctx* c, const float* d_phi, const double* h_alpha, int32_t batch,
+                          float* d_phi_out);
+
+/* Forward, loss = mean over all nodes of (phi_out - target)^2, and its gradient in the
+ * parameters (kept in the context; read with lbnop_get_grads). d_target: device FP32
+ * [batch][H][W]. Writes the loss to *h_loss if h_loss is not NULL (synchronises then). */
+lbch_status lbnop_backward(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,
+                           int32_t batch, double* h_loss);
+lbch_status lbnop_get_grads(lbnop_ctx* c, float* h_grad);     /* synchronises */
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with learning rate lr
+ * on the gradient of the last lbnop_backward. Asynchronous. */
+lbch_status lbnop_adam(lbnop_ctx* c, double lr);
+
+/* lbnop_backward followed by lbnop_adam. */
+lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,
+                             int32_t batch, double lr, double* h_loss);
+
+/* Runs `cycles` times: one leap of the network on the field of `lbm` (phi = sum f),
+ * f = f^eq(phi_out) as in lbch_init_field, then lbm_steps steps of the scheme. The lbch
+ * context must have nx = W, ny = H, FP32 storage, and work on the same CUDA stream as
+ * this context. Asynchronous. */
+lbch_status lbnop_leap_run(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cycles, int64_t lbm_steps);
+
+/* Operator entry points (device pointers, the given stream, asynchronous), as used by
+ * the network. BF16 tensors are uint16_t bit patterns, channels last:
+ *   x [B][H][W][c_in], w [9][c_out][c_in], y [B][H][W][c_out].
+ * c_in and c_out must be 16, 32, 64 or 96; any H, W >= 1.
+ *   conv3x3:             y = conv(x, w) + bias (bias may be NULL), FP32 out.
+ *   conv3x3_bwd_data:    dx = sum_d w_d^T dy(p - d), FP32 out ([B][H][W][c_in]).
+ *   conv3x3_bwd_weight:  dw[d] = sum_p dy(p) x(p + d)^T, FP32 out ([9][c_out][c_in]),
+ *                        dy being BF16 [B][H][W][c_out]. */
+lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float* d_bias, int32_t B, int32_t H,
+                          int32_t W, int32_t c_in, int32_t c_out, float* d_y, void* cuda_stream);
+lbch_status lbnop_conv3x3_bwd_data(const uint16_t* d_dy, const uint16_t* d_w, int32_t B, int32_t H, int32_t W,
+                                   int32_t c_in, int32_t c_out, float* d_dx, void* cuda_stream);
+lbch_status lbnop_conv3x3_bwd_weight(const uint16_t* d_x, const uint16_t* d_dy, int32_t B, int32_t H, int32_t W,
+                                     int32_t c_in, int32_t c_out, float* d_dw, void* cuda_stream);
+
+const char* lbnop_last_error(const lbnop_ctx* c);
+void lbnop_destroy(lbnop_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -154,32 +154,50 @@ def d2s(x):
 
 # ---------------------------------------------------------------- the network
 
-def forward(theta: np.ndarray, phi: np.ndarray, alpha: np.ndarray, scale: float):
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even) through FP32: the storage format of
+    weights, activations and activation gradients in the CUDA path."""
+    x = np.asarray(a, dtype=np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _identity(a):
+    return a
+
+
+def forward(theta: np.ndarray, phi: np.ndarray, alpha: np.ndarray, scale: float, quantize=None):
     """phi_out = phi + scale (D - mean D), D = d2s(U-Net(s2d(phi), alpha)).
 
+    quantize (default: none) is applied where the CUDA path stores BF16: the weights, the
+    network input, every activation, pooled and summed tensor, and linear layer output.
     Returns phi_out and the saved tensors the backward pass needs.
     """
+    Q = quantize or _identity
     P = unpack(theta)
     alpha = np.asarray(alpha, dtype=np.float64).reshape(-1, 1, 1, 1)
-    s = {}
+    s = {"Q": Q}
 
     def layer(name, x):
-        W, b = P[name][0], P[name][1]
+        W, b = Q(P[name][0]), P[name][1]
         z = conv(x, W, b)
         if name == "e0a":
             z = z + alpha * P[name][2]
         s["in_" + name], s["z_" + name] = x, z
         act = dict((l[0], l[4]) for l in LAYERS)[name]
-        return silu(z) if act else z
+        if name == "out":
+            return z
+        return Q(silu(z)) if act else Q(z)
 
-    x0 = s2d(phi)
+    x0 = Q(s2d(phi))
     h0 = layer("e0b", layer("e0a", x0))
-    h1 = layer("e1b", layer("e1a", pool(h0)))
-    h2 = layer("e2b", layer("e2a", pool(h1)))
-    h3 = layer("m3b", layer("m3a", pool(h2)))
-    zd2 = layer("d2b", layer("d2a", up(h3) + h2))
-    zd1 = layer("d1b", layer("d1a", up(zd2) + h1))
-    zo = layer("out", layer("d0a", up(zd1) + h0))
+    h1 = layer("e1b", layer("e1a", Q(pool(h0))))
+    h2 = layer("e2b", layer("e2a", Q(pool(h1))))
+    h3 = layer("m3b", layer("m3a", Q(pool(h2))))
+    zd2 = layer("d2b", layer("d2a", Q(up(h3) + h2)))
+    zd1 = layer("d1b", layer("d1a", Q(up(zd2) + h1)))
+    zo = layer("out", layer("d0a", Q(up(zd1) + h0)))
     D = d2s(zo)
     D = D - D.mean(axis=(1, 2), keepdims=True)
     s["alpha"] = alpha
@@ -195,13 +213,14 @@ def loss(phi_out: np.ndarray, target: np.ndarray) -> tuple[float, np.ndarray]:
 def backward(theta: np.ndarray, s: dict, dphi_out: np.ndarray, scale: float) -> np.ndarray:
     """Gradient of the loss in the flat parameter vector, given d loss / d phi_out."""
     P = unpack(theta)
+    Q = s["Q"]
     G = {}
 
     def layer_bwd(name, g_out, act):
         """g_out: gradient in the layer's output; returns the gradient in its input."""
         z, x = s["z_" + name], s["in_" + name]
-        dz = g_out * silu_grad(z) if act else g_out
-        W = P[name][0]
+        dz = Q(g_out * silu_grad(Q(z)) if act else g_out)
+        W = Q(P[name][0])
         grads = [conv_bwd_weight(x, dz), dz.sum(axis=(0, 1, 2))]
         if name == "e0a":
             grads.append((dz * s["alpha"]).sum(axis=(0, 1, 2)))
@@ -209,7 +228,7 @@ def backward(theta: np.ndarray, s: dict, dphi_out: np.ndarray, scale: float) -> 
         return conv_bwd_data(dz, W)
 
     dD = scale * (dphi_out - dphi_out.mean(axis=(1, 2), keepdims=True))
-    g = s2d(dD)  # adjoint of d2s
+    g = s2d(dD)  # adjoint of d2s (quantised as the output layer's dz)
     g = layer_bwd("out", g, False)
     g_in_d0a = layer_bwd("d0a", g, True)
     g_h0 = g_in_d0a.copy()

@@ -387,6 +387,30 @@ lbch_status lbch_init_field(lbch_ctx* c, const double* h_phi0) {
   return LBCH_OK;
 }
 
+lbch_status lbch_init_field_device(lbch_ctx* c, const float* d_phi0) {
+  lbch_status st = precheck(c, false);
+  if (st != LBCH_OK) return st;
+  if (!d_phi0) return LBCH_EINVAL;
+  c->has_state = false;
+  widen_kernel<<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(d_phi0, (long long)c->p.nx * c->p.ny, c->stage0);
+  mu_alpha_kernel<<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->stage0, c->stage1, grid_of(c), c->k,
+                                                                4.0 * c->beta, c->flags);
+  c->cur = 0;
+  DISPATCH(c->p.storage, launch_init, c, c->buf[0]);
+  if ((st = finish(c, "init_field_device: launch")) != LBCH_OK) return st;
+  c->has_state = true;
+  c->steps = 0;
+  return LBCH_OK;
+}
+
+lbch_status lbch_get_phi_device(lbch_ctx* c, float* d_phi) {
+  lbch_status st = precheck(c, true);
+  if (st != LBCH_OK) return st;
+  if (!d_phi) return LBCH_EINVAL;
+  DISPATCH(c->p.storage, launch_phi, c, nullptr, d_phi);
+  return finish(c, "get_phi_device: launch");
+}
+
 lbch_status lbch_step(lbch_ctx* c, int64_t n) {
   lbch_status st = precheck(c, true);
   if (st != LBCH_OK) return st;

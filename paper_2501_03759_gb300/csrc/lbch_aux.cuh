@@ -40,6 +40,12 @@ __device__ __forceinline__ double pulled(const Buf& b, const Grid& g, int i, int
 
 // mu_alpha = f(phi) - k lap phi (Eq. 16, Eq. 26b) in FP64 from an FP64 phi plane;
 // flags non-finite phi.
+// FP32 -> FP64 copy of a device field (the staging plane of lbch_init_field_device).
+__global__ void widen_kernel(const float* __restrict__ in, long long n, double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
 __global__ void mu_alpha_kernel(const double* __restrict__ phi, double* __restrict__ mua, Grid g,
                                 double k, double beta4, int* bad) {
   const long long n = (long long)g.nx * g.ny;

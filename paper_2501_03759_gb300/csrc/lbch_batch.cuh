@@ -376,6 +376,7 @@ lbch_status lbch_batch_step(lbch_batch* b, int64_t n) {
   }
 
 LBCH_BATCH_FIELD_CALL(lbch_batch_get_field(lbch_batch* b, int32_t i, double* h_phi), lbch_get_field(c, h_phi))
+LBCH_BATCH_FIELD_CALL(lbch_batch_get_phi_device(lbch_batch* b, int32_t i, float* d_phi), lbch_get_phi_device(c, d_phi))
 LBCH_BATCH_FIELD_CALL(lbch_batch_mass(lbch_batch* b, int32_t i, double* out), lbch_mass(c, out))
 LBCH_BATCH_FIELD_CALL(lbch_batch_free_energy(lbch_batch* b, int32_t i, double* out), lbch_free_energy(c, out))
 #undef LBCH_BATCH_FIELD_CALL

@@ -1,0 +1,1132 @@
+// The learned leap of include/lbnop.h: a periodic convolutional U-Net whose 3 x 3
+// convolutions are implicit GEMMs on BF16 tensor-core operands (mma.sync m16n8k16, FP32
+// accumulation), with its backward pass, Adam, and the leap/LBM alternation.
+//
+// GEMM views of one layer (p: pixel, t: tap of the 3 x 3 stencil, off(t) its offset):
+//   forward      y[p][n]  = sum_{t, k} x[p + off(t)][k] W[t][n][k]        M = pixels, K = 9 c_in
+//   data grad    dx[p][n] = sum_{t, k} dy[p + off(t)][k] W[8 - t][k][n]   the same kernel on a
+//                                                                         flipped, transposed copy
+//   weight grad  dW[t][m][n] = sum_p dy[p][m] x[p + off(t)][n]            K = pixels (split-K)
+// Activations are channels-last BF16; every tensor lives in the caller's workspace.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lbnop.h"
+
+namespace nop {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int NL = 14;
+struct LayerSpec {
+  int ci, co, level;
+  bool act;
+};
+// The table of include/lbnop.h.
+constexpr LayerSpec kL[NL] = {{16, 32, 0, true},  {32, 32, 0, true},  {32, 64, 1, true},  {64, 64, 1, true},
+                              {64, 96, 2, true},  {96, 96, 2, true},  {96, 96, 3, true},  {96, 96, 3, true},
+                              {96, 96, 2, true},  {96, 64, 2, false}, {64, 64, 1, true},  {64, 32, 1, false},
+                              {32, 32, 0, true},  {32, 16, 0, false}};
+enum { E0A, E0B, E1A, E1B, E2A, E2B, M3A, M3B, D2A, D2B, D1A, D1B, D0A, OUT };
+
+struct LayerTab {
+  int off_w[NL], ci[NL], co[NL], woff[NL];
+};
+
+// ---------------------------------------------------------------- small helpers
+
+__device__ __forceinline__ float sigmoid_f(float z) { return 1.0f / (1.0f + expf(-z)); }
+__device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
+__device__ __forceinline__ float silu_grad_f(float z) {
+  const float s = sigmoid_f(z);
+  return s * (1.0f + z * (1.0f - s));
+}
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// D += A B for one m16n8k16 tile: A row-major 16 x 16, B column-major 16 x 8, BF16 in,
+// FP32 accumulate. Fragment of lane l (g = l / 4, q = l % 4): a = {A[g][2q..], A[g+8][2q..],
+// A[g][2q+8..], A[g+8][2q+8..]}, b = {B[2q..][g], B[2q+8..][g]}, d = {D[g][2q..], D[g+8][2q..]}.
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const bf16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const bf16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+
+// ---------------------------------------------------------------- convolution (forward, data grad)
+
+struct ConvArgs {
+  const bf16* x;  // [B][H][W][CI]
+  const bf16* w;  // TW = false: [9][CO][CI]; TW = true: [9][CI][CO], read at tap 8 - t
+  int B, H, W;
+  const float* bias;  // [CO] or null
+  const float* film;  // [CO] or null: adds alpha[b] film[n]
+  bf16* z;            // BF16 pre-activation out, or null
+  bf16* a;            // BF16 SiLU(z) out, or null
+  float* yf;          // FP32 out, or null
+  int accumulate;     // yf += instead of yf =
+  float alpha[LBNOP_MAX_BATCH];
+};
+
+constexpr int CONV_THREADS = 128;  // four warps, 16 pixels each
+
+// Each warp computes 16 consecutive pixels x CO channels; A fragments come straight from
+// the channels-last input (32-bit pairs of channels), B fragments from the weights (L1).
+template <int CI, int CO, bool TW>
+__global__ void __launch_bounds__(CONV_THREADS) conv_kernel(const ConvArgs p) {
+  constexpr int NT = CO / 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
+  const int HW = p.H * p.W, npix = p.B * HW;
+  const int base = (blockIdx.x * 4 + warp) * 16;
+  if (base >= npix) return;
+  int bi[2], hi[2], wi[2];
+  bool ok[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    int pix = base + g + 8 * r;
+    ok[r] = pix < npix;
+    pix = ok[r] ? pix : base;  // out-of-range rows load a valid pixel; their results are dropped
+    bi[r] = pix / HW;
+    const int rem = pix - bi[r] * HW;
+    hi[r] = rem / p.W;
+    wi[r] = rem - hi[r] * p.W;
+  }
+  float acc[NT][4];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+
+#pragma unroll 1
+  for (int t = 0; t < 9; ++t) {
+    const int dy = t / 3 - 1, dx = t % 3 - 1;
+    const bf16* xr[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      xr[r] = p.x + ((size_t)(bi[r] * p.H + wrap1(hi[r] + dy, p.H)) * p.W + wrap1(wi[r] + dx, p.W)) * CI + 2 * q;
+#pragma unroll
+    for (int c0 = 0; c0 < CI; c0 += 16) {
+      const uint32_t a[4] = {ld32(xr[0] + c0), ld32(xr[1] + c0), ld32(xr[0] + c0 + 8), ld32(xr[1] + c0 + 8)};
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        uint32_t b0, b1;
+        if constexpr (!TW) {
+          const bf16* wr = p.w + ((size_t)t * CO + 8 * j + g) * CI + c0 + 2 * q;
+          b0 = ld32(wr);
+          b1 = ld32(wr + 8);
+        } else {
+          const bf16* wr = p.w + ((size_t)(8 - t) * CI + c0 + 2 * q) * CO + 8 * j + g;
+          b0 = pack2(wr[0], wr[CO]);
+          b1 = pack2(wr[8 * CO], wr[9 * CO]);
+        }
+        mma_bf16(acc[j], a, b0, b1);
+      }
+    }
+  }
+
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (!ok[r]) continue;
+    const int pix = base + g + 8 * r;
+    const float al = p.film ? p.alpha[bi[r]] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int n = 8 * j + 2 * q;
+      float v0 = acc[j][2 * r], v1 = acc[j][2 * r + 1];
+      if (p.bias) {
+        v0 += p.bias[n];
+        v1 += p.bias[n + 1];
+      }
+      if (p.film) {
+        v0 = fmaf(al, p.film[n], v0);
+        v1 = fmaf(al, p.film[n + 1], v1);
+      }
+      const size_t o = (size_t)pix * CO + n;
+      if (p.yf) {
+        float2* y = reinterpret_cast<float2*>(p.yf + o);
+        if (p.accumulate) {
+          const float2 old = *y;
+          *y = make_float2(old.x + v0, old.y + v1);
+        } else {
+          *y = make_float2(v0, v1);
+        }
+      }
+      if (p.z) *reinterpret_cast<__nv_bfloat162*>(p.z + o) = __floats2bfloat162_rn(v0, v1);
+      if (p.a) *reinterpret_cast<__nv_bfloat162*>(p.a + o) = __floats2bfloat162_rn(silu_f(v0), silu_f(v1));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- weight gradient
+
+struct WgradArgs {
+  const bf16* x;   // [B][H][W][CI]
+  const bf16* dz;  // [B][H][W][CO]
+  int B, H, W;
+  int chunk;  // pixels per block (multiple of 32)
+  float* dw;  // [9][CO][CI], accumulated with atomicAdd
+};
+
+// Block (chunk, tap): stages 32 pixels of dz and of the shifted x in shared memory, then
+// ldmatrix.trans gives fragments whose K index runs over pixels. Warps share the
+// (CO / 16) x (CI / 8) output tiles.
+template <int CI, int CO>
+__global__ void __launch_bounds__(128) wgrad_kernel(const WgradArgs p) {
+  constexpr int MT = CO / 16, NT = CI / 8, TILES = MT * NT, PER = (TILES + 3) / 4;
+  constexpr int PZ = CO + 8, PX = CI + 8;  // padded pitches: conflict-free ldmatrix rows
+  __shared__ __align__(16) bf16 sz[32 * PZ];
+  __shared__ __align__(16) bf16 sx[32 * PX];
+  const int t = blockIdx.y, dy = t / 3 - 1, dx = t % 3 - 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
+  const int HW = p.H * p.W, npix = p.B * HW;
+  const int p0 = blockIdx.x * p.chunk, p1 = min(npix, p0 + p.chunk);
+  float acc[PER][4];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
+
+  for (int pb = p0; pb < p1; pb += 32) {
+    constexpr int VZ = CO / 8, VX = CI / 8;
+    for (int v = threadIdx.x; v < 32 * VZ; v += 128) {
+      const int r = v / VZ, c = v - r * VZ, pix = pb + r;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (pix < p1) val = *reinterpret_cast<const uint4*>(p.dz + (size_t)pix * CO + 8 * c);
+      *reinterpret_cast<uint4*>(sz + r * PZ + 8 * c) = val;
+    }
+    for (int v = threadIdx.x; v < 32 * VX; v += 128) {
+      const int r = v / VX, c = v - r * VX, pix = pb + r;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (pix < p1) {
+        const int b = pix / HW, rem = pix - b * HW, h = rem / p.W, w = rem - h * p.W;
+        val = *reinterpret_cast<const uint4*>(
+            p.x + ((size_t)(b * p.H + wrap1(h + dy, p.H)) * p.W + wrap1(w + dx, p.W)) * CI + 8 * c);
+      }
+      *reinterpret_cast<uint4*>(sx + r * PX + 8 * c) = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 32; ks += 16) {
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int tile = warp + 4 * i;
+        if (tile < TILES) {
+          const int mt = tile / NT, nt = tile - mt * NT;
+          uint32_t a[4], b0, b1;
+          // matrix l/8 = (m block (l/8)&1, k block (l/8)>>1): a = {A00, A10, A01, A11}
+          ldsm_x4_t(a, sz + (ks + ((lane >> 4) << 3) + (lane & 7)) * PZ + 16 * mt + (((lane >> 3) & 1) << 3));
+          ldsm_x2_t(b0, b1, sx + (ks + (lane & 15)) * PX + 8 * nt);
+          mma_bf16(acc[i], a, b0, b1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int tile = warp + 4 * i;
+    if (tile < TILES) {
+      const int mt = tile / NT, nt = tile - mt * NT;
+      float* d = p.dw + ((size_t)t * CO + 16 * mt + g) * CI + 8 * nt + 2 * q;
+      atomicAdd(d, acc[i][0]);
+      atomicAdd(d + 1, acc[i][1]);
+      atomicAdd(d + 8 * CI, acc[i][2]);
+      atomicAdd(d + 8 * CI + 1, acc[i][3]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- elementwise and reductions
+
+// phi [B][H][W] FP32 -> x0 [B][H/4][W/4][16] BF16, channel 4 di + dj = phi[4 i + di][4 j + dj].
+__global__ void s2d_kernel(const float* __restrict__ phi, int B, int H, int W, bf16* __restrict__ x0) {
+  const int h = H / 4, w = W / 4, n = B * h * w;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int b = k / (h * w), rem = k - b * h * w, i = rem / w, j = rem - i * w;
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int di = 0; di < 4; ++di) {
+      const float4 r = *reinterpret_cast<const float4*>(phi + ((size_t)b * H + 4 * i + di) * W + 4 * j);
+      v[4 * di + 0] = __float2bfloat16_rn(r.x);
+      v[4 * di + 1] = __float2bfloat16_rn(r.y);
+      v[4 * di + 2] = __float2bfloat16_rn(r.z);
+      v[4 * di + 3] = __float2bfloat16_rn(r.w);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(x0 + (size_t)k * 16);
+    dst[0] = reinterpret_cast<const uint4*>(v)[0];
+    dst[1] = reinterpret_cast<const uint4*>(v)[1];
+  }
+}
+
+// 2 x 2 average: x [B][2h][2w][C] -> y [B][h][w][C].
+__global__ void pool_kernel(const bf16* __restrict__ x, int B, int h, int w, int C, bf16* __restrict__ y) {
+  const long long n = (long long)B * h * w * C;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(k % C);
+    const long long pix = k / C;
+    const int j = (int)(pix % w), i = (int)((pix / w) % h), b = (int)(pix / ((long long)w * h));
+    const size_t r0 = ((size_t)(b * 2 * h + 2 * i) * 2 * w + 2 * j) * C + c, r1 = r0 + (size_t)2 * w * C;
+    const float s = (__bfloat162float(x[r0]) + __bfloat162float(x[r0 + C])) +
+                    (__bfloat162float(x[r1]) + __bfloat162float(x[r1 + C]));
+    y[k] = __float2bfloat16_rn(0.25f * s);
+  }
+}
+
+// y [B][h][w][C] = nearest 2x upsampling of xc [B][h/2][w/2][C] plus skip [B][h][w][C].
+__global__ void up_add_kernel(const bf16* __restrict__ xc, const bf16* __restrict__ skip, int B, int h, int w, int C,
+                              bf16* __restrict__ y) {
+  const long long n = (long long)B * h * w * C;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(k % C);
+    const long long pix = k / C;
+    const int j = (int)(pix % w), i = (int)((pix / w) % h), b = (int)(pix / ((long long)w * h));
+    const size_t src = ((size_t)(b * (h / 2) + i / 2) * (w / 2) + j / 2) * C + c;
+    y[k] = __float2bfloat16_rn(__bfloat162float(xc[src]) + __bfloat162float(skip[k]));
+  }
+}
+
+// dz [B][h][w][C] (BF16) from FP32 gradients: g at the same level, or the 2 x 2 sums of gf
+// (the adjoint of nearest upsampling) when gf is given; times SiLU'(z) when z is given.
+__global__ void dz_kernel(const float* __restrict__ g, const float* __restrict__ gf, const bf16* __restrict__ z, int B,
+                          int h, int w, int C, bf16* __restrict__ dz) {
+  const long long n = (long long)B * h * w * C;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    float v;
+    if (gf) {
+      const int c = (int)(k % C);
+      const long long pix = k / C;
+      const int j = (int)(pix % w), i = (int)((pix / w) % h), b = (int)(pix / ((long long)w * h));
+      const size_t r0 = ((size_t)(b * 2 * h + 2 * i) * 2 * w + 2 * j) * C + c, r1 = r0 + (size_t)2 * w * C;
+      v = (gf[r0] + gf[r0 + C]) + (gf[r1] + gf[r1 + C]);
+    } else {
+      v = g[k];
+    }
+    if (z) v *= silu_grad_f(__bfloat162float(z[k]));
+    dz[k] = __float2bfloat16_rn(v);
+  }
+}
+
+// gf [B][2h][2w][C] += 0.25 gc[parent] (the adjoint of 2 x 2 average pooling).
+__global__ void pool_bwd_kernel(const float* __restrict__ gc, int B, int h, int w, int C, float* __restrict__ gf) {
+  const long long n = (long long)B * 4 * h * w * C;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(k % C);
+    const long long pix = k / C;
+    const int j = (int)(pix % (2 * w)), i = (int)((pix / (2 * w)) % (2 * h)), b = (int)(pix / ((long long)4 * w * h));
+    gf[k] += 0.25f * gc[((size_t)(b * h + i / 2) * w + j / 2) * C + c];
+  }
+}
+
+// Bias gradient sum_p dz[p][c] and conditioning gradient sum_p alpha[b(p)] dz[p][c].
+struct ColsumArgs {
+  const bf16* dz;
+  int P, B, C;  // P pixels per sample
+  float* db;
+  float* dv;  // or null
+  float alpha[LBNOP_MAX_BATCH];
+};
+__global__ void colsum_kernel(const ColsumArgs a) {
+  __shared__ float s_b[256], s_v[256];
+  const int rows = blockDim.x / a.C, c = threadIdx.x % a.C, r = threadIdx.x / a.C;
+  const long long n = (long long)a.P * a.B;
+  float sb = 0.0f, sv = 0.0f;
+  if (r < rows)
+    for (long long pix = (long long)blockIdx.x * rows + r; pix < n; pix += (long long)gridDim.x * rows) {
+      const float v = __bfloat162float(a.dz[pix * a.C + c]);
+      sb += v;
+      if (a.dv) sv = fmaf(a.alpha[pix / a.P], v, sv);
+    }
+  s_b[threadIdx.x] = sb;
+  s_v[threadIdx.x] = sv;
+  __syncthreads();
+  if (r == 0) {
+    for (int k = 1; k < rows; ++k) {
+      sb += s_b[k * a.C + c];
+      sv += s_v[k * a.C + c];
+    }
+    atomicAdd(a.db + c, sb);
+    if (a.dv) atomicAdd(a.dv + c, sv);
+  }
+}
+
+constexpr int HEAD_BLOCKS = 32;  // partial sums per sample (fixed order: deterministic)
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;
+}
+
+// partial[b][blk] = sums over slices of sample b of v (n values per sample); with
+// target, of (v - target) and of (v - target)^2 (partial2).
+__global__ void sample_sums_kernel(const float* __restrict__ v, const float* __restrict__ target, long long n,
+                                   double* __restrict__ partial, double* __restrict__ partial2) {
+  __shared__ double sh[32];
+  const int b = blockIdx.y;
+  const float* vb = v + (size_t)b * n;
+  const float* tb = target ? target + (size_t)b * n : nullptr;
+  double s = 0.0, s2 = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const double d = tb ? (double)vb[k] - (double)tb[k] : (double)vb[k];
+    s += d;
+    s2 += d * d;
+  }
+  s = block_sum_d(s, sh);
+  if (partial2) s2 = block_sum_d(s2, sh);
+  if (threadIdx.x == 0) {
+    partial[b * gridDim.x + blockIdx.x] = s;
+    if (partial2) partial2[b * gridDim.x + blockIdx.x] = s2;
+  }
+}
+
+// mean[b] = sum of partial[b][*] / n; with partial2, loss = sum over all of partial2 / (B n).
+__global__ void finish_sums_kernel(const double* __restrict__ partial, const double* __restrict__ partial2, int B,
+                                   long long n, double* __restrict__ mean, double* __restrict__ loss) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double tot2 = 0.0;
+  for (int b = 0; b < B; ++b) {
+    double s = 0.0;
+    for (int k = 0; k < HEAD_BLOCKS; ++k) {
+      s += partial[b * HEAD_BLOCKS + k];
+      if (partial2) tot2 += partial2[b * HEAD_BLOCKS + k];
+    }
+    mean[b] = s / (double)n;
+  }
+  if (partial2) *loss = tot2 / ((double)B * (double)n);
+}
+
+// phi_out = phi + scale (D - mean D), D = depth-to-space of zout [B][H/4][W/4][16].
+__global__ void head_kernel(const float* __restrict__ phi, const float* __restrict__ zout,
+                            const double* __restrict__ mean, int B, int H, int W, float scale,
+                            float* __restrict__ phi_out) {
+  const long long n = (long long)B * H * W;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(k % W), y = (int)((k / W) % H), b = (int)(k / ((long long)W * H));
+    const float D = zout[((size_t)(b * (H / 4) + y / 4) * (W / 4) + x / 4) * 16 + 4 * (y & 3) + (x & 3)];
+    phi_out[k] = phi[k] + scale * (D - (float)mean[b]);
+  }
+}
+
+// dz_out = space-to-depth of scale (g - mean g), g = 2 (phi_out - target) / (B H W) the
+// gradient of the mean squared error; mean_d[b] is the mean of (phi_out - target).
+__global__ void head_bwd_kernel(const float* __restrict__ phi_out, const float* __restrict__ target,
+                                const double* __restrict__ mean_d, int B, int H, int W, float coef,
+                                bf16* __restrict__ dz) {
+  const long long n = (long long)B * H * W;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(k % W), y = (int)((k / W) % H), b = (int)(k / ((long long)W * H));
+    const float d = (float)((double)phi_out[k] - (double)target[k] - mean_d[b]);
+    dz[((size_t)(b * (H / 4) + y / 4) * (W / 4) + x / 4) * 16 + 4 * (y & 3) + (x & 3)] = __float2bfloat16_rn(coef * d);
+  }
+}
+
+// Adam (Kingma and Ba 2015, Algorithm 1; c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)),
+// then the BF16 copies of every weight: wf[t][co][ci] and wb[t][ci][co] = W[8 - t][co][ci].
+__global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ grad, long long n, float lr, float c1, float c2, int update,
+                            const LayerTab tab, bf16* __restrict__ wf, bf16* __restrict__ wb) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    float th = theta[k];
+    if (update) {
+      const float gk = grad[k];
+      const float mk = fmaf(0.9f, m[k], 0.1f * gk);
+      const float vk = fmaf(0.999f, v[k], 0.001f * gk * gk);
+      m[k] = mk;
+      v[k] = vk;
+      th -= lr * (mk * c1) / (sqrtf(vk * c2) + 1e-8f);
+      theta[k] = th;
+    }
+    for (int l = 0; l < NL; ++l) {
+      const long long rel = k - tab.off_w[l];
+      const int ci = tab.ci[l], co = tab.co[l];
+      if (rel >= 0 && rel < 9LL * co * ci) {
+        const int t = (int)(rel / ((long long)co * ci)), r2 = (int)(rel % ((long long)co * ci));
+        const int o = r2 / ci, i = r2 - o * ci;
+        const bf16 hv = __float2bfloat16_rn(th);
+        wf[tab.woff[l] + rel] = hv;
+        wb[tab.woff[l] + ((size_t)(8 - t) * ci + i) * co + o] = hv;
+        break;
+      }
+    }
+  }
+}
+
+__global__ void finite_kernel(const float* __restrict__ v, long long n, int* bad) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(v[k])) atomicOr(bad, 1);
+}
+
+// ---------------------------------------------------------------- launch helpers
+
+template <int CI, int CO, bool TW>
+void conv_t(const ConvArgs& a, cudaStream_t s) {
+  const int npix = a.B * a.H * a.W;
+  conv_kernel<CI, CO, TW><<<(npix + 63) / 64, CONV_THREADS, 0, s>>>(a);
+}
+
+template <int CI, int CO>
+void wgrad_t(const WgradArgs& a, cudaStream_t s) {
+  const int npix = a.B * a.H * a.W;
+  wgrad_kernel<CI, CO><<<dim3((npix + a.chunk - 1) / a.chunk, 9), 128, 0, s>>>(a);
+}
+
+bool channels_ok(int c) { return c == 16 || c == 32 || c == 64 || c == 96; }
+
+#define NOP_CH_SWITCH(CI, CO, CALL)                    \
+  switch (CI * 1000 + CO) {                            \
+    case 16016: CALL(16, 16); break;                   \
+    case 16032: CALL(16, 32); break;                   \
+    case 16064: CALL(16, 64); break;                   \
+    case 16096: CALL(16, 96); break;                   \
+    case 32016: CALL(32, 16); break;                   \
+    case 32032: CALL(32, 32); break;                   \
+    case 32064: CALL(32, 64); break;                   \
+    case 32096: CALL(32, 96); break;                   \
+    case 64016: CALL(64, 16); break;                   \
+    case 64032: CALL(64, 32); break;                   \
+    case 64064: CALL(64, 64); break;                   \
+    case 64096: CALL(64, 96); break;                   \
+    case 96016: CALL(96, 16); break;                   \
+    case 96032: CALL(96, 32); break;                   \
+    case 96064: CALL(96, 64); break;                   \
+    case 96096: CALL(96, 96); break;                   \
+    default: break;                                    \
+  }
+
+void conv_launch(int ci, int co, bool tw, const ConvArgs& a, cudaStream_t s) {
+#define NOP_CONV_F(I, O) conv_t<I, O, false>(a, s)
+#define NOP_CONV_T(I, O) conv_t<I, O, true>(a, s)
+  if (tw) {
+    NOP_CH_SWITCH(ci, co, NOP_CONV_T)
+  } else {
+    NOP_CH_SWITCH(ci, co, NOP_CONV_F)
+  }
+#undef NOP_CONV_F
+#undef NOP_CONV_T
+}
+
+int wgrad_chunk(int npix) {
+  int c = (npix + 63) / 64;
+  c = (c + 31) / 32 * 32;
+  return c < 512 ? 512 : c;
+}
+
+void wgrad_launch(int ci, int co, const WgradArgs& a, cudaStream_t s) {
+#define NOP_WG(I, O) wgrad_t<I, O>(a, s)
+  NOP_CH_SWITCH(ci, co, NOP_WG)
+#undef NOP_WG
+}
+
+int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+}  // namespace nop
+
+using namespace nop;
+
+// ---------------------------------------------------------------- context
+
+struct lbnop_ctx {
+  lbnop_params p;
+  cudaStream_t stream;
+  LayerTab tab;
+  long long n_params, n_w;
+  int off_b[NL], off_v;
+  int h0, w0;  // level-0 size (H/4, W/4)
+  float *theta, *m, *v, *grad;
+  bf16 *wf, *wb;
+  // activations (BF16), by level; z_* pre-activations, a_* SiLU outputs
+  bf16 *x0, *z[NL], *a[NL], *p1, *p2, *p3, *in_d2a, *in_d1a, *in_d0a;
+  bf16* dz[4];
+  float *g0a, *g0b, *g1a, *g1b, *g2a, *g2b, *g3a;
+  float* zout;
+  double *partial, *partial2, *mean, *loss;
+  float *leap0, *leap1;
+  float* phi_out;  // [max_batch][H][W], the training forward's output
+  int* flags;
+  long long adam_t;
+  int last_batch;
+  bool failed;
+  char err[512];
+};
+
+namespace {
+
+constexpr size_t NOP_ALIGN = 256;
+size_t al(size_t b) { return (b + NOP_ALIGN - 1) / NOP_ALIGN * NOP_ALIGN; }
+
+const char* check_params(const lbnop_params* p) {
+  if (!p) return "params is NULL";
+  if (p->H < 32 || p->W < 32 || p->H > 8192 || p->W > 8192 || p->H % 32 || p->W % 32)
+    return "H and W must be multiples of 32 in [32, 8192]";
+  if (p->max_batch < 1 || p->max_batch > LBNOP_MAX_BATCH) return "max_batch must be in [1, 64]";
+  if (!(p->scale > 0.0) || !std::isfinite(p->scale)) return "scale must be finite and > 0";
+  return nullptr;
+}
+
+long long level_pixels(const lbnop_params* p, int level) {
+  return (long long)p->max_batch * ((p->H / 4) >> level) * ((p->W / 4) >> level);
+}
+
+// Walks the workspace layout; with c == nullptr only measures it.
+size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* r = base ? base + off : nullptr;
+    off += al(bytes);
+    return r;
+  };
+  long long n_params = 0, n_w = 0;
+  for (int l = 0; l < NL; ++l) {
+    n_params += 9LL * kL[l].co * kL[l].ci + kL[l].co + (l == E0A ? kL[l].co : 0);
+    n_w += 9LL * kL[l].co * kL[l].ci;
+  }
+  const long long P[4] = {level_pixels(p, 0), level_pixels(p, 1), level_pixels(p, 2), level_pixels(p, 3)};
+  char* theta = take(n_params * 4);
+  char* m = take(n_params * 4);
+  char* v = take(n_params * 4);
+  char* grad = take(n_params * 4);
+  char* wf = take(n_w * 2);
+  char* wb = take(n_w * 2);
+  char* x0 = take(P[0] * 16 * 2);
+  char *zz[NL], *aa[NL];
+  for (int l = 0; l < NL; ++l) {
+    zz[l] = take(P[kL[l].level] * kL[l].co * 2);
+    aa[l] = kL[l].act ? take(P[kL[l].level] * kL[l].co * 2) : nullptr;
+  }
+  char* p1 = take(P[1] * 32 * 2);
+  char* p2 = take(P[2] * 64 * 2);
+  char* p3 = take(P[3] * 96 * 2);
+  char* in2 = take(P[2] * 96 * 2);
+  char* in1 = take(P[1] * 64 * 2);
+  char* in0 = take(P[0] * 32 * 2);
+  char* dz[4] = {take(P[0] * 32 * 2), take(P[1] * 64 * 2), take(P[2] * 96 * 2), take(P[3] * 96 * 2)};
+  char* g0a = take(P[0] * 32 * 4);
+  char* g0b = take(P[0] * 32 * 4);
+  char* g1a = take(P[1] * 64 * 4);
+  char* g1b = take(P[1] * 64 * 4);
+  char* g2a = take(P[2] * 96 * 4);
+  char* g2b = take(P[2] * 96 * 4);
+  char* g3a = take(P[3] * 96 * 4);
+  char* zout = take(P[0] * 16 * 4);
+  char* partial = take((size_t)LBNOP_MAX_BATCH * HEAD_BLOCKS * 8);
+  char* partial2 = take((size_t)LBNOP_MAX_BATCH * HEAD_BLOCKS * 8);
+  char* mean = take(LBNOP_MAX_BATCH * 8);
+  char* loss = take(8);
+  char* leap0 = take((size_t)p->H * p->W * 4);
+  char* leap1 = take((size_t)p->H * p->W * 4);
+  char* phi_out = take((size_t)p->max_batch * p->H * p->W * 4);
+  char* flags = take(16);
+  if (c) {
+    c->n_params = n_params;
+    c->n_w = n_w;
+    c->theta = (float*)theta;
+    c->m = (float*)m;
+    c->v = (float*)v;
+    c->grad = (float*)grad;
+    c->wf = (bf16*)wf;
+    c->wb = (bf16*)wb;
+    c->x0 = (bf16*)x0;
+    for (int l = 0; l < NL; ++l) {
+      c->z[l] = (bf16*)zz[l];
+      c->a[l] = (bf16*)aa[l];
+    }
+    c->p1 = (bf16*)p1;
+    c->p2 = (bf16*)p2;
+    c->p3 = (bf16*)p3;
+    c->in_d2a = (bf16*)in2;
+    c->in_d1a = (bf16*)in1;
+    c->in_d0a = (bf16*)in0;
+    for (int k = 0; k < 4; ++k) c->dz[k] = (bf16*)dz[k];
+    c->g0a = (float*)g0a;
+    c->g0b = (float*)g0b;
+    c->g1a = (float*)g1a;
+    c->g1b = (float*)g1b;
+    c->g2a = (float*)g2a;
+    c->g2b = (float*)g2b;
+    c->g3a = (float*)g3a;
+    c->zout = (float*)zout;
+    c->partial = (double*)partial;
+    c->partial2 = (double*)partial2;
+    c->mean = (double*)mean;
+    c->loss = (double*)loss;
+    c->leap0 = (float*)leap0;
+    c->leap1 = (float*)leap1;
+    c->phi_out = (float*)phi_out;
+    c->flags = (int*)flags;
+  }
+  return off;
+}
+
+void set_err(lbnop_ctx* c, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c->err, sizeof(c->err), fmt, ap);
+  va_end(ap);
+}
+
+bool cuda_bad(lbnop_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return false;
+  c->failed = true;
+  set_err(c, "%s: %s", what, cudaGetErrorString(e));
+  return true;
+}
+
+lbch_status pre(lbnop_ctx* c) {
+  if (!c) return LBCH_EINVAL;
+  return c->failed ? LBCH_ESTATE : LBCH_OK;
+}
+
+lbch_status done(lbnop_ctx* c, const char* what) {
+  return cuda_bad(c, cudaGetLastError(), what) ? LBCH_ECUDA : LBCH_OK;
+}
+
+// Level dimensions for `batch` fields.
+struct Dims {
+  int B, h[4], w[4];
+};
+Dims dims(const lbnop_ctx* c, int batch) {
+  Dims d;
+  d.B = batch;
+  for (int l = 0; l < 4; ++l) {
+    d.h[l] = c->h0 >> l;
+    d.w[l] = c->w0 >> l;
+  }
+  return d;
+}
+
+const bf16* wf_of(const lbnop_ctx* c, int l) { return c->wf + c->tab.woff[l]; }
+const bf16* wb_of(const lbnop_ctx* c, int l) { return c->wb + c->tab.woff[l]; }
+const float* bias_of(const lbnop_ctx* c, int l) { return c->theta + c->off_b[l]; }
+
+// One layer forward: x -> z (kept when training or when the layer is linear) and a.
+void layer_fwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x, bool training, const double* alpha) {
+  ConvArgs a{};
+  a.x = x;
+  a.w = wf_of(c, l);
+  a.B = d.B;
+  a.H = d.h[kL[l].level];
+  a.W = d.w[kL[l].level];
+  a.bias = bias_of(c, l);
+  a.film = l == E0A ? c->theta + c->off_v : nullptr;
+  for (int b = 0; b < d.B; ++b) a.alpha[b] = (float)alpha[b];
+  if (l == OUT) {
+    a.yf = c->zout;
+  } else {
+    a.z = (training || !kL[l].act) ? c->z[l] : nullptr;
+    a.a = kL[l].act ? c->a[l] : nullptr;
+  }
+  conv_launch(kL[l].ci, kL[l].co, false, a, c->stream);
+}
+
+void forward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, int batch, float* d_out, bool training) {
+  const Dims d = dims(c, batch);
+  cudaStream_t s = c->stream;
+  const long long P0 = (long long)batch * d.h[0] * d.w[0];
+  s2d_kernel<<<grid_for(P0, 256), 256, 0, s>>>(d_phi, batch, c->p.H, c->p.W, c->x0);
+  layer_fwd(c, E0A, d, c->x0, training, alpha);
+  layer_fwd(c, E0B, d, c->a[E0A], training, alpha);
+  auto pool = [&](const bf16* x, int lvl, int C, bf16* y) {
+    const long long n = (long long)batch * d.h[lvl] * d.w[lvl] * C;
+    pool_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, batch, d.h[lvl], d.w[lvl], C, y);
+  };
+  auto up_add = [&](const bf16* xc, const bf16* skip, int lvl, int C, bf16* y) {
+    const long long n = (long long)batch * d.h[lvl] * d.w[lvl] * C;
+    up_add_kernel<<<grid_for(n, 256), 256, 0, s>>>(xc, skip, batch, d.h[lvl], d.w[lvl], C, y);
+  };
+  pool(c->a[E0B], 1, 32, c->p1);
+  layer_fwd(c, E1A, d, c->p1, training, alpha);
+  layer_fwd(c, E1B, d, c->a[E1A], training, alpha);
+  pool(c->a[E1B], 2, 64, c->p2);
+  layer_fwd(c, E2A, d, c->p2, training, alpha);
+  layer_fwd(c, E2B, d, c->a[E2A], training, alpha);
+  pool(c->a[E2B], 3, 96, c->p3);
+  layer_fwd(c, M3A, d, c->p3, training, alpha);
+  layer_fwd(c, M3B, d, c->a[M3A], training, alpha);
+  up_add(c->a[M3B], c->a[E2B], 2, 96, c->in_d2a);
+  layer_fwd(c, D2A, d, c->in_d2a, training, alpha);
+  layer_fwd(c, D2B, d, c->a[D2A], training, alpha);
+  up_add(c->z[D2B], c->a[E1B], 1, 64, c->in_d1a);
+  layer_fwd(c, D1A, d, c->in_d1a, training, alpha);
+  layer_fwd(c, D1B, d, c->a[D1A], training, alpha);
+  up_add(c->z[D1B], c->a[E0B], 0, 32, c->in_d0a);
+  layer_fwd(c, D0A, d, c->in_d0a, training, alpha);
+  layer_fwd(c, OUT, d, c->a[D0A], training, alpha);
+  // head: D - mean D per field
+  const long long nz = (long long)d.h[0] * d.w[0] * 16;
+  sample_sums_kernel<<<dim3(HEAD_BLOCKS, batch), 256, 0, s>>>(c->zout, nullptr, nz, c->partial, nullptr);
+  finish_sums_kernel<<<1, 32, 0, s>>>(c->partial, nullptr, batch, (long long)c->p.H * c->p.W, c->mean, nullptr);
+  const long long n = (long long)batch * c->p.H * c->p.W;
+  head_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_phi, c->zout, c->mean, batch, c->p.H, c->p.W, (float)c->p.scale,
+                                               d_out);
+}
+
+// Backward of layer l given dz (its pre-activation gradient, BF16, in c->dz[level]):
+// weight and bias gradients, and the input gradient into gin (FP32) unless gin is null.
+void layer_bwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x_in, float* gin, const double* alpha) {
+  cudaStream_t s = c->stream;
+  const int lvl = kL[l].level, ci = kL[l].ci, co = kL[l].co;
+  const bf16* dz = c->dz[lvl];
+  ColsumArgs cs{};
+  cs.dz = dz;
+  cs.P = d.h[lvl] * d.w[lvl];
+  cs.B = d.B;
+  cs.C = co;
+  cs.db = c->grad + c->off_b[l];
+  cs.dv = l == E0A ? c->grad + c->off_v : nullptr;
+  for (int b = 0; b < d.B; ++b) cs.alpha[b] = (float)alpha[b];
+  const long long npix = (long long)d.B * cs.P;
+  const int rows = 256 / co;
+  int blocks = (int)((npix + rows * 64 - 1) / (rows * 64));
+  blocks = blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks);
+  colsum_kernel<<<blocks, rows * co, 0, s>>>(cs);
+  WgradArgs wg{};
+  wg.x = x_in;
+  wg.dz = dz;
+  wg.B = d.B;
+  wg.H = d.h[lvl];
+  wg.W = d.w[lvl];
+  wg.chunk = wgrad_chunk((int)npix);
+  wg.dw = c->grad + c->tab.off_w[l];
+  wgrad_launch(ci, co, wg, s);
+  if (gin) {
+    ConvArgs a{};
+    a.x = dz;
+    a.w = wb_of(c, l);
+    a.B = d.B;
+    a.H = d.h[lvl];
+    a.W = d.w[lvl];
+    a.yf = gin;
+    conv_launch(co, ci, false, a, s);
+  }
+}
+
+// dz[level] = g (or up-adjoint of gf) times SiLU'(z) where z is given.
+void make_dz(lbnop_ctx* c, const Dims& d, int lvl, int C, const float* g, const float* gf, const bf16* z) {
+  const long long n = (long long)d.B * d.h[lvl] * d.w[lvl] * C;
+  dz_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(g, gf, z, d.B, d.h[lvl], d.w[lvl], C, c->dz[lvl]);
+}
+
+void pool_bwd(lbnop_ctx* c, const Dims& d, int lvl_coarse, int C, const float* gc, float* gf) {
+  const long long n = (long long)d.B * 4 * d.h[lvl_coarse] * d.w[lvl_coarse] * C;
+  pool_bwd_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(gc, d.B, d.h[lvl_coarse], d.w[lvl_coarse], C, gf);
+}
+
+void backward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, const float* d_target, int batch) {
+  cudaStream_t s = c->stream;
+  const Dims d = dims(c, batch);
+  float* phi_out = c->phi_out;
+  forward_impl(c, d_phi, alpha, batch, phi_out, true);
+  const long long hw = (long long)c->p.H * c->p.W, n = batch * hw;
+  sample_sums_kernel<<<dim3(HEAD_BLOCKS, batch), 256, 0, s>>>(phi_out, d_target, hw, c->partial, c->partial2);
+  finish_sums_kernel<<<1, 32, 0, s>>>(c->partial, c->partial2, batch, hw, c->mean, c->loss);
+  cudaMemsetAsync(c->grad, 0, c->n_params * sizeof(float), s);
+  head_bwd_kernel<<<grid_for(n, 256), 256, 0, s>>>(phi_out, d_target, c->mean, batch, c->p.H, c->p.W,
+                                                   (float)(c->p.scale * 2.0 / (double)n), c->dz[0]);
+  layer_bwd(c, OUT, d, c->a[D0A], c->g0a, alpha);
+  make_dz(c, d, 0, 32, c->g0a, nullptr, c->z[D0A]);
+  layer_bwd(c, D0A, d, c->in_d0a, c->g0b, alpha);  // g0b: gradient in h0 from here on
+  make_dz(c, d, 1, 32, nullptr, c->g0b, nullptr);
+  layer_bwd(c, D1B, d, c->a[D1A], c->g1a, alpha);
+  make_dz(c, d, 1, 64, c->g1a, nullptr, c->z[D1A]);
+  layer_bwd(c, D1A, d, c->in_d1a, c->g1b, alpha);  // g1b: gradient in h1
+  make_dz(c, d, 2, 64, nullptr, c->g1b, nullptr);
+  layer_bwd(c, D2B, d, c->a[D2A], c->g2a, alpha);
+  make_dz(c, d, 2, 96, c->g2a, nullptr, c->z[D2A]);
+  layer_bwd(c, D2A, d, c->in_d2a, c->g2b, alpha);  // g2b: gradient in h2
+  make_dz(c, d, 3, 96, nullptr, c->g2b, c->z[M3B]);
+  layer_bwd(c, M3B, d, c->a[M3A], c->g3a, alpha);
+  make_dz(c, d, 3, 96, c->g3a, nullptr, c->z[M3A]);
+  layer_bwd(c, M3A, d, c->p3, c->g3a, alpha);
+  pool_bwd(c, d, 3, 96, c->g3a, c->g2b);
+  make_dz(c, d, 2, 96, c->g2b, nullptr, c->z[E2B]);
+  layer_bwd(c, E2B, d, c->a[E2A], c->g2a, alpha);
+  make_dz(c, d, 2, 96, c->g2a, nullptr, c->z[E2A]);
+  layer_bwd(c, E2A, d, c->p2, c->g2a, alpha);
+  pool_bwd(c, d, 2, 64, c->g2a, c->g1b);
+  make_dz(c, d, 1, 64, c->g1b, nullptr, c->z[E1B]);
+  layer_bwd(c, E1B, d, c->a[E1A], c->g1a, alpha);
+  make_dz(c, d, 1, 64, c->g1a, nullptr, c->z[E1A]);
+  layer_bwd(c, E1A, d, c->p1, c->g1a, alpha);
+  pool_bwd(c, d, 1, 32, c->g1a, c->g0b);
+  make_dz(c, d, 0, 32, c->g0b, nullptr, c->z[E0B]);
+  layer_bwd(c, E0B, d, c->a[E0A], c->g0a, alpha);
+  make_dz(c, d, 0, 32, c->g0a, nullptr, c->z[E0A]);
+  layer_bwd(c, E0A, d, c->x0, nullptr, alpha);
+  c->last_batch = batch;
+}
+
+void refresh_or_update(lbnop_ctx* c, bool update, double lr) {
+  float c1 = 1.0f, c2 = 1.0f;
+  if (update) {
+    c->adam_t += 1;
+    c1 = (float)(1.0 / (1.0 - std::pow(0.9, (double)c->adam_t)));
+    c2 = (float)(1.0 / (1.0 - std::pow(0.999, (double)c->adam_t)));
+  }
+  adam_kernel<<<grid_for(c->n_params, 256), 256, 0, c->stream>>>(c->theta, c->m, c->v, c->grad, c->n_params,
+                                                                 (float)lr, c1, c2, update ? 1 : 0, c->tab, c->wf,
+                                                                 c->wb);
+}
+
+lbch_status check_batch(lbnop_ctx* c, int batch, const double* h_alpha) {
+  if (batch < 1 || batch > c->p.max_batch) {
+    set_err(c, "batch must be in [1, max_batch = %d]", c->p.max_batch);
+    return LBCH_EINVAL;
+  }
+  if (!h_alpha) {
+    set_err(c, "h_alpha is NULL");
+    return LBCH_EINVAL;
+  }
+  return LBCH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t lbnop_param_count(void) {
+  int64_t n = 0;
+  for (int l = 0; l < NL; ++l) n += 9LL * kL[l].co * kL[l].ci + kL[l].co + (l == E0A ? kL[l].co : 0);
+  return n;
+}
+
+size_t lbnop_workspace_bytes(const lbnop_params* p) {
+  if (check_params(p)) return 0;
+  return layout(p, nullptr, nullptr);
+}
+
+lbch_status lbnop_create(const lbnop_params* p, void* d_workspace, size_t bytes, void* cuda_stream, lbnop_ctx** out) {
+  if (!out || check_params(p)) return LBCH_EINVAL;
+  if (!d_workspace || bytes < lbnop_workspace_bytes(p) || ((uintptr_t)d_workspace % NOP_ALIGN) != 0)
+    return LBCH_ENOMEM;
+  lbnop_ctx* c = new (std::nothrow) lbnop_ctx();
+  if (!c) return LBCH_ENOMEM;
+  c->p = *p;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->h0 = p->H / 4;
+  c->w0 = p->W / 4;
+  layout(p, c, (char*)d_workspace);
+  int off = 0, woff = 0;
+  for (int l = 0; l < NL; ++l) {
+    c->tab.off_w[l] = off;
+    c->tab.ci[l] = kL[l].ci;
+    c->tab.co[l] = kL[l].co;
+    c->tab.woff[l] = woff;
+    off += 9 * kL[l].co * kL[l].ci;
+    woff += 9 * kL[l].co * kL[l].ci;
+    c->off_b[l] = off;
+    off += kL[l].co;
+    if (l == E0A) {
+      c->off_v = off;
+      off += kL[l].co;
+    }
+  }
+  c->adam_t = 0;
+  c->last_batch = 0;
+  c->failed = false;
+  c->err[0] = 0;
+  *out = c;
+  return LBCH_OK;
+}
+
+lbch_status lbnop_set_params(lbnop_ctx* c, const float* h_theta) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!h_theta) return LBCH_EINVAL;
+  const size_t nb = c->n_params * sizeof(float);
+  if (cuda_bad(c, cudaMemcpyAsync(c->theta, h_theta, nb, cudaMemcpyHostToDevice, c->stream), "set_params: copy") ||
+      cuda_bad(c, cudaMemsetAsync(c->m, 0, nb, c->stream), "set_params: clear") ||
+      cuda_bad(c, cudaMemsetAsync(c->v, 0, nb, c->stream), "set_params: clear") ||
+      cuda_bad(c, cudaMemsetAsync(c->flags, 0, sizeof(int), c->stream), "set_params: clear"))
+    return LBCH_ECUDA;
+  finite_kernel<<<grid_for(c->n_params, 256), 256, 0, c->stream>>>(c->theta, c->n_params, c->flags);
+  refresh_or_update(c, false, 0.0);
+  c->adam_t = 0;
+  int bad = 0;
+  if (cuda_bad(c, cudaMemcpyAsync(&bad, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "set_params") ||
+      cuda_bad(c, cudaStreamSynchronize(c->stream), "set_params: sync"))
+    return LBCH_ECUDA;
+  if (bad) {
+    set_err(c, "set_params: NaN or Inf in the parameters");
+    return LBCH_ENONFINITE;
+  }
+  return done(c, "set_params");
+}
+
+lbch_status lbnop_get_params(lbnop_ctx* c, float* h_theta) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!h_theta) return LBCH_EINVAL;
+  if (cuda_bad(c, cudaMemcpyAsync(h_theta, c->theta, c->n_params * 4, cudaMemcpyDeviceToHost, c->stream), "get") ||
+      cuda_bad(c, cudaStreamSynchronize(c->stream), "get_params: sync"))
+    return LBCH_ECUDA;
+  return LBCH_OK;
+}
+
+lbch_status lbnop_forward(lbnop_ctx* c, const float* d_phi, const double* h_alpha, int32_t batch, float* d_phi_out) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!d_phi || !d_phi_out) return LBCH_EINVAL;
+  if ((st = check_batch(c, batch, h_alpha)) != LBCH_OK) return st;
+  forward_impl(c, d_phi, h_alpha, batch, d_phi_out, false);
+  return done(c, "forward: launch");
+}
+
+lbch_status lbnop_backward(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,
+                           int32_t batch, double* h_loss) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!d_phi || !d_target) return LBCH_EINVAL;
+  if ((st = check_batch(c, batch, h_alpha)) != LBCH_OK) return st;
+  backward_impl(c, d_phi, h_alpha, d_target, batch);
+  if ((st = done(c, "backward: launch")) != LBCH_OK) return st;
+  if (h_loss) {
+    if (cuda_bad(c, cudaMemcpyAsync(h_loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss") ||
+        cuda_bad(c, cudaStreamSynchronize(c->stream), "backward: sync"))
+      return LBCH_ECUDA;
+  }
+  return LBCH_OK;
+}
+
+lbch_status lbnop_get_grads(lbnop_ctx* c, float* h_grad) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!h_grad) return LBCH_EINVAL;
+  if (cuda_bad(c, cudaMemcpyAsync(h_grad, c->grad, c->n_params * 4, cudaMemcpyDeviceToHost, c->stream), "grads") ||
+      cuda_bad(c, cudaStreamSynchronize(c->stream), "get_grads: sync"))
+    return LBCH_ECUDA;
+  return LBCH_OK;
+}
+
+lbch_status lbnop_adam(lbnop_ctx* c, double lr) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!(lr >= 0.0) || !std::isfinite(lr)) return LBCH_EINVAL;
+  if (c->last_batch == 0) {
+    set_err(c, "adam: no gradient yet (call lbnop_backward first)");
+    return LBCH_EINVAL;
+  }
+  refresh_or_update(c, true, lr);
+  return done(c, "adam: launch");
+}
+
+lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,
+                             int32_t batch, double lr, double* h_loss) {
+  lbch_status st = lbnop_backward(c, d_phi, h_alpha, d_target, batch, nullptr);
+  if (st != LBCH_OK) return st;
+  if ((st = lbnop_adam(c, lr)) != LBCH_OK) return st;
+  if (h_loss) {
+    if (cuda_bad(c, cudaMemcpyAsync(h_loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss") ||
+        cuda_bad(c, cudaStreamSynchronize(c->stream), "train_step: sync"))
+      return LBCH_ECUDA;
+  }
+  return LBCH_OK;
+}
+
+lbch_status lbnop_leap_run(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cycles, int64_t lbm_steps) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!lbm || cycles < 0 || lbm_steps < 0) return LBCH_EINVAL;
+  for (int64_t k = 0; k < cycles; ++k) {
+    if ((st = lbch_get_phi_device(lbm, c->leap0)) != LBCH_OK) {
+      set_err(c, "leap_run: lbch_get_phi_device: %s", lbch_last_error(lbm));
+      return st;
+    }
+    forward_impl(c, c->leap0, &alpha, 1, c->leap0, false);
+    if ((st = lbch_init_field_device(lbm, c->leap0)) != LBCH_OK ||
+        (st = lbch_step(lbm, lbm_steps)) != LBCH_OK) {
+      set_err(c, "leap_run: %s", lbch_last_error(lbm));
+      return st;
+    }
+  }
+  return done(c, "leap_run: launch");
+}
+
+static lbch_status op_check(int32_t B, int32_t H, int32_t W, int32_t ci, int32_t co) {
+  if (B < 1 || H < 1 || W < 1 || (long long)B * H * W >= (1LL << 31) / 96) return LBCH_EINVAL;
+  if (!channels_ok(ci) || !channels_ok(co)) return LBCH_EINVAL;
+  return LBCH_OK;
+}
+
+lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float* d_bias, int32_t B, int32_t H,
+                          int32_t W, int32_t c_in, int32_t c_out, float* d_y, void* cuda_stream) {
+  if (!d_x || !d_w || !d_y || op_check(B, H, W, c_in, c_out) != LBCH_OK) return LBCH_EINVAL;
+  ConvArgs a{};
+  a.x = (const bf16*)d_x;
+  a.w = (const bf16*)d_w;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.bias = d_bias;
+  a.yf = d_y;
+  conv_launch(c_in, c_out, false, a, (cudaStream_t)cuda_stream);
+  return cudaGetLastError() == cudaSuccess ? LBCH_OK : LBCH_ECUDA;
+}
+
+lbch_status lbnop_conv3x3_bwd_data(const uint16_t* d_dy, const uint16_t* d_w, int32_t B, int32_t H, int32_t W,
+                                   int32_t c_in, int32_t c_out, float* d_dx, void* cuda_stream) {
+  if (!d_dy || !d_w || !d_dx || op_check(B, H, W, c_in, c_out) != LBCH_OK) return LBCH_EINVAL;
+  ConvArgs a{};
+  a.x = (const bf16*)d_dy;
+  a.w = (const bf16*)d_w;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.yf = d_dx;
+  conv_launch(c_out, c_in, true, a, (cudaStream_t)cuda_stream);
+  return cudaGetLastError() == cudaSuccess ? LBCH_OK : LBCH_ECUDA;
+}
+
+lbch_status lbnop_conv3x3_bwd_weight(const uint16_t* d_x, const uint16_t* d_dy, int32_t B, int32_t H, int32_t W,
+                                     int32_t c_in, int32_t c_out, float* d_dw, void* cuda_stream) {
+  if (!d_x || !d_dy || !d_dw || op_check(B, H, W, c_in, c_out) != LBCH_OK) return LBCH_EINVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (cudaMemsetAsync(d_dw, 0, (size_t)9 * c_in * c_out * sizeof(float), s) != cudaSuccess) return LBCH_ECUDA;
+  WgradArgs a{};
+  a.x = (const bf16*)d_x;
+  a.dz = (const bf16*)d_dy;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.chunk = wgrad_chunk(B * H * W);
+  a.dw = d_dw;
+  wgrad_launch(c_in, c_out, a, s);
+  return cudaGetLastError() == cudaSuccess ? LBCH_OK : LBCH_ECUDA;
+}
+
+const char* lbnop_last_error(const lbnop_ctx* c) { return c ? c->err : "context is NULL"; }
+
+void lbnop_destroy(lbnop_ctx* c) { delete c; }
+
+}  // extern "C"

@@ -120,6 +120,11 @@ def load():
             getattr(lib, name).restype = ctypes.c_int
         lib.lbch_step.argtypes = [vp, ctypes.c_int64]
         lib.lbch_step.restype = ctypes.c_int
+        for name in ("lbch_init_field_device", "lbch_get_phi_device"):
+            getattr(lib, name).argtypes = [vp, vp]
+            getattr(lib, name).restype = ctypes.c_int
+        lib.lbch_batch_get_phi_device.argtypes = [vp, ctypes.c_int32, vp]
+        lib.lbch_batch_get_phi_device.restype = ctypes.c_int
         lib.lbch_steps_taken.argtypes = [vp]
         lib.lbch_steps_taken.restype = ctypes.c_int64
         lib.lbch_last_error.argtypes = [vp]
@@ -189,6 +194,15 @@ def _as_host_f64(a, n: int, what: str) -> np.ndarray:
     return a
 
 
+def _check_device_f32(t, n: int, what: str) -> None:
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{what}: expected a contiguous float32 CUDA tensor")
+    if t.numel() != n:
+        raise ValueError(f"{what}: expected {n} values, got {t.numel()}")
+
+
 # ---------------------------------------------------------------- C-ABI, same names
 
 def lbch_workspace_bytes(p: lbch_params) -> int:
@@ -205,6 +219,14 @@ def lbch_create(p: lbch_params, d_workspace: int, nbytes: int, cuda_stream: int 
 
 def lbch_init_field(ctx, phi0) -> None:
     _check(ctx, load().lbch_init_field(ctx, _host_ptr(phi0)), "lbch_init_field")
+
+
+def lbch_init_field_device(ctx, d_phi0: int) -> None:
+    _check(ctx, load().lbch_init_field_device(ctx, ctypes.c_void_p(int(d_phi0))), "lbch_init_field_device")
+
+
+def lbch_get_phi_device(ctx, d_phi: int) -> None:
+    _check(ctx, load().lbch_get_phi_device(ctx, ctypes.c_void_p(int(d_phi))), "lbch_get_phi_device")
 
 
 def lbch_step(ctx, n: int) -> None:
@@ -298,6 +320,23 @@ class Solver:
         with self._on_device():
             lbch_step(self.ctx, n)
 
+    def init_field_device(self, phi0) -> None:
+        """f = f^eq(phi0) from a contiguous float32 CUDA tensor of shape (ny, nx)."""
+        _check_device_f32(phi0, self.nx * self.ny, "phi0")
+        with self._on_device():
+            lbch_init_field_device(self.ctx, phi0.data_ptr())
+
+    def phi_device(self, out=None):
+        """phi = sum_i f_i into a float32 CUDA tensor (ny, nx) (allocated if out is None)."""
+        import torch
+
+        if out is None:
+            out = torch.empty((self.ny, self.nx), dtype=torch.float32, device=self.device)
+        _check_device_f32(out, self.nx * self.ny, "out")
+        with self._on_device():
+            lbch_get_phi_device(self.ctx, out.data_ptr())
+        return out
+
     def mass(self) -> float:
         with self._on_device():
             return lbch_mass(self.ctx)
@@ -384,6 +423,11 @@ def lbch_batch_get_field(b, i: int, out: np.ndarray) -> np.ndarray:
     return out
 
 
+def lbch_batch_get_phi_device(b, i: int, d_phi: int) -> None:
+    _batch_check(b, load().lbch_batch_get_phi_device(b, int(i), ctypes.c_void_p(int(d_phi))),
+                 "lbch_batch_get_phi_device")
+
+
 def lbch_batch_mass(b, i: int) -> float:
     v = ctypes.c_double()
     _batch_check(b, load().lbch_batch_mass(b, int(i), ctypes.byref(v)), "lbch_batch_mass")
@@ -445,6 +489,12 @@ class Batch:
     def step(self, n: int) -> None:
         with self._on_device():
             lbch_batch_step(self.handle, n)
+
+    def phi_device(self, i: int, out) -> None:
+        """phi of field i into a contiguous float32 CUDA tensor of ny[i] x nx[i] values."""
+        _check_device_f32(out, self.nx[i] * self.ny[i], "out")
+        with self._on_device():
+            lbch_batch_get_phi_device(self.handle, i, out.data_ptr())
 
     def field(self, i: int) -> np.ndarray:
         out = np.empty((self.ny[i], self.nx[i]), dtype=np.float64)

@@ -1,0 +1,25 @@
+"""Host-side checks of the learned leap's C-ABI (no GPU): parameter count, workspace
+sizing and parameter validation."""
+import pytest
+
+from oracle import nop_oracle as N
+from paper_2501_03759_gb300 import lbnop
+
+
+def test_param_count_matches_the_layout():
+    assert lbnop.lbnop_param_count() == N.param_count() == 581520
+
+
+@pytest.mark.parametrize("H,W,B,scale", [(31, 64, 1, 0.1), (64, 48, 1, 0.1), (64, 64, 0, 0.1), (64, 64, 65, 0.1),
+                                         (64, 64, 1, 0.0), (64, 64, 1, float("nan")), (16, 16, 1, 0.1)])
+def test_invalid_params_have_no_workspace(H, W, B, scale):
+    assert lbnop.lbnop_workspace_bytes(lbnop.make_params(H, W, B, scale)) == 0
+
+
+def test_workspace_grows_with_batch_and_size():
+    a = lbnop.lbnop_workspace_bytes(lbnop.make_params(64, 64, 1))
+    b = lbnop.lbnop_workspace_bytes(lbnop.make_params(64, 64, 4))
+    c = lbnop.lbnop_workspace_bytes(lbnop.make_params(128, 128, 4))
+    assert 0 < a < b < c
+    # parameters, Adam state and gradients alone: 4 FP32 copies
+    assert a > 4 * 4 * N.param_count()

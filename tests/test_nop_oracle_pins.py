@@ -1,7 +1,7 @@
 """Pins of the learned-leap oracle (oracle/nop_oracle.py) against facts that do not
 depend on it: FFT circular correlation, adjoint (dot-product) identities, central
 finite differences of the whole network's loss, exact mass conservation of the
-head, and the closed form of Adam's first steps."""
+head, the closed form of Adam's first steps, and BF16 round-to-nearest-even cases."""
 import numpy as np
 import pytest
 
@@ -149,3 +149,9 @@ def test_shapes(H, W):
     theta = rand_theta(5)
     out, _ = N.forward(theta, rng.uniform(-1, 1, (1, H, W)), [0.3], 0.1)
     assert out.shape == (1, H, W)
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    x = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -9, 1 + 3 * 2 ** -8, -(1 + 2 ** -7 + 2 ** -9), 2.0 ** -130])
+    want = np.array([1.0, 1.0, 1 + 2 ** -7, 1 + 2 ** -6, -(1 + 2 ** -7), 2.0 ** -130])
+    assert np.array_equal(N.bf16(x), want)

@@ -88,3 +88,29 @@ def batch_field(spec) -> np.ndarray:
     if spec["kind"] == "droplet":
         return droplet(n, n, radius=0.3 * n, width=np.sqrt(2.0) * 1.5)
     return noise(n, n, 0.05, spec["seed"])
+
+
+def bf16_exact(shape, seed: int, scale: float, levels: int = 64) -> np.ndarray:
+    """Seeded values k * scale / levels with integer k in [-levels, levels]: with levels <= 128
+    and scale a power of two every value has at most 8 significant bits, so it is exact in
+    BF16 and products of two such values are exact in FP32 (operator test inputs)."""
+    r = np.random.default_rng(seed)
+    return r.integers(-levels, levels + 1, size=shape).astype(np.float64) * (scale / levels)
+
+
+def surrogate_theta(seed: int, out_scale: float = 1.0) -> np.ndarray:
+    """A seeded parameter vector for the learned leap (flat layout of include/lbnop.h):
+    He-normal 3 x 3 weights (std sqrt(2 / (9 c_in))), the output layer's scaled by
+    out_scale, biases N(0, 0.01), conditioning vector N(0, 0.25), rounded to float32."""
+    layers = [(16, 32), (32, 32), (32, 64), (64, 64), (64, 96), (96, 96), (96, 96), (96, 96),
+              (96, 96), (96, 64), (64, 64), (64, 32), (32, 32), (32, 16)]
+    r = np.random.default_rng(seed)
+    parts = []
+    for k, (ci, co) in enumerate(layers):
+        w = r.normal(0.0, (2.0 / (9 * ci)) ** 0.5, 9 * co * ci)
+        if k == len(layers) - 1:
+            w *= out_scale
+        parts += [w, r.normal(0.0, 0.1, co)]
+        if k == 0:
+            parts.append(r.normal(0.0, 0.5, co))
+    return np.concatenate(parts).astype(np.float32).astype(np.float64)
