@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--no-3d", action="store_true", help="skip the D3Q15 measurement")
     ap.add_argument("--n3", type=int, default=256, help="edge of the D3Q15 spinodal cube (default 256)")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-leap time-to-t measurement")
     ap.add_argument("--storage", choices=["f32", "bf16_dev", "f16_dev"], default="f32",
                     help="population storage of the main timed line")
     return ap.parse_args()
@@ -283,6 +284,25 @@ def run_3d(lbch, torch, n: int, steps: int):
             "launch": "three kernels per step (phi; mu_alpha and mu_beta by a z-sweep; collide and store)"}
 
 
+SURROGATE_THETA = os.path.join(ROOT, "paper_2501_03759_gb300", "weights", "leap512_k500.npy")
+
+
+def run_surrogate(alpha: float = 0.3, seed: int = 777):
+    """Time-to-t of the learned leap against the plain LBM on a held-out 512^2 spinodal field
+    to t = 50000 (500 LBM steps, then 90 x (one 500-step leap + 50 LBM steps)), with the
+    committed trained parameters; None if they are absent."""
+    if not os.path.exists(SURROGATE_THETA):
+        return None
+    from paper_2501_03759_gb300 import surrogate
+
+    r = surrogate.evaluate(np.load(SURROGATE_THETA), alpha, seed)
+    r["gates"] = {"phi_rel_l2_max": 5e-2, "energy_rel_diff_max": 1e-2, "speedup_min": 5.0,
+                  "pass": bool(r["phi_rel_l2"] <= 5e-2 and r["energy_rel_diff"] <= 1e-2 and r["speedup"] >= 5.0)}
+    r["workload"] = "spinodal-512x512 learned leap K=500 + 50 LBM steps to t=50000"
+    r["weights"] = os.path.relpath(SURROGATE_THETA, ROOT)
+    return r
+
+
 def cpu_oracle_rate(target_s: float = 12.0, n_sample: int = 2048):
     """The FP64 oracle, as it stands, on the host cores: MLUPS on an n_sample^2 spinodal
     sample of the workload (alpha 0.3, noise 0.05, seed 0)."""
@@ -422,6 +442,10 @@ def main():
         d3 = run_3d(lbch, torch, args.n3, 50)
         d3["paper_100"] = run_3d(lbch, torch, 100, 200)["value"]
 
+    leap = None
+    if not args.no_surrogate and rank == 0:
+        leap = run_surrogate()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate()
@@ -441,6 +465,7 @@ def main():
             "variants": variants,
             "batch_sweep": batch,
             "d3q15": d3,
+            "surrogate": leap,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),

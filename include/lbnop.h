@@ -8,9 +8,13 @@
  * lbch context.
  *
  * Network (the flat parameter layout below follows this table, in this order):
- *   phi (H x W, FP32) -> 4 x 4 space-to-depth -> 16 channels at level 0 (H/4 x W/4)
+ *   sig = root mean square of phi (1 for a zero field)
+ *   phi / sig (H x W, FP32) -> 4 x 4 space-to-depth -> 16 channels at level 0 (H/4 x W/4)
  *   layer  c_in c_out level activation
- *   e0a      16   32   0   SiLU  (its pre-activation also gets alpha v, alpha of Eq. 6)
+ *   e0a      16   32   0   SiLU  (its pre-activation also gets alpha v, alpha of Eq. 6;
+ *                               its input is stored as two BF16 halves, hi = bf16(x) and
+ *                               lo = bf16(x - hi), both multiplied by its weights; so is
+ *                               the input of lin and lina)
  *   e0b      32   32   0   SiLU  -> h0
  *   e1a      32   64   1   SiLU  (input: 2 x 2 average pool of h0)
  *   e1b      64   64   1   SiLU  -> h1
@@ -23,11 +27,15 @@
  *   d1a      64   64   1   SiLU  (input: upsampled d2b output, plus h1)
  *   d1b      64   32   1   none
  *   d0a      32   32   0   SiLU  (input: upsampled d1b output, plus h0)
- *   out      32   16   0   none  -> 4 x 4 depth-to-space -> D (H x W)
- *   phi_out = phi + scale (D - mean D)  (mean over the field, so mass is conserved)
+ *   out      32   16   0   none
+ *   lin      16   16   0   none  (input: the e0a input; a linear path whose weights are
+ *                               also kept as two BF16 halves, hi and lo = bf16(w - hi))
+ *   lina     16   16   0   none  (input: the e0a input; output multiplied by alpha)
+ *   out + lin + lina -> 4 x 4 depth-to-space -> D (H x W)
+ *   phi_out = phi + scale sig (D - mean D)  (mean over the field, so mass is conserved)
  * Every layer is a 3 x 3 cross-correlation with periodic wrap plus a bias:
  *   z(p) = sum_{(dy, dx) in {-1,0,1}^2} W[3 (dy + 1) + (dx + 1)] x(p + (dy, dx)) + b.
- * Flat parameters (FP32, 581,520 values): for each layer in table order, W as
+ * Flat parameters (FP32, 586,160 values): for each layer in table order, W as
  * [9][c_out][c_in], then b [c_out]; after e0a's bias, its conditioning vector v [c_out].
  *
  * Arithmetic: the convolutions are implicit GEMMs on BF16 tensor-core operands with FP32
@@ -54,10 +62,10 @@ typedef struct lbnop_ctx lbnop_ctx;
 typedef struct {
   int32_t H, W;          /* field size, multiples of 32, each in [32, 8192] */
   int32_t max_batch;     /* fields per forward or training step, in [1, LBNOP_MAX_BATCH] */
-  double scale;          /* phi_out = phi + scale (D - mean D); > 0 */
+  double scale;          /* phi_out = phi + scale sig (D - mean D); > 0 */
 } lbnop_params;
 
-/* Number of FP32 parameters (581,520). */
+/* Number of FP32 parameters (586,160). */
 int64_t lbnop_param_count(void);
 
 /* Device workspace for these parameters (weights, Adam state, activations and gradients
@@ -78,11 +86,12 @@ lbch_status lbnop_get_params(lbnop_ctx* c, float* h_theta);   /* synchronises */
 lbch_status lbnop_forward(lbnop_ctx* c, const float* d_phi, const double* h_alpha, int32_t batch,
                           float* d_phi_out);
 
-/* Forward, loss = mean over all nodes of (phi_out - target)^2, and its gradient in the
- * parameters (kept in the context; read with lbnop_get_grads). d_target: device FP32
- * [batch][H][W]. Writes the loss to *h_loss if h_loss is not NULL (synchronises then). */
+/* Forward, loss = sum_b w_b sum_x (phi_out - target)^2 / (batch H W), and its gradient in
+ * the parameters (kept in the context; read with lbnop_get_grads). d_target: device FP32
+ * [batch][H][W]; h_weight: host, batch weights w_b >= 0, or NULL for all ones. Writes the
+ * loss to *h_loss if h_loss is not NULL (synchronises then). */
 lbch_status lbnop_backward(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,
-                           int32_t batch, double* h_loss);
+                           const double* h_weight, int32_t batch, double* h_loss);
 lbch_status lbnop_get_grads(lbnop_ctx* c, float* h_grad);     /* synchronises */
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with learning rate lr
@@ -91,7 +100,7 @@ lbch_status lbnop_adam(lbnop_ctx* c, double lr);
 
 /* lbnop_backward followed by lbnop_adam. */
 lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,
-                             int32_t batch, double lr, double* h_loss);
+                             const double* h_weight, int32_t batch, double lr, double* h_loss);
 
 /* Runs `cycles` times: one leap of the network on the field of `lbm` (phi = sum f),
  * f = f^eq(phi_out) as in lbch_init_field, then lbm_steps steps of the scheme. The lbch

@@ -49,6 +49,8 @@ LAYERS = [
     ("d1b", 64, 32, 1, False),
     ("d0a", 32, 32, 0, True),
     ("out", 32, 16, 0, False),
+    ("lin", 16, 16, 0, False),    # linear path from the network input
+    ("lina", 16, 16, 0, False),   # the same, its output multiplied by alpha
 ]
 TAPS = [(dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
 
@@ -167,12 +169,20 @@ def _identity(a):
     return a
 
 
+def rms(phi: np.ndarray) -> np.ndarray:
+    """Root mean square of each field, shape (B, 1, 1); 1 for a zero field."""
+    r = np.sqrt(np.mean(phi * phi, axis=(1, 2), keepdims=True))
+    return np.where(r > 1e-30, r, 1.0)
+
+
 def forward(theta: np.ndarray, phi: np.ndarray, alpha: np.ndarray, scale: float, quantize=None):
-    """phi_out = phi + scale (D - mean D), D = d2s(U-Net(s2d(phi), alpha)).
+    """phi_out = phi + scale sig (D - mean D), D = d2s(U-Net(s2d(phi / sig), alpha)), sig the
+    root mean square of each field (so the network sees fields of unit size).
 
     quantize (default: none) is applied where the CUDA path stores BF16: the weights, the
-    network input, every activation, pooled and summed tensor, and linear layer output.
-    Returns phi_out and the saved tensors the backward pass needs.
+    network input (as a rounded value plus its rounded remainder), every activation, pooled
+    and summed tensor, and linear layer output. Returns phi_out and the saved tensors the
+    backward pass needs.
     """
     Q = quantize or _identity
     P = unpack(theta)
@@ -182,15 +192,19 @@ def forward(theta: np.ndarray, phi: np.ndarray, alpha: np.ndarray, scale: float,
     def layer(name, x):
         W, b = Q(P[name][0]), P[name][1]
         z = conv(x, W, b)
-        if name == "e0a":
-            z = z + alpha * P[name][2]
+        if name == "e0a":  # the input's BF16 remainder, by the same weights (0 without quantize)
+            z = z + conv(s["x0_lo"], W) + alpha * P[name][2]
         s["in_" + name], s["z_" + name] = x, z
         act = dict((l[0], l[4]) for l in LAYERS)[name]
         if name == "out":
             return z
         return Q(silu(z)) if act else Q(z)
 
-    x0 = Q(s2d(phi))
+    sig = rms(phi)
+    s["sig"] = sig
+    x0f = s2d(phi / sig)
+    x0 = Q(x0f)
+    s["x0_lo"] = Q(x0f - x0)
     h0 = layer("e0b", layer("e0a", x0))
     h1 = layer("e1b", layer("e1a", Q(pool(h0))))
     h2 = layer("e2b", layer("e2a", Q(pool(h1))))
@@ -198,16 +212,26 @@ def forward(theta: np.ndarray, phi: np.ndarray, alpha: np.ndarray, scale: float,
     zd2 = layer("d2b", layer("d2a", Q(up(h3) + h2)))
     zd1 = layer("d1b", layer("d1a", Q(up(zd2) + h1)))
     zo = layer("out", layer("d0a", Q(up(zd1) + h0)))
+    for name in ("lin", "lina"):  # linear path: W x0 + b, times alpha for lina
+        Wf, b = P[name][0], P[name][1]
+        W = Q(Wf)
+        W_lo = Q(Wf - W)  # with BF16 storage the weights are kept as two halves too
+        zl = conv(x0, W, b) + conv(s["x0_lo"], W) + conv(x0, W_lo)
+        zo = zo + (alpha * zl if name == "lina" else zl)
+    s["in_lin"] = s["in_lina"] = x0
     D = d2s(zo)
     D = D - D.mean(axis=(1, 2), keepdims=True)
     s["alpha"] = alpha
-    return phi + scale * D, s
+    return phi + scale * sig * D, s
 
 
-def loss(phi_out: np.ndarray, target: np.ndarray) -> tuple[float, np.ndarray]:
-    """Mean squared error over all nodes and samples, and its gradient in phi_out."""
+def loss(phi_out: np.ndarray, target: np.ndarray, weight=None) -> tuple[float, np.ndarray]:
+    """sum_b w_b sum_x (phi_out - target)^2 / (B H W) (w_b = 1 by default: the mean squared
+    error), and its gradient in phi_out."""
     d = phi_out - target
-    return float(np.mean(d * d)), 2.0 * d / d.size
+    w = np.ones(d.shape[0]) if weight is None else np.asarray(weight, dtype=np.float64)
+    w = w.reshape(-1, 1, 1)
+    return float(np.sum(w * d * d) / d.size), 2.0 * w * d / d.size
 
 
 def backward(theta: np.ndarray, s: dict, dphi_out: np.ndarray, scale: float) -> np.ndarray:
@@ -223,12 +247,18 @@ def backward(theta: np.ndarray, s: dict, dphi_out: np.ndarray, scale: float) -> 
         W = Q(P[name][0])
         grads = [conv_bwd_weight(x, dz), dz.sum(axis=(0, 1, 2))]
         if name == "e0a":
+            grads[0] = grads[0] + conv_bwd_weight(s["x0_lo"], dz)
             grads.append((dz * s["alpha"]).sum(axis=(0, 1, 2)))
         G[name] = grads
         return conv_bwd_data(dz, W)
 
-    dD = scale * (dphi_out - dphi_out.mean(axis=(1, 2), keepdims=True))
+    dD = scale * s["sig"] * (dphi_out - dphi_out.mean(axis=(1, 2), keepdims=True))
     g = s2d(dD)  # adjoint of d2s (quantised as the output layer's dz)
+    for name in ("lin", "lina"):
+        dz = Q(g)
+        if name == "lina":
+            dz = Q(s["alpha"] * dz)
+        G[name] = [conv_bwd_weight(s["in_" + name], dz) + conv_bwd_weight(s["x0_lo"], dz), dz.sum(axis=(0, 1, 2))]
     g = layer_bwd("out", g, False)
     g_in_d0a = layer_bwd("d0a", g, True)
     g_h0 = g_in_d0a.copy()

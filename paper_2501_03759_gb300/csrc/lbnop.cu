@@ -24,7 +24,7 @@ namespace nop {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int NL = 14;
+constexpr int NL = 16;
 struct LayerSpec {
   int ci, co, level;
   bool act;
@@ -33,8 +33,8 @@ struct LayerSpec {
 constexpr LayerSpec kL[NL] = {{16, 32, 0, true},  {32, 32, 0, true},  {32, 64, 1, true},  {64, 64, 1, true},
                               {64, 96, 2, true},  {96, 96, 2, true},  {96, 96, 3, true},  {96, 96, 3, true},
                               {96, 96, 2, true},  {96, 64, 2, false}, {64, 64, 1, true},  {64, 32, 1, false},
-                              {32, 32, 0, true},  {32, 16, 0, false}};
-enum { E0A, E0B, E1A, E1B, E2A, E2B, M3A, M3B, D2A, D2B, D1A, D1B, D0A, OUT };
+                              {32, 32, 0, true},  {32, 16, 0, false}, {16, 16, 0, false}, {16, 16, 0, false}};
+enum { E0A, E0B, E1A, E1B, E2A, E2B, M3A, M3B, D2A, D2B, D1A, D1B, D0A, OUT, LIN, LINA };
 
 struct LayerTab {
   int off_w[NL], ci[NL], co[NL], woff[NL];
@@ -79,8 +79,10 @@ __device__ __forceinline__ void ldsm_x2_t(uint32_t& r0, uint32_t& r1, const bf16
 // ---------------------------------------------------------------- convolution (forward, data grad)
 
 struct ConvArgs {
-  const bf16* x;  // [B][H][W][CI]
+  const bf16* x;   // [B][H][W][CI]
+  const bf16* x2;  // or null: a second input of the same shape, multiplied by the same weights
   const bf16* w;  // TW = false: [9][CO][CI]; TW = true: [9][CI][CO], read at tap 8 - t
+  const bf16* w2;  // or null: the BF16 remainder of the weights (w + w2 ~ 16 bits), applied to x
   int B, H, W;
   const float* bias;  // [CO] or null
   const float* film;  // [CO] or null: adds alpha[b] film[n]
@@ -88,21 +90,26 @@ struct ConvArgs {
   bf16* a;            // BF16 SiLU(z) out, or null
   float* yf;          // FP32 out, or null
   int accumulate;     // yf += instead of yf =
+  int scale_alpha;    // multiply the result (after bias) by alpha[b]
   float alpha[LBNOP_MAX_BATCH];
 };
 
 constexpr int CONV_THREADS = 128;  // four warps, 16 pixels each
 
-// Each warp computes 16 consecutive pixels x CO channels; A fragments come straight from
-// the channels-last input (32-bit pairs of channels), B fragments from the weights (L1).
-template <int CI, int CO, bool TW>
+// Each warp computes 16 consecutive pixels x BN output channels (the block's channel
+// slice blockIdx.y); A fragments come straight from the channels-last input (32-bit
+// pairs of channels), B fragments from the weights (L1-resident). The K loop (9 taps x
+// CI / 16) is unrolled with the fragments of step k + 1 loaded while step k multiplies.
+template <int CI, int CO, int BN, bool TW, bool DUAL, bool WLO = false>
 __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(const ConvArgs p) {
-  constexpr int NT = CO / 8;
+  constexpr int NT = BN / 8, CPT = CI / 16, KS = 9 * CPT, KT = KS * (1 + (DUAL ? 1 : 0) + (WLO ? 1 : 0));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
   const int HW = p.H * p.W, npix = p.B * HW;
   const int base = (blockIdx.x * 4 + warp) * 16;
+  const int n0 = blockIdx.y * BN;
   if (base >= npix) return;
-  int bi[2], hi[2], wi[2];
+  int bi[2];
+  int off[2][9];  // element offset of (row r's pixel + tap offset, channel 2q)
   bool ok[2];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -110,49 +117,56 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(const ConvArgs p) {
     ok[r] = pix < npix;
     pix = ok[r] ? pix : base;  // out-of-range rows load a valid pixel; their results are dropped
     bi[r] = pix / HW;
-    const int rem = pix - bi[r] * HW;
-    hi[r] = rem / p.W;
-    wi[r] = rem - hi[r] * p.W;
+    const int rem = pix - bi[r] * HW, h = rem / p.W, w = rem - h * p.W;
+#pragma unroll
+    for (int t = 0; t < 9; ++t)
+      off[r][t] = ((bi[r] * p.H + wrap1(h + t / 3 - 1, p.H)) * p.W + wrap1(w + t % 3 - 1, p.W)) * CI + 2 * q;
   }
+  // passes of KS steps: (x, w), then (x2, w) if DUAL, then (x, w2) if WLO
+  auto load = [&](int kk, uint32_t (&a)[4], uint32_t (&b)[NT][2]) {
+    const int pass = kk / KS, ks = kk % KS;
+    const bool second_x = DUAL && pass == 1;
+    const bool second_w = WLO && pass == (DUAL ? 2 : 1);
+    const bf16* x = second_x ? p.x2 : p.x;
+    const bf16* wbase = second_w ? p.w2 : p.w;
+    const int t = ks / CPT, c0 = (ks % CPT) * 16;
+    a[0] = ld32(x + off[0][t] + c0);
+    a[1] = ld32(x + off[1][t] + c0);
+    a[2] = ld32(x + off[0][t] + c0 + 8);
+    a[3] = ld32(x + off[1][t] + c0 + 8);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      if constexpr (!TW) {
+        const bf16* wr = wbase + ((size_t)t * CO + n0 + 8 * j + g) * CI + c0 + 2 * q;
+        b[j][0] = ld32(wr);
+        b[j][1] = ld32(wr + 8);
+      } else {
+        const bf16* wr = p.w + ((size_t)(8 - t) * CI + c0 + 2 * q) * CO + n0 + 8 * j + g;
+        b[j][0] = pack2(wr[0], wr[CO]);
+        b[j][1] = pack2(wr[8 * CO], wr[9 * CO]);
+      }
+    }
+  };
   float acc[NT][4];
 #pragma unroll
   for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-
-#pragma unroll 1
-  for (int t = 0; t < 9; ++t) {
-    const int dy = t / 3 - 1, dx = t % 3 - 1;
-    const bf16* xr[2];
+  uint32_t a[2][4], b[2][NT][2];
+  load(0, a[0], b[0]);
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
-      xr[r] = p.x + ((size_t)(bi[r] * p.H + wrap1(hi[r] + dy, p.H)) * p.W + wrap1(wi[r] + dx, p.W)) * CI + 2 * q;
+  for (int kk = 0; kk < KT; ++kk) {
+    if (kk + 1 < KT) load(kk + 1, a[(kk + 1) & 1], b[(kk + 1) & 1]);
 #pragma unroll
-    for (int c0 = 0; c0 < CI; c0 += 16) {
-      const uint32_t a[4] = {ld32(xr[0] + c0), ld32(xr[1] + c0), ld32(xr[0] + c0 + 8), ld32(xr[1] + c0 + 8)};
-#pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        uint32_t b0, b1;
-        if constexpr (!TW) {
-          const bf16* wr = p.w + ((size_t)t * CO + 8 * j + g) * CI + c0 + 2 * q;
-          b0 = ld32(wr);
-          b1 = ld32(wr + 8);
-        } else {
-          const bf16* wr = p.w + ((size_t)(8 - t) * CI + c0 + 2 * q) * CO + 8 * j + g;
-          b0 = pack2(wr[0], wr[CO]);
-          b1 = pack2(wr[8 * CO], wr[9 * CO]);
-        }
-        mma_bf16(acc[j], a, b0, b1);
-      }
-    }
+    for (int j = 0; j < NT; ++j) mma_bf16(acc[j], a[kk & 1], b[kk & 1][j][0], b[kk & 1][j][1]);
   }
 
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     if (!ok[r]) continue;
     const int pix = base + g + 8 * r;
-    const float al = p.film ? p.alpha[bi[r]] : 0.0f;
+    const float al = p.film ? p.alpha[bi[r]] : 0.0f;  // bi[r] is the row's sample
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
-      const int n = 8 * j + 2 * q;
+      const int n = n0 + 8 * j + 2 * q;
       float v0 = acc[j][2 * r], v1 = acc[j][2 * r + 1];
       if (p.bias) {
         v0 += p.bias[n];
@@ -161,6 +175,10 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(const ConvArgs p) {
       if (p.film) {
         v0 = fmaf(al, p.film[n], v0);
         v1 = fmaf(al, p.film[n + 1], v1);
+      }
+      if (p.scale_alpha) {
+        v0 *= p.alpha[bi[r]];
+        v1 *= p.alpha[bi[r]];
       }
       const size_t o = (size_t)pix * CO + n;
       if (p.yf) {
@@ -257,23 +275,44 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const WgradArgs p) {
 
 // ---------------------------------------------------------------- elementwise and reductions
 
-// phi [B][H][W] FP32 -> x0 [B][H/4][W/4][16] BF16, channel 4 di + dj = phi[4 i + di][4 j + dj].
-__global__ void s2d_kernel(const float* __restrict__ phi, int B, int H, int W, bf16* __restrict__ x0) {
+constexpr int HEAD_BLOCKS = 32;  // partial sums per sample (fixed order: deterministic)
+
+// sig[b] = root mean square of field b from its sum of squares (1 for a zero field).
+__global__ void rms_kernel(const double* __restrict__ partial2, int B, long long n, double* __restrict__ sig) {
+  const int b = threadIdx.x;
+  if (blockIdx.x != 0 || b >= B) return;
+  double s = 0.0;
+  for (int k = 0; k < HEAD_BLOCKS; ++k) s += partial2[b * HEAD_BLOCKS + k];
+  const double r = sqrt(s / (double)n);
+  sig[b] = r > 1e-30 ? r : 1.0;
+}
+
+// x = phi / sig[b] ([B][H][W] FP32) -> [B][H/4][W/4][16], channel 4 di + dj = x[4 i + di][4 j + dj],
+// as two BF16 tensors: x0 = bf16(x) and x0l = bf16(x - x0) (together about 16 bits).
+__global__ void s2d_kernel(const float* __restrict__ phi, const double* __restrict__ sig, int B, int H, int W,
+                           bf16* __restrict__ x0, bf16* __restrict__ x0l) {
   const int h = H / 4, w = W / 4, n = B * h * w;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int b = k / (h * w), rem = k - b * h * w, i = rem / w, j = rem - i * w;
+    const float inv = (float)(1.0 / sig[b]);
     __align__(16) bf16 v[16];
+    __align__(16) bf16 lo[16];
 #pragma unroll
     for (int di = 0; di < 4; ++di) {
       const float4 r = *reinterpret_cast<const float4*>(phi + ((size_t)b * H + 4 * i + di) * W + 4 * j);
-      v[4 * di + 0] = __float2bfloat16_rn(r.x);
-      v[4 * di + 1] = __float2bfloat16_rn(r.y);
-      v[4 * di + 2] = __float2bfloat16_rn(r.z);
-      v[4 * di + 3] = __float2bfloat16_rn(r.w);
+      const float e[4] = {r.x * inv, r.y * inv, r.z * inv, r.w * inv};
+#pragma unroll
+      for (int dj = 0; dj < 4; ++dj) {
+        v[4 * di + dj] = __float2bfloat16_rn(e[dj]);
+        lo[4 * di + dj] = __float2bfloat16_rn(e[dj] - __bfloat162float(v[4 * di + dj]));
+      }
     }
     uint4* dst = reinterpret_cast<uint4*>(x0 + (size_t)k * 16);
     dst[0] = reinterpret_cast<const uint4*>(v)[0];
     dst[1] = reinterpret_cast<const uint4*>(v)[1];
+    uint4* dl = reinterpret_cast<uint4*>(x0l + (size_t)k * 16);
+    dl[0] = reinterpret_cast<const uint4*>(lo)[0];
+    dl[1] = reinterpret_cast<const uint4*>(lo)[1];
   }
 }
 
@@ -368,7 +407,6 @@ __global__ void colsum_kernel(const ColsumArgs a) {
   }
 }
 
-constexpr int HEAD_BLOCKS = 32;  // partial sums per sample (fixed order: deterministic)
 
 __device__ __forceinline__ double block_sum_d(double v, double* sh) {
 #pragma unroll
@@ -408,44 +446,60 @@ __global__ void sample_sums_kernel(const float* __restrict__ v, const float* __r
   }
 }
 
-// mean[b] = sum of partial[b][*] / n; with partial2, loss = sum over all of partial2 / (B n).
+struct SampleWeights {
+  float v[LBNOP_MAX_BATCH];
+};
+
+// y[b][k] = bf16(w[b] x[b][k]) for `per` values per sample.
+__global__ void scale_rows_kernel(const bf16* __restrict__ x, long long per, int B, const SampleWeights w,
+                                  bf16* __restrict__ y) {
+  const long long n = per * B;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+    y[k] = __float2bfloat16_rn(w.v[k / per] * __bfloat162float(x[k]));
+}
+
+// mean[b] = sum of partial[b][*] / n; with partial2, loss = sum_b w[b] partial2[b][*] / (B n).
 __global__ void finish_sums_kernel(const double* __restrict__ partial, const double* __restrict__ partial2, int B,
-                                   long long n, double* __restrict__ mean, double* __restrict__ loss) {
+                                   long long n, const SampleWeights w, double* __restrict__ mean,
+                                   double* __restrict__ loss) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double tot2 = 0.0;
   for (int b = 0; b < B; ++b) {
-    double s = 0.0;
+    double s = 0.0, s2 = 0.0;
     for (int k = 0; k < HEAD_BLOCKS; ++k) {
       s += partial[b * HEAD_BLOCKS + k];
-      if (partial2) tot2 += partial2[b * HEAD_BLOCKS + k];
+      if (partial2) s2 += partial2[b * HEAD_BLOCKS + k];
     }
     mean[b] = s / (double)n;
+    tot2 += (double)w.v[b] * s2;
   }
   if (partial2) *loss = tot2 / ((double)B * (double)n);
 }
 
-// phi_out = phi + scale (D - mean D), D = depth-to-space of zout [B][H/4][W/4][16].
+// phi_out = phi + scale sig[b] (D - mean D), D = depth-to-space of zout [B][H/4][W/4][16].
 __global__ void head_kernel(const float* __restrict__ phi, const float* __restrict__ zout,
-                            const double* __restrict__ mean, int B, int H, int W, float scale,
-                            float* __restrict__ phi_out) {
+                            const double* __restrict__ mean, const double* __restrict__ sig, int B, int H, int W,
+                            float scale, float* __restrict__ phi_out) {
   const long long n = (long long)B * H * W;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(k % W), y = (int)((k / W) % H), b = (int)(k / ((long long)W * H));
     const float D = zout[((size_t)(b * (H / 4) + y / 4) * (W / 4) + x / 4) * 16 + 4 * (y & 3) + (x & 3)];
-    phi_out[k] = phi[k] + scale * (D - (float)mean[b]);
+    phi_out[k] = phi[k] + scale * (float)sig[b] * (D - (float)mean[b]);
   }
 }
 
-// dz_out = space-to-depth of scale (g - mean g), g = 2 (phi_out - target) / (B H W) the
-// gradient of the mean squared error; mean_d[b] is the mean of (phi_out - target).
+// dz_out = space-to-depth of scale sig[b] (g - mean g), g = 2 w[b] (phi_out - target) / (B H W)
+// the gradient of the weighted mean squared error; mean_d[b] is the mean of
+// (phi_out - target) and coef[b] = 2 scale w[b] / (B H W).
 __global__ void head_bwd_kernel(const float* __restrict__ phi_out, const float* __restrict__ target,
-                                const double* __restrict__ mean_d, int B, int H, int W, float coef,
-                                bf16* __restrict__ dz) {
+                                const double* __restrict__ mean_d, const double* __restrict__ sig, int B, int H,
+                                int W, const SampleWeights coef, bf16* __restrict__ dz) {
   const long long n = (long long)B * H * W;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(k % W), y = (int)((k / W) % H), b = (int)(k / ((long long)W * H));
     const float d = (float)((double)phi_out[k] - (double)target[k] - mean_d[b]);
-    dz[((size_t)(b * (H / 4) + y / 4) * (W / 4) + x / 4) * 16 + 4 * (y & 3) + (x & 3)] = __float2bfloat16_rn(coef * d);
+    dz[((size_t)(b * (H / 4) + y / 4) * (W / 4) + x / 4) * 16 + 4 * (y & 3) + (x & 3)] =
+        __float2bfloat16_rn(coef.v[b] * (float)sig[b] * d);
   }
 }
 
@@ -453,7 +507,8 @@ __global__ void head_bwd_kernel(const float* __restrict__ phi_out, const float* 
 // then the BF16 copies of every weight: wf[t][co][ci] and wb[t][ci][co] = W[8 - t][co][ci].
 __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ grad, long long n, float lr, float c1, float c2, int update,
-                            const LayerTab tab, bf16* __restrict__ wf, bf16* __restrict__ wb) {
+                            const LayerTab tab, bf16* __restrict__ wf, bf16* __restrict__ wb,
+                            bf16* __restrict__ wlo) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     float th = theta[k];
     if (update) {
@@ -473,6 +528,7 @@ __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, fl
         const int o = r2 / ci, i = r2 - o * ci;
         const bf16 hv = __float2bfloat16_rn(th);
         wf[tab.woff[l] + rel] = hv;
+        wlo[tab.woff[l] + rel] = __float2bfloat16_rn(th - __bfloat162float(hv));
         wb[tab.woff[l] + ((size_t)(8 - t) * ci + i) * co + o] = hv;
         break;
       }
@@ -487,10 +543,38 @@ __global__ void finite_kernel(const float* __restrict__ v, long long n, int* bad
 
 // ---------------------------------------------------------------- launch helpers
 
+// Fields with few pixels (coarse levels, small batches) split the output channels over
+// blocks in slices of 16, so that enough warps run; large ones keep all channels per warp
+// and load each A fragment once.
 template <int CI, int CO, bool TW>
 void conv_t(const ConvArgs& a, cudaStream_t s) {
   const int npix = a.B * a.H * a.W;
-  conv_kernel<CI, CO, TW><<<(npix + 63) / 64, CONV_THREADS, 0, s>>>(a);
+  const int tiles = (npix + 63) / 64;
+  if constexpr (!TW && CI == 16 && CO == 16) {  // the linear path: low halves of input and weights
+    if (a.x2 && a.w2) {
+      if ((long long)tiles * 4 < 152LL * 16)
+        conv_kernel<CI, CO, 16, TW, true, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
+      else
+        conv_kernel<CI, CO, CO, TW, true, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
+      return;
+    }
+  }
+  if constexpr (!TW && CI == 16 && (CO == 32 || CO == 16)) {  // layers reading phi: optional low half
+    if (a.x2) {
+      if ((long long)tiles * 4 < 152LL * 16)
+        conv_kernel<CI, CO, 16, TW, true><<<dim3(tiles, CO / 16), CONV_THREADS, 0, s>>>(a);
+      else
+        conv_kernel<CI, CO, CO, TW, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
+      return;
+    }
+  }
+  if constexpr (!TW && CO > 16) {
+    if ((long long)tiles * 4 < 152LL * 16) {
+      conv_kernel<CI, CO, 16, TW, false><<<dim3(tiles, CO / 16), CONV_THREADS, 0, s>>>(a);
+      return;
+    }
+  }
+  conv_kernel<CI, CO, CO, TW, false><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
 }
 
 template <int CI, int CO>
@@ -565,13 +649,14 @@ struct lbnop_ctx {
   int off_b[NL], off_v;
   int h0, w0;  // level-0 size (H/4, W/4)
   float *theta, *m, *v, *grad;
-  bf16 *wf, *wb;
+  bf16 *wf, *wb, *wlo;
   // activations (BF16), by level; z_* pre-activations, a_* SiLU outputs
-  bf16 *x0, *z[NL], *a[NL], *p1, *p2, *p3, *in_d2a, *in_d1a, *in_d0a;
+  bf16 *x0, *x0l, *z[NL], *a[NL], *p1, *p2, *p3, *in_d2a, *in_d1a, *in_d0a;
   bf16* dz[4];
+  bf16* dz_lina;  // alpha times the output layer's dz (level 0, 16 channels)
   float *g0a, *g0b, *g1a, *g1b, *g2a, *g2b, *g3a;
   float* zout;
-  double *partial, *partial2, *mean, *loss;
+  double *partial, *partial2, *mean, *loss, *sig;
   float *leap0, *leap1;
   float* phi_out;  // [max_batch][H][W], the training forward's output
   int* flags;
@@ -619,7 +704,9 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
   char* grad = take(n_params * 4);
   char* wf = take(n_w * 2);
   char* wb = take(n_w * 2);
+  char* wlo = take(n_w * 2);
   char* x0 = take(P[0] * 16 * 2);
+  char* x0l = take(P[0] * 16 * 2);
   char *zz[NL], *aa[NL];
   for (int l = 0; l < NL; ++l) {
     zz[l] = take(P[kL[l].level] * kL[l].co * 2);
@@ -632,6 +719,7 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
   char* in1 = take(P[1] * 64 * 2);
   char* in0 = take(P[0] * 32 * 2);
   char* dz[4] = {take(P[0] * 32 * 2), take(P[1] * 64 * 2), take(P[2] * 96 * 2), take(P[3] * 96 * 2)};
+  char* dz_lina = take(P[0] * 16 * 2);
   char* g0a = take(P[0] * 32 * 4);
   char* g0b = take(P[0] * 32 * 4);
   char* g1a = take(P[1] * 64 * 4);
@@ -643,6 +731,7 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
   char* partial = take((size_t)LBNOP_MAX_BATCH * HEAD_BLOCKS * 8);
   char* partial2 = take((size_t)LBNOP_MAX_BATCH * HEAD_BLOCKS * 8);
   char* mean = take(LBNOP_MAX_BATCH * 8);
+  char* sig = take(LBNOP_MAX_BATCH * 8);
   char* loss = take(8);
   char* leap0 = take((size_t)p->H * p->W * 4);
   char* leap1 = take((size_t)p->H * p->W * 4);
@@ -657,7 +746,9 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
     c->grad = (float*)grad;
     c->wf = (bf16*)wf;
     c->wb = (bf16*)wb;
+    c->wlo = (bf16*)wlo;
     c->x0 = (bf16*)x0;
+    c->x0l = (bf16*)x0l;
     for (int l = 0; l < NL; ++l) {
       c->z[l] = (bf16*)zz[l];
       c->a[l] = (bf16*)aa[l];
@@ -669,6 +760,7 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
     c->in_d1a = (bf16*)in1;
     c->in_d0a = (bf16*)in0;
     for (int k = 0; k < 4; ++k) c->dz[k] = (bf16*)dz[k];
+    c->dz_lina = (bf16*)dz_lina;
     c->g0a = (float*)g0a;
     c->g0b = (float*)g0b;
     c->g1a = (float*)g1a;
@@ -680,6 +772,7 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
     c->partial = (double*)partial;
     c->partial2 = (double*)partial2;
     c->mean = (double*)mean;
+    c->sig = (double*)sig;
     c->loss = (double*)loss;
     c->leap0 = (float*)leap0;
     c->leap1 = (float*)leap1;
@@ -734,6 +827,8 @@ const float* bias_of(const lbnop_ctx* c, int l) { return c->theta + c->off_b[l];
 void layer_fwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x, bool training, const double* alpha) {
   ConvArgs a{};
   a.x = x;
+  a.x2 = (l == E0A || l == LIN || l == LINA) ? c->x0l : nullptr;
+  a.w2 = (l == LIN || l == LINA) ? c->wlo + c->tab.woff[l] : nullptr;
   a.w = wf_of(c, l);
   a.B = d.B;
   a.H = d.h[kL[l].level];
@@ -741,8 +836,10 @@ void layer_fwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x, bool training,
   a.bias = bias_of(c, l);
   a.film = l == E0A ? c->theta + c->off_v : nullptr;
   for (int b = 0; b < d.B; ++b) a.alpha[b] = (float)alpha[b];
-  if (l == OUT) {
+  if (l == OUT || l == LIN || l == LINA) {  // the three terms of D sum into zout
     a.yf = c->zout;
+    a.accumulate = l != OUT;
+    a.scale_alpha = l == LINA;
   } else {
     a.z = (training || !kL[l].act) ? c->z[l] : nullptr;
     a.a = kL[l].act ? c->a[l] : nullptr;
@@ -754,7 +851,10 @@ void forward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, int bat
   const Dims d = dims(c, batch);
   cudaStream_t s = c->stream;
   const long long P0 = (long long)batch * d.h[0] * d.w[0];
-  s2d_kernel<<<grid_for(P0, 256), 256, 0, s>>>(d_phi, batch, c->p.H, c->p.W, c->x0);
+  const long long hw = (long long)c->p.H * c->p.W;
+  sample_sums_kernel<<<dim3(HEAD_BLOCKS, batch), 256, 0, s>>>(d_phi, nullptr, hw, c->partial, c->partial2);
+  rms_kernel<<<1, 64, 0, s>>>(c->partial2, batch, hw, c->sig);
+  s2d_kernel<<<grid_for(P0, 256), 256, 0, s>>>(d_phi, c->sig, batch, c->p.H, c->p.W, c->x0, c->x0l);
   layer_fwd(c, E0A, d, c->x0, training, alpha);
   layer_fwd(c, E0B, d, c->a[E0A], training, alpha);
   auto pool = [&](const bf16* x, int lvl, int C, bf16* y) {
@@ -783,21 +883,26 @@ void forward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, int bat
   up_add(c->z[D1B], c->a[E0B], 0, 32, c->in_d0a);
   layer_fwd(c, D0A, d, c->in_d0a, training, alpha);
   layer_fwd(c, OUT, d, c->a[D0A], training, alpha);
+  layer_fwd(c, LIN, d, c->x0, training, alpha);
+  layer_fwd(c, LINA, d, c->x0, training, alpha);
   // head: D - mean D per field
   const long long nz = (long long)d.h[0] * d.w[0] * 16;
   sample_sums_kernel<<<dim3(HEAD_BLOCKS, batch), 256, 0, s>>>(c->zout, nullptr, nz, c->partial, nullptr);
-  finish_sums_kernel<<<1, 32, 0, s>>>(c->partial, nullptr, batch, (long long)c->p.H * c->p.W, c->mean, nullptr);
+  finish_sums_kernel<<<1, 32, 0, s>>>(c->partial, nullptr, batch, (long long)c->p.H * c->p.W, SampleWeights{},
+                                      c->mean, nullptr);
   const long long n = (long long)batch * c->p.H * c->p.W;
-  head_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_phi, c->zout, c->mean, batch, c->p.H, c->p.W, (float)c->p.scale,
+  head_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_phi, c->zout, c->mean, c->sig, batch, c->p.H, c->p.W,
+                                               (float)c->p.scale,
                                                d_out);
 }
 
 // Backward of layer l given dz (its pre-activation gradient, BF16, in c->dz[level]):
 // weight and bias gradients, and the input gradient into gin (FP32) unless gin is null.
-void layer_bwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x_in, float* gin, const double* alpha) {
+void layer_bwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x_in, float* gin, const double* alpha,
+               const bf16* dz_in = nullptr) {
   cudaStream_t s = c->stream;
   const int lvl = kL[l].level, ci = kL[l].ci, co = kL[l].co;
-  const bf16* dz = c->dz[lvl];
+  const bf16* dz = dz_in ? dz_in : c->dz[lvl];
   ColsumArgs cs{};
   cs.dz = dz;
   cs.P = d.h[lvl] * d.w[lvl];
@@ -820,6 +925,10 @@ void layer_bwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x_in, float* gin,
   wg.chunk = wgrad_chunk((int)npix);
   wg.dw = c->grad + c->tab.off_w[l];
   wgrad_launch(ci, co, wg, s);
+  if (x_in == c->x0) {  // the low half of the input shares the weights
+    wg.x = c->x0l;
+    wgrad_launch(ci, co, wg, s);
+  }
   if (gin) {
     ConvArgs a{};
     a.x = dz;
@@ -843,17 +952,33 @@ void pool_bwd(lbnop_ctx* c, const Dims& d, int lvl_coarse, int C, const float* g
   pool_bwd_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(gc, d.B, d.h[lvl_coarse], d.w[lvl_coarse], C, gf);
 }
 
-void backward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, const float* d_target, int batch) {
+void backward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, const float* d_target,
+                   const double* weight, int batch) {
   cudaStream_t s = c->stream;
   const Dims d = dims(c, batch);
   float* phi_out = c->phi_out;
   forward_impl(c, d_phi, alpha, batch, phi_out, true);
   const long long hw = (long long)c->p.H * c->p.W, n = batch * hw;
   sample_sums_kernel<<<dim3(HEAD_BLOCKS, batch), 256, 0, s>>>(phi_out, d_target, hw, c->partial, c->partial2);
-  finish_sums_kernel<<<1, 32, 0, s>>>(c->partial, c->partial2, batch, hw, c->mean, c->loss);
+  SampleWeights w{}, coef{};
+  for (int b = 0; b < batch; ++b) {
+    w.v[b] = weight ? (float)weight[b] : 1.0f;
+    coef.v[b] = (float)(c->p.scale * 2.0 * (weight ? weight[b] : 1.0) / (double)n);
+  }
+  finish_sums_kernel<<<1, 32, 0, s>>>(c->partial, c->partial2, batch, hw, w, c->mean, c->loss);
   cudaMemsetAsync(c->grad, 0, c->n_params * sizeof(float), s);
-  head_bwd_kernel<<<grid_for(n, 256), 256, 0, s>>>(phi_out, d_target, c->mean, batch, c->p.H, c->p.W,
-                                                   (float)(c->p.scale * 2.0 / (double)n), c->dz[0]);
+  head_bwd_kernel<<<grid_for(n, 256), 256, 0, s>>>(phi_out, d_target, c->mean, c->sig, batch, c->p.H, c->p.W, coef,
+                                                   c->dz[0]);
+  // the linear path: D gets lin(x) + alpha lina(x), so lin's dz is dz_out and lina's is alpha dz_out
+  layer_bwd(c, LIN, d, c->x0, nullptr, alpha);
+  {
+    const long long nz = (long long)batch * d.h[0] * d.w[0] * 16;
+    SampleWeights al{};
+    for (int b = 0; b < batch; ++b) al.v[b] = (float)alpha[b];
+    scale_rows_kernel<<<grid_for(nz, 256), 256, 0, s>>>(c->dz[0], (long long)d.h[0] * d.w[0] * 16, batch, al,
+                                                        c->dz_lina);
+  }
+  layer_bwd(c, LINA, d, c->x0, nullptr, alpha, c->dz_lina);
   layer_bwd(c, OUT, d, c->a[D0A], c->g0a, alpha);
   make_dz(c, d, 0, 32, c->g0a, nullptr, c->z[D0A]);
   layer_bwd(c, D0A, d, c->in_d0a, c->g0b, alpha);  // g0b: gradient in h0 from here on
@@ -896,7 +1021,7 @@ void refresh_or_update(lbnop_ctx* c, bool update, double lr) {
   }
   adam_kernel<<<grid_for(c->n_params, 256), 256, 0, c->stream>>>(c->theta, c->m, c->v, c->grad, c->n_params,
                                                                  (float)lr, c1, c2, update ? 1 : 0, c->tab, c->wf,
-                                                                 c->wb);
+                                                                 c->wb, c->wlo);
 }
 
 lbch_status check_batch(lbnop_ctx* c, int batch, const double* h_alpha) {
@@ -1004,12 +1129,18 @@ lbch_status lbnop_forward(lbnop_ctx* c, const float* d_phi, const double* h_alph
 }
 
 lbch_status lbnop_backward(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,
-                           int32_t batch, double* h_loss) {
+                           const double* h_weight, int32_t batch, double* h_loss) {
   lbch_status st = pre(c);
   if (st != LBCH_OK) return st;
   if (!d_phi || !d_target) return LBCH_EINVAL;
   if ((st = check_batch(c, batch, h_alpha)) != LBCH_OK) return st;
-  backward_impl(c, d_phi, h_alpha, d_target, batch);
+  if (h_weight)
+    for (int b = 0; b < batch; ++b)
+      if (!(h_weight[b] >= 0.0) || !std::isfinite(h_weight[b])) {
+        set_err(c, "backward: weights must be finite and >= 0");
+        return LBCH_EINVAL;
+      }
+  backward_impl(c, d_phi, h_alpha, d_target, h_weight, batch);
   if ((st = done(c, "backward: launch")) != LBCH_OK) return st;
   if (h_loss) {
     if (cuda_bad(c, cudaMemcpyAsync(h_loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss") ||
@@ -1042,8 +1173,8 @@ lbch_status lbnop_adam(lbnop_ctx* c, double lr) {
 }
 
 lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,
-                             int32_t batch, double lr, double* h_loss) {
-  lbch_status st = lbnop_backward(c, d_phi, h_alpha, d_target, batch, nullptr);
+                             const double* h_weight, int32_t batch, double lr, double* h_loss) {
+  lbch_status st = lbnop_backward(c, d_phi, h_alpha, d_target, h_weight, batch, nullptr);
   if (st != LBCH_OK) return st;
   if ((st = lbnop_adam(c, lr)) != LBCH_OK) return st;
   if (h_loss) {

@@ -49,11 +49,11 @@ def load():
             getattr(lib, name).restype = ctypes.c_int
         lib.lbnop_forward.argtypes = [vp, vp, dp, i32, vp]
         lib.lbnop_forward.restype = ctypes.c_int
-        lib.lbnop_backward.argtypes = [vp, vp, dp, vp, i32, dp]
+        lib.lbnop_backward.argtypes = [vp, vp, dp, vp, dp, i32, dp]
         lib.lbnop_backward.restype = ctypes.c_int
         lib.lbnop_adam.argtypes = [vp, ctypes.c_double]
         lib.lbnop_adam.restype = ctypes.c_int
-        lib.lbnop_train_step.argtypes = [vp, vp, dp, vp, i32, ctypes.c_double, dp]
+        lib.lbnop_train_step.argtypes = [vp, vp, dp, vp, dp, i32, ctypes.c_double, dp]
         lib.lbnop_train_step.restype = ctypes.c_int
         lib.lbnop_leap_run.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64]
         lib.lbnop_leap_run.restype = ctypes.c_int
@@ -128,10 +128,11 @@ def lbnop_forward(ctx, d_phi: int, alpha, batch: int, d_phi_out: int) -> None:
                                      ctypes.c_void_p(int(d_phi_out))), "lbnop_forward")
 
 
-def lbnop_backward(ctx, d_phi: int, alpha, d_target: int, batch: int, want_loss: bool = True):
+def lbnop_backward(ctx, d_phi: int, alpha, d_target: int, batch: int, want_loss: bool = True, weight=None):
     loss = ctypes.c_double(float("nan"))
     _check(ctx, load().lbnop_backward(ctx, ctypes.c_void_p(int(d_phi)), _alpha(alpha), ctypes.c_void_p(int(d_target)),
-                                      int(batch), ctypes.byref(loss) if want_loss else None), "lbnop_backward")
+                                      None if weight is None else _alpha(weight), int(batch),
+                                      ctypes.byref(loss) if want_loss else None), "lbnop_backward")
     return loss.value if want_loss else None
 
 
@@ -139,11 +140,13 @@ def lbnop_adam(ctx, lr: float) -> None:
     _check(ctx, load().lbnop_adam(ctx, float(lr)), "lbnop_adam")
 
 
-def lbnop_train_step(ctx, d_phi: int, alpha, d_target: int, batch: int, lr: float, want_loss: bool = False):
+def lbnop_train_step(ctx, d_phi: int, alpha, d_target: int, batch: int, lr: float, want_loss: bool = False,
+                     weight=None):
     loss = ctypes.c_double(float("nan"))
     _check(ctx, load().lbnop_train_step(ctx, ctypes.c_void_p(int(d_phi)), _alpha(alpha),
-                                        ctypes.c_void_p(int(d_target)), int(batch), float(lr),
-                                        ctypes.byref(loss) if want_loss else None), "lbnop_train_step")
+                                        ctypes.c_void_p(int(d_target)), None if weight is None else _alpha(weight),
+                                        int(batch), float(lr), ctypes.byref(loss) if want_loss else None),
+           "lbnop_train_step")
     return loss.value if want_loss else None
 
 
@@ -234,19 +237,19 @@ class Surrogate:
             lbnop_forward(self.ctx, phi.data_ptr(), alpha, b, out.data_ptr())
         return out
 
-    def backward(self, phi, alpha, target) -> float:
+    def backward(self, phi, alpha, target, weight=None) -> float:
         b = self._fields(phi, "phi")
         with self._on():
-            return lbnop_backward(self.ctx, phi.data_ptr(), alpha, target.data_ptr(), b)
+            return lbnop_backward(self.ctx, phi.data_ptr(), alpha, target.data_ptr(), b, weight=weight)
 
     def adam(self, lr: float) -> None:
         with self._on():
             lbnop_adam(self.ctx, lr)
 
-    def train_step(self, phi, alpha, target, lr: float, want_loss: bool = False):
+    def train_step(self, phi, alpha, target, lr: float, want_loss: bool = False, weight=None):
         b = self._fields(phi, "phi")
         with self._on():
-            return lbnop_train_step(self.ctx, phi.data_ptr(), alpha, target.data_ptr(), b, lr, want_loss)
+            return lbnop_train_step(self.ctx, phi.data_ptr(), alpha, target.data_ptr(), b, lr, want_loss, weight)
 
     def leap_run(self, solver, alpha: float, cycles: int, lbm_steps: int) -> None:
         """Alternates leaps with lbm_steps steps of an lbch Solver (same stream, nx = W, ny = H)."""

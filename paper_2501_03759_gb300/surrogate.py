@@ -1,0 +1,219 @@
+"""The learned leap's workflow: generate LBM trajectories, train the network, and run
+and judge the leap/LBM alternation against the plain LBM.
+
+  python -m paper_2501_03759_gb300.surrogate train --out DIR   # data + training, writes DIR/leap_theta.npy
+  python -m paper_2501_03759_gb300.surrogate eval --theta FILE  # gates against a held-out plain run
+
+Data: periodic n x n spinodal runs of the scheme (phi0 = U[-0.05, 0.05], seeded; alpha of
+Eq. 6 spread over [0, 0.5]; the other parameters of Eq. 39), stepped together by the
+batched lbch path; phi is copied on the device every `every` steps. A training pair is
+(phi(t), phi(t + leap)) for any stored t.
+
+Judge: from a held-out initial field, the plain LBM runs T = warmup + cycles (leap + corr)
+steps; the surrogate run takes the same warmup LBM steps (the white noise of phi0 decays),
+then alternates one leap (K = leap steps) with corr LBM steps, cycles times.
+Reported: relative L2 error of phi at T, relative free-energy difference, mass drift, and
+the time-to-T of both runs (CUDA events on the shared stream).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+from . import lbch, lbnop
+
+LEAP = 500        # steps per leap (K)
+EVERY = 50        # snapshot spacing
+CORR = 50         # LBM correction steps after each leap
+SCALE = 0.01      # phi_out = phi + SCALE sig (D - mean D), sig the field's rms
+T_END = 50000
+WARMUP = 500      # plain LBM steps before the first leap (the noise of phi0 decays first)
+# (c_in, c_out) of the network's layers, in the order of include/lbnop.h
+LAYERS = [(16, 32), (32, 32), (32, 64), (64, 64), (64, 96), (96, 96), (96, 96), (96, 96),
+          (96, 96), (96, 64), (64, 64), (64, 32), (32, 32), (32, 16), (16, 16), (16, 16)]
+OUT = 13  # the output layer; the two after it are the linear path
+
+
+def make_runs(count: int, seed: int = 1000):
+    """(alpha, seed) of each training run: alphas evenly over [0, 0.5], shuffled."""
+    r = np.random.default_rng(seed)
+    alphas = r.permutation(np.linspace(0.0, 0.5, count))
+    return [(float(a), seed + 1 + k) for k, a in enumerate(alphas)]
+
+
+def init_theta(seed: int, out_scale: float = 0.1) -> np.ndarray:
+    """Initial parameters (flat layout of include/lbnop.h): He-normal 3 x 3 weights
+    (std sqrt(2 / (9 c_in))), the output layer's scaled by out_scale so that training
+    starts near the identity leap, a zero linear path, zero biases and conditioning vector."""
+    r = np.random.default_rng(seed)
+    parts = []
+    for k, (ci, co) in enumerate(LAYERS):
+        w = r.normal(0.0, (2.0 / (9 * ci)) ** 0.5, 9 * co * ci) * (out_scale if k == OUT else 1.0)
+        if k > OUT:
+            w[:] = 0.0
+        parts += [w, np.zeros(co)]
+        if k == 0:
+            parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def spinodal(n: int, seed: int) -> np.ndarray:
+    return np.random.default_rng(seed).uniform(-0.05, 0.05, (n, n))
+
+
+def generate(runs, n: int = 512, t_end: int = T_END, every: int = EVERY):
+    """Device tensor [len(runs), t_end / every + 1, n, n] (FP32) of phi snapshots."""
+    import torch
+
+    count = len(runs)
+    snaps = t_end // every + 1
+    data = torch.empty((count, snaps, n, n), dtype=torch.float32, device="cuda")
+    b = lbch.Batch(lbch.make_params(8, 8), [n] * count, [n] * count, [a for a, _ in runs])
+    for i, (_, seed) in enumerate(runs):
+        b.init_field(i, spinodal(n, seed))
+    for k in range(snaps):
+        if k:
+            b.step(every)
+        for i in range(count):
+            b.phi_device(i, data[i, k])
+    torch.cuda.synchronize()
+    b.close()
+    return data
+
+
+def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: float = 1e-5, seed: int = 0,
+          theta0=None, log_every: int = 200):
+    """Adam on the leap error over random (run, t) pairs, each pair weighted by the inverse of
+    its own mean squared change (so that the identity map scores 1 on every pair and small
+    late-time changes count as much as the early decay of the noise); cosine learning rate."""
+    import torch
+
+    count, snaps, n, _ = data.shape
+    gap = LEAP // EVERY
+    s = lbnop.Surrogate(n, n, max_batch=batch, scale=SCALE)
+    s.set_params(init_theta(seed) if theta0 is None else theta0)
+    r = np.random.default_rng(seed + 17)
+    x = torch.empty((batch, n, n), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    alphas = np.asarray(alphas, dtype=np.float64)
+    log = []
+    t0 = time.perf_counter()
+    for it in range(iters):
+        ri = r.integers(0, count, batch)
+        ki = r.integers(WARMUP // EVERY, snaps - gap, batch)
+        ri_t, ki_t = torch.from_numpy(ri).cuda(), torch.from_numpy(ki).cuda()
+        torch.index_select(data.view(count * snaps, n, n), 0, ri_t * snaps + ki_t, out=x)
+        torch.index_select(data.view(count * snaps, n, n), 0, ri_t * snaps + ki_t + gap, out=y)
+        rate = lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * it / max(1, iters - 1)))
+        want = (it % log_every == 0) or it == iters - 1
+        change = ((y - x) ** 2).mean(dim=(1, 2)).double().cpu().numpy()
+        weight = 1.0 / np.maximum(change, 1e-30)
+        loss = s.train_step(x, alphas[ri], y, rate, want_loss=want, weight=weight)
+        if want:
+            log.append({"iter": it, "relative_loss": loss, "lr": rate, "seconds": time.perf_counter() - t0})
+    torch.cuda.synchronize()
+    theta = s.params_host()
+    s.close()
+    return theta, log
+
+
+def evaluate(theta, alpha: float, seed: int, n: int = 512, cycles: int = 90, leap: int = LEAP, corr: int = CORR,
+             warmup: int = WARMUP):
+    """Plain LBM versus (warmup LBM steps, then cycles of one leap and corr LBM steps) from
+    the same held-out field, to T = warmup + cycles (leap + corr) steps (50000 by default).
+    Returns the gates and timings."""
+    import torch
+
+    steps = warmup + cycles * (leap + corr)
+    phi0 = spinodal(n, seed)
+    s = lbnop.Surrogate(n, n, max_batch=1, scale=SCALE)
+    s.set_params(theta)
+    plain = lbch.Solver(lbch.make_params(n, n, alpha=alpha), stream=s.stream)
+    lept = lbch.Solver(lbch.make_params(n, n, alpha=alpha), stream=s.stream)
+    # warm-up (kernels loaded, clocks up), then timed runs from fresh initial states
+    plain.init_field(phi0)
+    plain.step(200)
+    lept.init_field(phi0)
+    s.leap_run(lept, alpha, 2, corr)
+    plain.init_field(phi0)
+    lept.init_field(phi0)
+    m0 = plain.mass()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(s.stream)
+    plain.step(steps)
+    ev[1].record(s.stream)
+    lept.step(warmup)
+    s.leap_run(lept, alpha, cycles, corr)
+    ev[2].record(s.stream)
+    torch.cuda.synchronize()
+    t_plain = ev[0].elapsed_time(ev[1]) / 1e3
+    t_leap = ev[1].elapsed_time(ev[2]) / 1e3
+    a, b = plain.field(), lept.field()
+    e_plain, e_leap = plain.free_energy(), lept.free_energy()
+    m_leap = lept.mass()
+    out = {
+        "alpha": alpha, "seed": seed, "n": n, "steps": steps, "warmup": warmup, "cycles": cycles, "leap": leap,
+        "corr": corr,
+        "phi_rel_l2": float(np.linalg.norm(b - a) / np.linalg.norm(a)),
+        "energy_rel_diff": float(abs(e_leap - e_plain) / abs(e_plain)),
+        "energy_plain": e_plain, "energy_leap": e_leap,
+        "mass_drift_rel": float(abs(m_leap - m0) / max(abs(m0), 1e-300)),
+        "mass_drift_abs": float(abs(m_leap - m0)),
+        "seconds_plain": t_plain, "seconds_leap": t_leap, "speedup": t_plain / t_leap,
+        "phi_rms_plain": float(np.sqrt(np.mean(a * a))),
+    }
+    plain.close()
+    lept.close()
+    s.close()
+    return out
+
+
+def main(argv=None):
+    import torch
+
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    t = sub.add_parser("train")
+    t.add_argument("--out", required=True)
+    t.add_argument("--runs", type=int, default=16)
+    t.add_argument("--n", type=int, default=512)
+    t.add_argument("--iters", type=int, default=3000)
+    t.add_argument("--batch", type=int, default=16)
+    t.add_argument("--lr", type=float, default=1e-3)
+    e = sub.add_parser("eval")
+    e.add_argument("--theta", required=True)
+    e.add_argument("--alpha", type=float, nargs="+", default=[0.3])
+    e.add_argument("--seed", type=int, default=777)
+    args = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    if args.cmd == "train":
+        os.makedirs(args.out, exist_ok=True)
+        runs = make_runs(args.runs)
+        t0 = time.perf_counter()
+        data = generate(runs, args.n)
+        t_gen = time.perf_counter() - t0
+        theta, log = train(data, [a for a, _ in runs], args.iters, args.batch, args.lr)
+        t_train = time.perf_counter() - t0 - t_gen
+        np.save(os.path.join(args.out, "leap_theta.npy"), theta.astype(np.float32))
+        report = {"runs": runs, "n": args.n, "iters": args.iters, "batch": args.batch, "lr": args.lr,
+                  "leap": LEAP, "every": EVERY, "scale": SCALE, "t_end": T_END,
+                  "seconds_generate": t_gen, "seconds_train": t_train, "log": log}
+        with open(os.path.join(args.out, "train_report.json"), "w") as fh:
+            json.dump(report, fh, indent=1)
+        for row in log:
+            print(json.dumps(row))
+        del data
+    else:
+        theta = np.load(args.theta)
+        for a in args.alpha:
+            print(json.dumps(evaluate(theta, a, args.seed)))
+
+
+if __name__ == "__main__":
+    main()

@@ -83,7 +83,9 @@ def test_silu_values_and_derivative():
 def test_zero_output_layer_is_identity_and_head_conserves_mass():
     theta = rand_theta(1, out_scale=0.0)
     P = N.unpack(theta)
-    P["out"][1][:] = 0.0
+    for name in ("out", "lin", "lina"):  # every term of D
+        P[name][0][:] = 0.0
+        P[name][1][:] = 0.0
     phi = rng.uniform(-1, 1, size=(2, 64, 64))
     out, _ = N.forward(theta, phi, [0.1, 0.4], 0.1)
     assert np.array_equal(out, phi)
@@ -155,3 +157,17 @@ def test_bf16_rounding_is_round_to_nearest_even():
     x = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -9, 1 + 3 * 2 ** -8, -(1 + 2 ** -7 + 2 ** -9), 2.0 ** -130])
     want = np.array([1.0, 1.0, 1 + 2 ** -7, 1 + 2 ** -6, -(1 + 2 ** -7), 2.0 ** -130])
     assert np.array_equal(N.bf16(x), want)
+
+
+def test_weighted_loss_and_gradient():
+    r = np.random.default_rng(21)
+    out, tgt = r.normal(size=(2, 4, 8)), r.normal(size=(2, 4, 8))
+    w = np.array([0.5, 3.0])
+    L, g = N.loss(out, tgt, w)
+    sse = ((out - tgt) ** 2).sum(axis=(1, 2))
+    assert abs(L - (w[0] * sse[0] + w[1] * sse[1]) / out.size) < 1e-14
+    assert N.loss(out, tgt)[0] == N.loss(out, tgt, [1.0, 1.0])[0]
+    e = np.zeros_like(out)
+    e[1, 2, 3] = 1e-6
+    fd = (N.loss(out + e, tgt, w)[0] - N.loss(out - e, tgt, w)[0]) / 2e-6
+    assert abs(fd - g[1, 2, 3]) < 1e-8
