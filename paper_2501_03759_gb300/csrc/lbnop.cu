@@ -30,11 +30,15 @@ struct LayerSpec {
   bool act;
 };
 // The table of include/lbnop.h.
-constexpr LayerSpec kL[NL] = {{16, 32, 0, true},  {32, 32, 0, true},  {32, 64, 1, true},  {64, 64, 1, true},
+constexpr LayerSpec kL[NL] = {{16, 64, 0, true},  {64, 64, 0, true},  {64, 64, 1, true},  {64, 64, 1, true},
                               {64, 96, 2, true},  {96, 96, 2, true},  {96, 96, 3, true},  {96, 96, 3, true},
-                              {96, 96, 2, true},  {96, 64, 2, false}, {64, 64, 1, true},  {64, 32, 1, false},
-                              {32, 32, 0, true},  {32, 16, 0, false}, {16, 16, 0, false}, {16, 16, 0, false}};
+                              {96, 96, 2, true},  {96, 64, 2, false}, {64, 64, 1, true},  {64, 64, 1, false},
+                              {64, 64, 0, true},  {64, 16, 0, false}, {16, 16, 0, false}, {16, 16, 0, false}};
 enum { E0A, E0B, E1A, E1B, E2A, E2B, M3A, M3B, D2A, D2B, D1A, D1B, D0A, OUT, LIN, LINA };
+// Channels of the skip tensors h0..h3 at levels 0..3 (and of every tensor summed with them).
+constexpr int CH[4] = {kL[E0B].co, kL[E1B].co, kL[E2B].co, kL[M3B].co};
+static_assert(kL[D1B].co == CH[0] && kL[D2B].co == CH[1] && kL[D2A].ci == CH[3] && kL[D2A].ci == CH[2],
+              "skip additions need equal channel counts");
 
 struct LayerTab {
   int off_w[NL], ci[NL], co[NL], woff[NL];
@@ -559,7 +563,7 @@ void conv_t(const ConvArgs& a, cudaStream_t s) {
       return;
     }
   }
-  if constexpr (!TW && CI == 16 && (CO == 32 || CO == 16)) {  // layers reading phi: optional low half
+  if constexpr (!TW && CI == 16) {  // layers reading phi: optional low half of the input
     if (a.x2) {
       if ((long long)tiles * 4 < 152LL * 16)
         conv_kernel<CI, CO, 16, TW, true><<<dim3(tiles, CO / 16), CONV_THREADS, 0, s>>>(a);
@@ -712,21 +716,28 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
     zz[l] = take(P[kL[l].level] * kL[l].co * 2);
     aa[l] = kL[l].act ? take(P[kL[l].level] * kL[l].co * 2) : nullptr;
   }
-  char* p1 = take(P[1] * 32 * 2);
-  char* p2 = take(P[2] * 64 * 2);
-  char* p3 = take(P[3] * 96 * 2);
-  char* in2 = take(P[2] * 96 * 2);
-  char* in1 = take(P[1] * 64 * 2);
-  char* in0 = take(P[0] * 32 * 2);
-  char* dz[4] = {take(P[0] * 32 * 2), take(P[1] * 64 * 2), take(P[2] * 96 * 2), take(P[3] * 96 * 2)};
+  // widest tensor per level (the dz and gradient buffers serve every layer of their level)
+  int wide[4] = {16, 0, 0, 0};
+  for (int l = 0; l < NL; ++l) {
+    wide[kL[l].level] = wide[kL[l].level] > kL[l].co ? wide[kL[l].level] : kL[l].co;
+    wide[kL[l].level] = wide[kL[l].level] > kL[l].ci ? wide[kL[l].level] : kL[l].ci;
+  }
+  char* p1 = take(P[1] * CH[0] * 2);
+  char* p2 = take(P[2] * CH[1] * 2);
+  char* p3 = take(P[3] * CH[2] * 2);
+  char* in2 = take(P[2] * CH[2] * 2);
+  char* in1 = take(P[1] * CH[1] * 2);
+  char* in0 = take(P[0] * CH[0] * 2);
+  char* dz[4] = {take(P[0] * wide[0] * 2), take(P[1] * wide[1] * 2), take(P[2] * wide[2] * 2),
+                 take(P[3] * wide[3] * 2)};
   char* dz_lina = take(P[0] * 16 * 2);
-  char* g0a = take(P[0] * 32 * 4);
-  char* g0b = take(P[0] * 32 * 4);
-  char* g1a = take(P[1] * 64 * 4);
-  char* g1b = take(P[1] * 64 * 4);
-  char* g2a = take(P[2] * 96 * 4);
-  char* g2b = take(P[2] * 96 * 4);
-  char* g3a = take(P[3] * 96 * 4);
+  char* g0a = take(P[0] * wide[0] * 4);
+  char* g0b = take(P[0] * wide[0] * 4);
+  char* g1a = take(P[1] * wide[1] * 4);
+  char* g1b = take(P[1] * wide[1] * 4);
+  char* g2a = take(P[2] * wide[2] * 4);
+  char* g2b = take(P[2] * wide[2] * 4);
+  char* g3a = take(P[3] * wide[3] * 4);
   char* zout = take(P[0] * 16 * 4);
   char* partial = take((size_t)LBNOP_MAX_BATCH * HEAD_BLOCKS * 8);
   char* partial2 = take((size_t)LBNOP_MAX_BATCH * HEAD_BLOCKS * 8);
@@ -865,22 +876,22 @@ void forward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, int bat
     const long long n = (long long)batch * d.h[lvl] * d.w[lvl] * C;
     up_add_kernel<<<grid_for(n, 256), 256, 0, s>>>(xc, skip, batch, d.h[lvl], d.w[lvl], C, y);
   };
-  pool(c->a[E0B], 1, 32, c->p1);
+  pool(c->a[E0B], 1, CH[0], c->p1);
   layer_fwd(c, E1A, d, c->p1, training, alpha);
   layer_fwd(c, E1B, d, c->a[E1A], training, alpha);
-  pool(c->a[E1B], 2, 64, c->p2);
+  pool(c->a[E1B], 2, CH[1], c->p2);
   layer_fwd(c, E2A, d, c->p2, training, alpha);
   layer_fwd(c, E2B, d, c->a[E2A], training, alpha);
-  pool(c->a[E2B], 3, 96, c->p3);
+  pool(c->a[E2B], 3, CH[2], c->p3);
   layer_fwd(c, M3A, d, c->p3, training, alpha);
   layer_fwd(c, M3B, d, c->a[M3A], training, alpha);
-  up_add(c->a[M3B], c->a[E2B], 2, 96, c->in_d2a);
+  up_add(c->a[M3B], c->a[E2B], 2, CH[2], c->in_d2a);
   layer_fwd(c, D2A, d, c->in_d2a, training, alpha);
   layer_fwd(c, D2B, d, c->a[D2A], training, alpha);
-  up_add(c->z[D2B], c->a[E1B], 1, 64, c->in_d1a);
+  up_add(c->z[D2B], c->a[E1B], 1, CH[1], c->in_d1a);
   layer_fwd(c, D1A, d, c->in_d1a, training, alpha);
   layer_fwd(c, D1B, d, c->a[D1A], training, alpha);
-  up_add(c->z[D1B], c->a[E0B], 0, 32, c->in_d0a);
+  up_add(c->z[D1B], c->a[E0B], 0, CH[0], c->in_d0a);
   layer_fwd(c, D0A, d, c->in_d0a, training, alpha);
   layer_fwd(c, OUT, d, c->a[D0A], training, alpha);
   layer_fwd(c, LIN, d, c->x0, training, alpha);
@@ -980,34 +991,34 @@ void backward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, const 
   }
   layer_bwd(c, LINA, d, c->x0, nullptr, alpha, c->dz_lina);
   layer_bwd(c, OUT, d, c->a[D0A], c->g0a, alpha);
-  make_dz(c, d, 0, 32, c->g0a, nullptr, c->z[D0A]);
+  make_dz(c, d, 0, kL[D0A].co, c->g0a, nullptr, c->z[D0A]);
   layer_bwd(c, D0A, d, c->in_d0a, c->g0b, alpha);  // g0b: gradient in h0 from here on
-  make_dz(c, d, 1, 32, nullptr, c->g0b, nullptr);
+  make_dz(c, d, 1, kL[D1B].co, nullptr, c->g0b, nullptr);
   layer_bwd(c, D1B, d, c->a[D1A], c->g1a, alpha);
-  make_dz(c, d, 1, 64, c->g1a, nullptr, c->z[D1A]);
+  make_dz(c, d, 1, kL[D1A].co, c->g1a, nullptr, c->z[D1A]);
   layer_bwd(c, D1A, d, c->in_d1a, c->g1b, alpha);  // g1b: gradient in h1
-  make_dz(c, d, 2, 64, nullptr, c->g1b, nullptr);
+  make_dz(c, d, 2, kL[D2B].co, nullptr, c->g1b, nullptr);
   layer_bwd(c, D2B, d, c->a[D2A], c->g2a, alpha);
-  make_dz(c, d, 2, 96, c->g2a, nullptr, c->z[D2A]);
+  make_dz(c, d, 2, kL[D2A].co, c->g2a, nullptr, c->z[D2A]);
   layer_bwd(c, D2A, d, c->in_d2a, c->g2b, alpha);  // g2b: gradient in h2
-  make_dz(c, d, 3, 96, nullptr, c->g2b, c->z[M3B]);
+  make_dz(c, d, 3, kL[M3B].co, nullptr, c->g2b, c->z[M3B]);
   layer_bwd(c, M3B, d, c->a[M3A], c->g3a, alpha);
-  make_dz(c, d, 3, 96, c->g3a, nullptr, c->z[M3A]);
+  make_dz(c, d, 3, kL[M3A].co, c->g3a, nullptr, c->z[M3A]);
   layer_bwd(c, M3A, d, c->p3, c->g3a, alpha);
-  pool_bwd(c, d, 3, 96, c->g3a, c->g2b);
-  make_dz(c, d, 2, 96, c->g2b, nullptr, c->z[E2B]);
+  pool_bwd(c, d, 3, kL[M3A].ci, c->g3a, c->g2b);
+  make_dz(c, d, 2, kL[E2B].co, c->g2b, nullptr, c->z[E2B]);
   layer_bwd(c, E2B, d, c->a[E2A], c->g2a, alpha);
-  make_dz(c, d, 2, 96, c->g2a, nullptr, c->z[E2A]);
+  make_dz(c, d, 2, kL[E2A].co, c->g2a, nullptr, c->z[E2A]);
   layer_bwd(c, E2A, d, c->p2, c->g2a, alpha);
-  pool_bwd(c, d, 2, 64, c->g2a, c->g1b);
-  make_dz(c, d, 1, 64, c->g1b, nullptr, c->z[E1B]);
+  pool_bwd(c, d, 2, kL[E2A].ci, c->g2a, c->g1b);
+  make_dz(c, d, 1, kL[E1B].co, c->g1b, nullptr, c->z[E1B]);
   layer_bwd(c, E1B, d, c->a[E1A], c->g1a, alpha);
-  make_dz(c, d, 1, 64, c->g1a, nullptr, c->z[E1A]);
+  make_dz(c, d, 1, kL[E1A].co, c->g1a, nullptr, c->z[E1A]);
   layer_bwd(c, E1A, d, c->p1, c->g1a, alpha);
-  pool_bwd(c, d, 1, 32, c->g1a, c->g0b);
-  make_dz(c, d, 0, 32, c->g0b, nullptr, c->z[E0B]);
+  pool_bwd(c, d, 1, kL[E1A].ci, c->g1a, c->g0b);
+  make_dz(c, d, 0, kL[E0B].co, c->g0b, nullptr, c->z[E0B]);
   layer_bwd(c, E0B, d, c->a[E0A], c->g0a, alpha);
-  make_dz(c, d, 0, 32, c->g0a, nullptr, c->z[E0A]);
+  make_dz(c, d, 0, kL[E0A].co, c->g0a, nullptr, c->z[E0A]);
   layer_bwd(c, E0A, d, c->x0, nullptr, alpha);
   c->last_batch = batch;
 }
