@@ -3,6 +3,7 @@ and judge the leap/LBM alternation against the plain LBM.
 
   python -m paper_2501_03759_gb300.surrogate train --out DIR   # data + training, writes DIR/leap_theta.npy
   python -m paper_2501_03759_gb300.surrogate eval --theta FILE  # gates against a held-out plain run
+  python -m paper_2501_03759_gb300.surrogate time --theta FILE  # device time of a forward and a step
 
 Data: periodic n x n spinodal runs of the scheme (phi0 = U[-0.05, 0.05], seeded; alpha of
 Eq. 6 spread over [0, 0.5]; the other parameters of Eq. 39), stepped together by the
@@ -174,6 +175,35 @@ def evaluate(theta, alpha: float, seed: int, n: int = 512, cycles: int = 90, lea
     return out
 
 
+def time_kernels(theta, n: int = 512, batch: int = 16, reps: int = 20):
+    """Mean device time (CUDA events) of one leap forward of a single field and of one
+    training step on `batch` fields, both n x n."""
+    import torch
+
+    s = lbnop.Surrogate(n, n, max_batch=batch, scale=SCALE)
+    s.set_params(theta)
+    r = np.random.default_rng(0)
+    x1 = torch.from_numpy(r.uniform(-0.05, 0.05, (1, n, n)).astype(np.float32)).cuda()
+    xb = torch.from_numpy(r.uniform(-0.05, 0.05, (batch, n, n)).astype(np.float32)).cuda()
+    out1 = torch.empty_like(x1)
+
+    def clock(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        for _ in range(k):
+            fn()
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k * 1e3
+
+    fwd = clock(lambda: s.forward(x1, [0.3], out1), reps)
+    step = clock(lambda: s.train_step(xb, [0.3] * batch, xb, 0.0), max(1, reps // 4))
+    s.close()
+    return {"n": n, "forward_batch1_us": fwd, "train_step_us": step, "train_batch": batch}
+
+
 def main(argv=None):
     import torch
 
@@ -190,6 +220,9 @@ def main(argv=None):
     e.add_argument("--theta", required=True)
     e.add_argument("--alpha", type=float, nargs="+", default=[0.3])
     e.add_argument("--seed", type=int, default=777)
+    k = sub.add_parser("time")
+    k.add_argument("--theta", required=True)
+    k.add_argument("--reps", type=int, default=20)
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
     if args.cmd == "train":
@@ -209,6 +242,8 @@ def main(argv=None):
         for row in log:
             print(json.dumps(row))
         del data
+    elif args.cmd == "time":
+        print(json.dumps(time_kernels(np.load(args.theta), reps=args.reps)))
     else:
         theta = np.load(args.theta)
         for a in args.alpha:
