@@ -287,20 +287,25 @@ def run_3d(lbch, torch, n: int, steps: int):
 SURROGATE_THETA = os.path.join(ROOT, "paper_2501_03759_gb300", "weights", "leap512_k500.npy")
 
 
-def run_surrogate(alpha: float = 0.3, seed: int = 777):
+def run_surrogate(alphas=(0.1, 0.3, 0.45), seed: int = 777):
     """Time-to-t of the learned leap against the plain LBM on a held-out 512^2 spinodal field
     to t = 50000 (500 LBM steps, then 90 x (one 500-step leap + 50 LBM steps)), with the
-    committed trained parameters; None if they are absent."""
+    committed trained parameters, for each anisotropy strength; None if they are absent."""
     if not os.path.exists(SURROGATE_THETA):
         return None
     from paper_2501_03759_gb300 import surrogate
 
-    r = surrogate.evaluate(np.load(SURROGATE_THETA), alpha, seed)
-    r["gates"] = {"phi_rel_l2_max": 5e-2, "energy_rel_diff_max": 1e-2, "speedup_min": 5.0,
-                  "pass": bool(r["phi_rel_l2"] <= 5e-2 and r["energy_rel_diff"] <= 1e-2 and r["speedup"] >= 5.0)}
-    r["workload"] = "spinodal-512x512 learned leap K=500 + 50 LBM steps to t=50000"
-    r["weights"] = os.path.relpath(SURROGATE_THETA, ROOT)
-    return r
+    theta = np.load(SURROGATE_THETA)
+    gates = {"phi_rel_l2_max": 5e-2, "energy_rel_diff_max": 1e-2, "speedup_min": 5.0}
+    runs = []
+    for a in alphas:
+        r = surrogate.evaluate(theta, a, seed)
+        r["pass"] = bool(r["phi_rel_l2"] <= gates["phi_rel_l2_max"] and
+                         r["energy_rel_diff"] <= gates["energy_rel_diff_max"] and r["speedup"] >= gates["speedup_min"])
+        runs.append(r)
+    return {"workload": "spinodal-512x512 learned leap K=500 + 50 LBM steps to t=50000, held-out seed",
+            "weights": os.path.relpath(SURROGATE_THETA, ROOT), "gates": gates, "by_alpha": runs,
+            "speedup": min(r["speedup"] for r in runs)}
 
 
 def cpu_oracle_rate(target_s: float = 12.0, n_sample: int = 2048):

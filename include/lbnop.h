@@ -11,12 +11,12 @@
  *   sig = root mean square of phi (1 for a zero field)
  *   phi / sig (H x W, FP32) -> 4 x 4 space-to-depth -> 16 channels at level 0 (H/4 x W/4)
  *   layer  c_in c_out level activation
- *   e0a      16   64   0   SiLU  (its pre-activation also gets alpha v, alpha of Eq. 6;
+ *   e0a      16   96   0   SiLU  (its pre-activation also gets alpha v, alpha of Eq. 6;
  *                               its input is stored as two BF16 halves, hi = bf16(x) and
  *                               lo = bf16(x - hi), both multiplied by its weights; so is
  *                               the input of lin and lina)
- *   e0b      64   64   0   SiLU  -> h0
- *   e1a      64   64   1   SiLU  (input: 2 x 2 average pool of h0)
+ *   e0b      96   96   0   SiLU  -> h0
+ *   e1a      96   64   1   SiLU  (input: 2 x 2 average pool of h0)
  *   e1b      64   64   1   SiLU  -> h1
  *   e2a      64   96   2   SiLU  (input: pool of h1)
  *   e2b      96   96   2   SiLU  -> h2
@@ -25,9 +25,9 @@
  *   d2a      96   96   2   SiLU  (input: nearest 2x upsampling of h3, plus h2)
  *   d2b      96   64   2   none
  *   d1a      64   64   1   SiLU  (input: upsampled d2b output, plus h1)
- *   d1b      64   64   1   none
- *   d0a      64   64   0   SiLU  (input: upsampled d1b output, plus h0)
- *   out      64   16   0   none
+ *   d1b      64   96   1   none
+ *   d0a      96   96   0   SiLU  (input: upsampled d1b output, plus h0)
+ *   out      96   16   0   none
  *   lin      16   16   0   none  (input: the e0a input; a linear path whose weights are
  *                               also kept as two BF16 halves, hi and lo = bf16(w - hi))
  *   lina     16   16   0   none  (input: the e0a input; output multiplied by alpha)
@@ -35,7 +35,7 @@
  *   phi_out = phi + scale sig (D - mean D)  (mean over the field, so mass is conserved)
  * Every layer is a 3 x 3 cross-correlation with periodic wrap plus a bias:
  *   z(p) = sum_{(dy, dx) in {-1,0,1}^2} W[3 (dy + 1) + (dx + 1)] x(p + (dy, dx)) + b.
- * Flat parameters (FP32, 687,696 values): for each layer in table order, W as
+ * Flat parameters (FP32, 826,096 values): for each layer in table order, W as
  * [9][c_out][c_in], then b [c_out]; after e0a's bias, its conditioning vector v [c_out].
  *
  * Arithmetic: the convolutions are implicit GEMMs on BF16 tensor-core operands with FP32
@@ -65,7 +65,7 @@ typedef struct {
   double scale;          /* phi_out = phi + scale sig (D - mean D); > 0 */
 } lbnop_params;
 
-/* Number of FP32 parameters (687,696). */
+/* Number of FP32 parameters (826,096). */
 int64_t lbnop_param_count(void);
 
 /* Device workspace for these parameters (weights, Adam state, activations and gradients

@@ -35,9 +35,9 @@ import numpy as np
 
 # name, c_in, c_out, level (resolution H/4 / 2^level), activation
 LAYERS = [
-    ("e0a", 16, 64, 0, True),
-    ("e0b", 64, 64, 0, True),
-    ("e1a", 64, 64, 1, True),
+    ("e0a", 16, 96, 0, True),
+    ("e0b", 96, 96, 0, True),
+    ("e1a", 96, 64, 1, True),
     ("e1b", 64, 64, 1, True),
     ("e2a", 64, 96, 2, True),
     ("e2b", 96, 96, 2, True),
@@ -46,9 +46,9 @@ LAYERS = [
     ("d2a", 96, 96, 2, True),
     ("d2b", 96, 64, 2, False),
     ("d1a", 64, 64, 1, True),
-    ("d1b", 64, 64, 1, False),
-    ("d0a", 64, 64, 0, True),
-    ("out", 64, 16, 0, False),
+    ("d1b", 64, 96, 1, False),
+    ("d0a", 96, 96, 0, True),
+    ("out", 96, 16, 0, False),
     ("lin", 16, 16, 0, False),    # linear path from the network input
     ("lina", 16, 16, 0, False),   # the same, its output multiplied by alpha
 ]

@@ -30,10 +30,10 @@ struct LayerSpec {
   bool act;
 };
 // The table of include/lbnop.h.
-constexpr LayerSpec kL[NL] = {{16, 64, 0, true},  {64, 64, 0, true},  {64, 64, 1, true},  {64, 64, 1, true},
+constexpr LayerSpec kL[NL] = {{16, 96, 0, true},  {96, 96, 0, true},  {96, 64, 1, true},  {64, 64, 1, true},
                               {64, 96, 2, true},  {96, 96, 2, true},  {96, 96, 3, true},  {96, 96, 3, true},
-                              {96, 96, 2, true},  {96, 64, 2, false}, {64, 64, 1, true},  {64, 64, 1, false},
-                              {64, 64, 0, true},  {64, 16, 0, false}, {16, 16, 0, false}, {16, 16, 0, false}};
+                              {96, 96, 2, true},  {96, 64, 2, false}, {64, 64, 1, true},  {64, 96, 1, false},
+                              {96, 96, 0, true},  {96, 16, 0, false}, {16, 16, 0, false}, {16, 16, 0, false}};
 enum { E0A, E0B, E1A, E1B, E2A, E2B, M3A, M3B, D2A, D2B, D1A, D1B, D0A, OUT, LIN, LINA };
 // Channels of the skip tensors h0..h3 at levels 0..3 (and of every tensor summed with them).
 constexpr int CH[4] = {kL[E0B].co, kL[E1B].co, kL[E2B].co, kL[M3B].co};

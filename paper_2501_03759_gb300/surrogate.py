@@ -35,8 +35,8 @@ SCALE = 0.01      # phi_out = phi + SCALE sig (D - mean D), sig the field's rms
 T_END = 50000
 WARMUP = 500      # plain LBM steps before the first leap (the noise of phi0 decays first)
 # (c_in, c_out) of the network's layers, in the order of include/lbnop.h
-LAYERS = [(16, 64), (64, 64), (64, 64), (64, 64), (64, 96), (96, 96), (96, 96), (96, 96),
-          (96, 96), (96, 64), (64, 64), (64, 64), (64, 64), (64, 16), (16, 16), (16, 16)]
+LAYERS = [(16, 96), (96, 96), (96, 64), (64, 64), (64, 96), (96, 96), (96, 96), (96, 96),
+          (96, 96), (96, 64), (64, 64), (64, 96), (96, 96), (96, 16), (16, 16), (16, 16)]
 OUT = 13  # the output layer; the two after it are the linear path
 
 

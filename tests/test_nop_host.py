@@ -7,7 +7,7 @@ from paper_2501_03759_gb300 import lbnop
 
 
 def test_param_count_matches_the_layout():
-    assert lbnop.lbnop_param_count() == N.param_count() == 687696
+    assert lbnop.lbnop_param_count() == N.param_count() == 826096
 
 
 @pytest.mark.parametrize("H,W,B,scale", [(31, 64, 1, 0.1), (64, 48, 1, 0.1), (64, 64, 0, 0.1), (64, 64, 65, 0.1),

@@ -102,8 +102,8 @@ def surrogate_theta(seed: int, out_scale: float = 1.0) -> np.ndarray:
     """A seeded parameter vector for the learned leap (flat layout of include/lbnop.h):
     He-normal 3 x 3 weights (std sqrt(2 / (9 c_in))), those of the output layer and the
     linear path scaled by out_scale, biases N(0, 0.01), conditioning vector N(0, 0.25), rounded to float32."""
-    layers = [(16, 64), (64, 64), (64, 64), (64, 64), (64, 96), (96, 96), (96, 96), (96, 96),
-              (96, 96), (96, 64), (64, 64), (64, 64), (64, 64), (64, 16), (16, 16), (16, 16)]
+    layers = [(16, 96), (96, 96), (96, 64), (64, 64), (64, 96), (96, 96), (96, 96), (96, 96),
+              (96, 96), (96, 64), (64, 64), (64, 96), (96, 96), (96, 16), (16, 16), (16, 16)]
     r = np.random.default_rng(seed)
     parts = []
     for k, (ci, co) in enumerate(layers):
