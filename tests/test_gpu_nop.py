@@ -32,6 +32,9 @@ def stream():
 
 
 SHAPES = [(2, 8, 12), (1, 1, 5), (3, 7, 3), (1, 16, 20)]
+# Enough pixels (>= 152 x 16 warps of 16) that the kernel keeps every output channel in one
+# block instead of slicing them by 16: the path training takes on large batches.
+LARGE = (4, 96, 104)
 CHANNELS = [(16, 32), (32, 64), (64, 96), (96, 96), (96, 16), (32, 16), (16, 16), (96, 64)]
 
 
@@ -225,3 +228,20 @@ def test_invalid_arguments():
     with pytest.raises(lbch.LbchError):
         s.set_params(bad)
     s.close()
+
+
+@pytest.mark.parametrize("ci,co", [(16, 96), (96, 96), (96, 64), (64, 96), (64, 64), (96, 16)])
+def test_conv_forward_and_data_grad_large_tiles(ci, co):
+    B, H, Wd = LARGE
+    x = W.bf16_exact((B, H, Wd, ci), 11, 1.0)
+    w = W.bf16_exact((9, co, ci), 12, 0.25)
+    dy = W.bf16_exact((B, H, Wd, co), 13, 1.0)
+    y = torch.empty((B, H, Wd, co), dtype=torch.float32, device="cuda")
+    dx = torch.empty((B, H, Wd, ci), dtype=torch.float32, device="cuda")
+    xd, wd, dyd = dev_bf16(x), dev_bf16(w), dev_bf16(dy)
+    lbnop.lbnop_conv3x3(xd.data_ptr(), wd.data_ptr(), None, B, H, Wd, ci, co, y.data_ptr(), stream())
+    lbnop.lbnop_conv3x3_bwd_data(dyd.data_ptr(), wd.data_ptr(), B, H, Wd, ci, co, dx.data_ptr(), stream())
+    ref = N.conv(x, w)
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-6 * (N.conv(np.abs(x), np.abs(w)).max() + 1.0)
+    ref = N.conv_bwd_data(dy, w)
+    assert np.abs(dx.cpu().numpy() - ref).max() <= 1e-6 * (N.conv_bwd_data(np.abs(dy), np.abs(w)).max() + 1.0)
