@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -547,6 +548,19 @@ __global__ void finite_kernel(const float* __restrict__ v, long long n, int* bad
 
 // ---------------------------------------------------------------- launch helpers
 
+// Multiprocessor count of the current device, queried once per device.
+int device_sms() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n == 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+    cache[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
+
 // Fields with few pixels (coarse levels, small batches) split the output channels over
 // blocks in slices of 16, so that enough warps run; large ones keep all channels per warp
 // and load each A fragment once.
@@ -554,9 +568,10 @@ template <int CI, int CO, bool TW>
 void conv_t(const ConvArgs& a, cudaStream_t s) {
   const int npix = a.B * a.H * a.W;
   const int tiles = (npix + 63) / 64;
+  const long long want_warps = (long long)device_sms() * 16;  // below this, slice the channels
   if constexpr (!TW && CI == 16 && CO == 16) {  // the linear path: low halves of input and weights
     if (a.x2 && a.w2) {
-      if ((long long)tiles * 4 < 152LL * 16)
+      if ((long long)tiles * 4 < want_warps)
         conv_kernel<CI, CO, 16, TW, true, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
       else
         conv_kernel<CI, CO, CO, TW, true, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
@@ -565,7 +580,7 @@ void conv_t(const ConvArgs& a, cudaStream_t s) {
   }
   if constexpr (!TW && CI == 16) {  // layers reading phi: optional low half of the input
     if (a.x2) {
-      if ((long long)tiles * 4 < 152LL * 16)
+      if ((long long)tiles * 4 < want_warps)
         conv_kernel<CI, CO, 16, TW, true><<<dim3(tiles, CO / 16), CONV_THREADS, 0, s>>>(a);
       else
         conv_kernel<CI, CO, CO, TW, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
@@ -573,7 +588,7 @@ void conv_t(const ConvArgs& a, cudaStream_t s) {
     }
   }
   if constexpr (!TW && CO > 16) {
-    if ((long long)tiles * 4 < 152LL * 16) {
+    if ((long long)tiles * 4 < want_warps) {
       conv_kernel<CI, CO, 16, TW, false><<<dim3(tiles, CO / 16), CONV_THREADS, 0, s>>>(a);
       return;
     }
@@ -636,7 +651,8 @@ void wgrad_launch(int ci, int co, const WgradArgs& a, cudaStream_t s) {
 
 int grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
-  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+  const long long cap = (long long)device_sms() * 16;
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 }  // namespace nop
