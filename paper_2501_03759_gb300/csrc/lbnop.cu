@@ -99,6 +99,49 @@ struct ConvArgs {
   float alpha[LBNOP_MAX_BATCH];
 };
 
+// Bias, conditioning, alpha scaling and the stores for the lane's two pixel rows (pixels
+// base + g and base + g + 8, ok[r] false past the end) and its NT pairs of channels
+// n0 + 8 j + 2 q, from the m16n8 accumulator layout.
+template <int CO, int NT>
+__device__ __forceinline__ void conv_epilogue(const ConvArgs& p, const float (&acc)[NT][4], int base, int n0,
+                                              int g, int q, const bool (&ok)[2], const int (&bi)[2]) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (!ok[r]) continue;
+    const int pix = base + g + 8 * r;
+    const float al = p.film ? p.alpha[bi[r]] : 0.0f;  // bi[r] is the row's sample
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int n = n0 + 8 * j + 2 * q;
+      float v0 = acc[j][2 * r], v1 = acc[j][2 * r + 1];
+      if (p.bias) {
+        v0 += p.bias[n];
+        v1 += p.bias[n + 1];
+      }
+      if (p.film) {
+        v0 = fmaf(al, p.film[n], v0);
+        v1 = fmaf(al, p.film[n + 1], v1);
+      }
+      if (p.scale_alpha) {
+        v0 *= p.alpha[bi[r]];
+        v1 *= p.alpha[bi[r]];
+      }
+      const size_t o = (size_t)pix * CO + n;
+      if (p.yf) {
+        float2* y = reinterpret_cast<float2*>(p.yf + o);
+        if (p.accumulate) {
+          const float2 old = *y;
+          *y = make_float2(old.x + v0, old.y + v1);
+        } else {
+          *y = make_float2(v0, v1);
+        }
+      }
+      if (p.z) *reinterpret_cast<__nv_bfloat162*>(p.z + o) = __floats2bfloat162_rn(v0, v1);
+      if (p.a) *reinterpret_cast<__nv_bfloat162*>(p.a + o) = __floats2bfloat162_rn(silu_f(v0), silu_f(v1));
+    }
+  }
+}
+
 constexpr int CONV_THREADS = 128;  // four warps, 16 pixels each
 
 // Each warp computes 16 consecutive pixels x BN output channels (the block's channel
@@ -164,41 +207,65 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(const ConvArgs p) {
     for (int j = 0; j < NT; ++j) mma_bf16(acc[j], a[kk & 1], b[kk & 1][j][0], b[kk & 1][j][1]);
   }
 
+  conv_epilogue<CO, NT>(p, acc, base, n0, g, q, ok, bi);
+}
+
+constexpr int SPLITK_THREADS = 9 * 32;  // one warp per tap
+
+// The same convolution for layers with few pixels: one block per 16 pixels x 16 output
+// channels, warp t multiplies tap t only (CI / 16 k-steps instead of 9 CI / 16), and the
+// nine partial tiles are added in shared memory in tap order before the epilogue. The
+// chain of dependent steps per warp is nine times shorter, so the coarse levels, which have
+// too few pixels to fill the GPU, stop waiting on it.
+template <int CI, int CO>
+__global__ void __launch_bounds__(SPLITK_THREADS) conv_splitk_kernel(const ConvArgs p) {
+  constexpr int CPT = CI / 16;
+  __shared__ float red[9][8][32];
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
+  const int HW = p.H * p.W, npix = p.B * HW;
+  const int base = blockIdx.x * 16, n0 = blockIdx.y * 16;
+  int bi[2], off[2];
+  bool ok[2];
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
-    if (!ok[r]) continue;
-    const int pix = base + g + 8 * r;
-    const float al = p.film ? p.alpha[bi[r]] : 0.0f;  // bi[r] is the row's sample
+    int pix = base + g + 8 * r;
+    ok[r] = pix < npix;
+    pix = ok[r] ? pix : base;  // out-of-range rows load a valid pixel; their results are dropped
+    bi[r] = pix / HW;
+    const int rem = pix - bi[r] * HW, h = rem / p.W, w = rem - h * p.W;
+    off[r] = ((bi[r] * p.H + wrap1(h + t / 3 - 1, p.H)) * p.W + wrap1(w + t % 3 - 1, p.W)) * CI + 2 * q;
+  }
+  float acc[2][4];
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const int n = n0 + 8 * j + 2 * q;
-      float v0 = acc[j][2 * r], v1 = acc[j][2 * r + 1];
-      if (p.bias) {
-        v0 += p.bias[n];
-        v1 += p.bias[n + 1];
-      }
-      if (p.film) {
-        v0 = fmaf(al, p.film[n], v0);
-        v1 = fmaf(al, p.film[n + 1], v1);
-      }
-      if (p.scale_alpha) {
-        v0 *= p.alpha[bi[r]];
-        v1 *= p.alpha[bi[r]];
-      }
-      const size_t o = (size_t)pix * CO + n;
-      if (p.yf) {
-        float2* y = reinterpret_cast<float2*>(p.yf + o);
-        if (p.accumulate) {
-          const float2 old = *y;
-          *y = make_float2(old.x + v0, old.y + v1);
-        } else {
-          *y = make_float2(v0, v1);
-        }
-      }
-      if (p.z) *reinterpret_cast<__nv_bfloat162*>(p.z + o) = __floats2bfloat162_rn(v0, v1);
-      if (p.a) *reinterpret_cast<__nv_bfloat162*>(p.a + o) = __floats2bfloat162_rn(silu_f(v0), silu_f(v1));
+  for (int j = 0; j < 2; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+  for (int cc = 0; cc < CPT; ++cc) {
+    const int c0 = cc * 16;
+    const uint32_t a[4] = {ld32(p.x + off[0] + c0), ld32(p.x + off[1] + c0), ld32(p.x + off[0] + c0 + 8),
+                           ld32(p.x + off[1] + c0 + 8)};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const bf16* wr = p.w + ((size_t)t * CO + n0 + 8 * j + g) * CI + c0 + 2 * q;
+      mma_bf16(acc[j], a, ld32(wr), ld32(wr + 8));
     }
   }
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) red[t][4 * j + e][lane] = acc[j][e];
+  __syncthreads();
+  if (t != 0) return;
+  float sum[2][4];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float v = red[0][4 * j + e][lane];
+#pragma unroll
+      for (int tt = 1; tt < 9; ++tt) v += red[tt][4 * j + e][lane];
+      sum[j][e] = v;
+    }
+  conv_epilogue<CO, 2>(p, sum, base, n0, g, q, ok, bi);
 }
 
 // ---------------------------------------------------------------- weight gradient
@@ -280,16 +347,27 @@ __global__ void __launch_bounds__(128) wgrad_kernel(const WgradArgs p) {
 
 // ---------------------------------------------------------------- elementwise and reductions
 
-constexpr int HEAD_BLOCKS = 32;  // partial sums per sample (fixed order: deterministic)
+constexpr int HEAD_BLOCKS = 128;  // partial sums per sample (fixed order: deterministic)
 
 // sig[b] = root mean square of field b from its sum of squares (1 for a zero field).
+// Sum of one sample's HEAD_BLOCKS partial sums by one warp, in a fixed order (valid in lane 0).
+__device__ __forceinline__ double warp_partials(const double* __restrict__ part, int lane) {
+  double v = 0.0;
+  for (int k = lane; k < HEAD_BLOCKS; k += 32) v += part[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One warp per sample (grid B, 32 threads).
 __global__ void rms_kernel(const double* __restrict__ partial2, int B, long long n, double* __restrict__ sig) {
-  const int b = threadIdx.x;
-  if (blockIdx.x != 0 || b >= B) return;
-  double s = 0.0;
-  for (int k = 0; k < HEAD_BLOCKS; ++k) s += partial2[b * HEAD_BLOCKS + k];
-  const double r = sqrt(s / (double)n);
-  sig[b] = r > 1e-30 ? r : 1.0;
+  const int b = blockIdx.x, lane = threadIdx.x;
+  if (b >= B) return;
+  const double s = warp_partials(partial2 + (size_t)b * HEAD_BLOCKS, lane);
+  if (lane == 0) {
+    const double r = sqrt(s / (double)n);
+    sig[b] = r > 1e-30 ? r : 1.0;
+  }
 }
 
 // x = phi / sig[b] ([B][H][W] FP32) -> [B][H/4][W/4][16], channel 4 di + dj = x[4 i + di][4 j + dj],
@@ -467,18 +545,23 @@ __global__ void scale_rows_kernel(const bf16* __restrict__ x, long long per, int
 __global__ void finish_sums_kernel(const double* __restrict__ partial, const double* __restrict__ partial2, int B,
                                    long long n, const SampleWeights w, double* __restrict__ mean,
                                    double* __restrict__ loss) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double tot2 = 0.0;
-  for (int b = 0; b < B; ++b) {
-    double s = 0.0, s2 = 0.0;
-    for (int k = 0; k < HEAD_BLOCKS; ++k) {
-      s += partial[b * HEAD_BLOCKS + k];
-      if (partial2) s2 += partial2[b * HEAD_BLOCKS + k];
+  // one block of 32 warps; warp k handles samples k and k + 32 (B <= 64)
+  __shared__ double s2s[LBNOP_MAX_BATCH];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int b = wid; b < B; b += 32) {
+    const double sm = warp_partials(partial + (size_t)b * HEAD_BLOCKS, lane);
+    const double s2 = partial2 ? warp_partials(partial2 + (size_t)b * HEAD_BLOCKS, lane) : 0.0;
+    if (lane == 0) {
+      mean[b] = sm / (double)n;
+      s2s[b] = s2;
     }
-    mean[b] = s / (double)n;
-    tot2 += (double)w.v[b] * s2;
   }
-  if (partial2) *loss = tot2 / ((double)B * (double)n);
+  __syncthreads();
+  if (threadIdx.x == 0 && partial2) {
+    double tot2 = 0.0;
+    for (int b = 0; b < B; ++b) tot2 += (double)w.v[b] * s2s[b];
+    *loss = tot2 / ((double)B * (double)n);
+  }
 }
 
 // phi_out = phi + scale sig[b] (D - mean D), D = depth-to-space of zout [B][H/4][W/4][16].
@@ -584,6 +667,13 @@ void conv_t(const ConvArgs& a, cudaStream_t s) {
         conv_kernel<CI, CO, 16, TW, true><<<dim3(tiles, CO / 16), CONV_THREADS, 0, s>>>(a);
       else
         conv_kernel<CI, CO, CO, TW, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
+      return;
+    }
+  }
+  if constexpr (!TW) {
+    // few enough blocks of 16 x 16 that about five per SM cover the layer: the coarse levels
+    if (!a.x2 && !a.w2 && (long long)((npix + 15) / 16) * (CO / 16) <= (long long)device_sms() * 5) {
+      conv_splitk_kernel<CI, CO><<<dim3((npix + 15) / 16, CO / 16), SPLITK_THREADS, 0, s>>>(a);
       return;
     }
   }
@@ -880,7 +970,7 @@ void forward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, int bat
   const long long P0 = (long long)batch * d.h[0] * d.w[0];
   const long long hw = (long long)c->p.H * c->p.W;
   sample_sums_kernel<<<dim3(HEAD_BLOCKS, batch), 256, 0, s>>>(d_phi, nullptr, hw, c->partial, c->partial2);
-  rms_kernel<<<1, 64, 0, s>>>(c->partial2, batch, hw, c->sig);
+  rms_kernel<<<batch, 32, 0, s>>>(c->partial2, batch, hw, c->sig);
   s2d_kernel<<<grid_for(P0, 256), 256, 0, s>>>(d_phi, c->sig, batch, c->p.H, c->p.W, c->x0, c->x0l);
   layer_fwd(c, E0A, d, c->x0, training, alpha);
   layer_fwd(c, E0B, d, c->a[E0A], training, alpha);
@@ -915,7 +1005,7 @@ void forward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, int bat
   // head: D - mean D per field
   const long long nz = (long long)d.h[0] * d.w[0] * 16;
   sample_sums_kernel<<<dim3(HEAD_BLOCKS, batch), 256, 0, s>>>(c->zout, nullptr, nz, c->partial, nullptr);
-  finish_sums_kernel<<<1, 32, 0, s>>>(c->partial, nullptr, batch, (long long)c->p.H * c->p.W, SampleWeights{},
+  finish_sums_kernel<<<1, 1024, 0, s>>>(c->partial, nullptr, batch, (long long)c->p.H * c->p.W, SampleWeights{},
                                       c->mean, nullptr);
   const long long n = (long long)batch * c->p.H * c->p.W;
   head_kernel<<<grid_for(n, 256), 256, 0, s>>>(d_phi, c->zout, c->mean, c->sig, batch, c->p.H, c->p.W,
@@ -992,7 +1082,7 @@ void backward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, const 
     w.v[b] = weight ? (float)weight[b] : 1.0f;
     coef.v[b] = (float)(c->p.scale * 2.0 * (weight ? weight[b] : 1.0) / (double)n);
   }
-  finish_sums_kernel<<<1, 32, 0, s>>>(c->partial, c->partial2, batch, hw, w, c->mean, c->loss);
+  finish_sums_kernel<<<1, 1024, 0, s>>>(c->partial, c->partial2, batch, hw, w, c->mean, c->loss);
   cudaMemsetAsync(c->grad, 0, c->n_params * sizeof(float), s);
   head_bwd_kernel<<<grid_for(n, 256), 256, 0, s>>>(phi_out, d_target, c->mean, c->sig, batch, c->p.H, c->p.W, coef,
                                                    c->dz[0]);

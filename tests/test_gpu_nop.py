@@ -245,3 +245,18 @@ def test_conv_forward_and_data_grad_large_tiles(ci, co):
     assert np.abs(y.cpu().numpy() - ref).max() <= 1e-6 * (N.conv(np.abs(x), np.abs(w)).max() + 1.0)
     ref = N.conv_bwd_data(dy, w)
     assert np.abs(dx.cpu().numpy() - ref).max() <= 1e-6 * (N.conv_bwd_data(np.abs(dy), np.abs(w)).max() + 1.0)
+
+
+# Mid-size layers (too many output warps for the per-tap split, too few to keep all channels
+# in one block): the channel-sliced path a single 512^2 field takes at level 0.
+@pytest.mark.parametrize("ci,co,shape", [(96, 96, (1, 64, 128)), (16, 96, (1, 64, 128)), (64, 64, (1, 96, 128)),
+                                         (96, 64, (1, 96, 128))])
+def test_conv_forward_mid_tiles(ci, co, shape):
+    B, H, Wd = shape
+    x = W.bf16_exact((B, H, Wd, ci), 14, 1.0)
+    w = W.bf16_exact((9, co, ci), 15, 0.25)
+    y = torch.empty((B, H, Wd, co), dtype=torch.float32, device="cuda")
+    xd, wd = dev_bf16(x), dev_bf16(w)
+    lbnop.lbnop_conv3x3(xd.data_ptr(), wd.data_ptr(), None, B, H, Wd, ci, co, y.data_ptr(), stream())
+    ref = N.conv(x, w)
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-6 * (N.conv(np.abs(x), np.abs(w)).max() + 1.0)
