@@ -111,7 +111,7 @@ lbch_status lbnop_leap_run(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cy
 /* Operator entry points (device pointers, the given stream, asynchronous), as used by
  * the network. BF16 tensors are uint16_t bit patterns, channels last:
  *   x [B][H][W][c_in], w [9][c_out][c_in], y [B][H][W][c_out].
- * c_in and c_out must be 16, 32, 64 or 96; any H, W >= 1.
+ * c_in and c_out must be 16, 64 or 96 (the widths of the network); any H, W >= 1.
  *   conv3x3:             y = conv(x, w) + bias (bias may be NULL), FP32 out.
  *   conv3x3_bwd_data:    dx = sum_d w_d^T dy(p - d), FP32 out ([B][H][W][c_in]).
  *   conv3x3_bwd_weight:  dw[d] = sum_p dy(p) x(p + d)^T, FP32 out ([9][c_out][c_in]),

@@ -268,6 +268,107 @@ __global__ void __launch_bounds__(SPLITK_THREADS) conv_splitk_kernel(const ConvA
   conv_epilogue<CO, 2>(p, sum, base, n0, g, q, ok, bi);
 }
 
+// ---------------------------------------------------------------- convolution, shared-memory staged
+
+__device__ __forceinline__ void cp_async16_cg(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const bf16* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+template <int CI, int BN>
+constexpr int conv_smem_bytes() {
+  return 2 * (64 + BN) * (CI + 8) * 2 + 64 * 16;
+}
+
+// The convolution with its operands staged through shared memory: a block computes 64
+// pixels x BN output channels (slice blockIdx.y). For each tap it copies the 64 shifted
+// input rows (CI channels each) and the tap's BN x CI weights with 16-byte cp.async into a
+// two-stage ring (the next tap lands while this one multiplies), and each warp reads its
+// fragments with ldmatrix: A (16 pixels x 16 channels) once per k-step, B in pairs of
+// 8-channel tiles. Rows are padded by 16 bytes so that ldmatrix rows hit distinct banks.
+template <int CI, int CO, int BN>
+__global__ void __launch_bounds__(CONV_THREADS) conv_smem_kernel(const ConvArgs p) {
+  constexpr int PA = CI + 8, NT = BN / 8, CPT = CI / 16, CH = CI / 8;
+  static_assert(NT % 2 == 0, "n-tiles come in pairs");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  bf16* stage_base = reinterpret_cast<bf16*>(smem_raw);
+  int4* spix = reinterpret_cast<int4*>(smem_raw + 2 * (64 + BN) * PA * 2);  // (b, h, w, ok) per tile pixel
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, q = lane & 3;
+  const int HW = p.H * p.W, npix = p.B * HW;
+  const int base0 = blockIdx.x * 64, n0 = blockIdx.y * BN;
+  if (tid < 64) {
+    int pix = base0 + tid;
+    const int ok = pix < npix;
+    pix = ok ? pix : base0;  // rows past the end copy a valid pixel; their results are dropped
+    const int b = pix / HW, rem = pix - b * HW, h = rem / p.W;
+    spix[tid] = make_int4(b, h, rem - h * p.W, ok);
+  }
+  __syncthreads();
+  auto stage = [&](int t, int buf) {
+    bf16* sA = stage_base + buf * (64 + BN) * PA;
+    bf16* sB = sA + 64 * PA;
+    const int dy = t / 3 - 1, dx = t % 3 - 1;
+    for (int v = tid; v < 64 * CH; v += CONV_THREADS) {
+      const int r = v / CH, c = v - r * CH;
+      const int4 pb = spix[r];
+      cp_async16_cg(sA + r * PA + 8 * c,
+                    p.x + ((size_t)(pb.x * p.H + wrap1(pb.y + dy, p.H)) * p.W + wrap1(pb.z + dx, p.W)) * CI + 8 * c);
+    }
+    for (int v = tid; v < BN * CH; v += CONV_THREADS) {
+      const int n = v / CH, c = v - n * CH;
+      cp_async16_cg(sB + n * PA + 8 * c, p.w + ((size_t)t * CO + n0 + n) * CI + 8 * c);
+    }
+  };
+  float acc[NT][4];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+  stage(0, 0);
+  cp_async_commit_group();
+#pragma unroll 1
+  for (int t = 0; t < 9; ++t) {
+    if (t + 1 < 9) stage(t + 1, (t + 1) & 1);
+    cp_async_commit_group();  // (empty after the last tap)
+    cp_async_wait_group<1>();  // tap t has landed for this thread
+    __syncthreads();           // and for everyone
+    const bf16* sA = stage_base + (t & 1) * (64 + BN) * PA + (warp * 16) * PA;
+    const bf16* sB = stage_base + (t & 1) * (64 + BN) * PA + 64 * PA;
+#pragma unroll
+    for (int kk = 0; kk < CPT; ++kk) {
+      uint32_t a[4];
+      ldsm_x4(a, sA + (lane & 15) * PA + kk * 16 + (lane >> 4) * 8);
+#pragma unroll
+      for (int jp = 0; jp < NT / 2; ++jp) {
+        uint32_t b[4];  // {b0, b1} of n-tile 2 jp, then of n-tile 2 jp + 1
+        ldsm_x4(b, sB + (jp * 16 + (lane >> 4) * 8 + (lane & 7)) * PA + kk * 16 + ((lane >> 3) & 1) * 8);
+        mma_bf16(acc[2 * jp], a, b[0], b[1]);
+        mma_bf16(acc[2 * jp + 1], a, b[2], b[3]);
+      }
+    }
+    __syncthreads();  // the buffer of tap t is refilled with tap t + 2 next
+  }
+  const int base = base0 + warp * 16;
+  int bi[2];
+  bool ok[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int4 pb = spix[warp * 16 + g + 8 * r];
+    bi[r] = pb.x;
+    ok[r] = pb.w != 0;
+  }
+  conv_epilogue<CO, NT>(p, acc, base, n0, g, q, ok, bi);
+}
+
 // ---------------------------------------------------------------- weight gradient
 
 struct WgradArgs {
@@ -647,43 +748,64 @@ int device_sms() {
 // Fields with few pixels (coarse levels, small batches) split the output channels over
 // blocks in slices of 16, so that enough warps run; large ones keep all channels per warp
 // and load each A fragment once.
+// conv_smem_kernel with its dynamic shared memory (opted in once per device above 48 KB).
+template <int CI, int CO, int BN>
+void launch_smem(const ConvArgs& a, dim3 grid, cudaStream_t s) {
+  constexpr int bytes = conv_smem_bytes<CI, BN>();
+  if constexpr (bytes > 48 * 1024) {
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(done.load(std::memory_order_relaxed) & bit)) {
+      cudaFuncSetAttribute(conv_smem_kernel<CI, CO, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      done.fetch_or(bit, std::memory_order_relaxed);
+    }
+  }
+  conv_smem_kernel<CI, CO, BN><<<grid, CONV_THREADS, bytes, s>>>(a);
+}
+
 template <int CI, int CO, bool TW>
 void conv_t(const ConvArgs& a, cudaStream_t s) {
   const int npix = a.B * a.H * a.W;
   const int tiles = (npix + 63) / 64;
   const long long want_warps = (long long)device_sms() * 16;  // below this, slice the channels
-  if constexpr (!TW && CI == 16 && CO == 16) {  // the linear path: low halves of input and weights
-    if (a.x2 && a.w2) {
-      if ((long long)tiles * 4 < want_warps)
-        conv_kernel<CI, CO, 16, TW, true, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
-      else
-        conv_kernel<CI, CO, CO, TW, true, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
-      return;
+  if constexpr (TW) {  // the operator entry point on forward-layout weights (register-fed)
+    conv_kernel<CI, CO, CO, true, false><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
+  } else {
+    if constexpr (CI == 16) {  // layers reading phi: low halves of the input (and weights)
+      if (a.x2 && a.w2) {
+        if constexpr (CO == 16) {
+          if ((long long)tiles * 4 < want_warps)
+            conv_kernel<CI, CO, 16, false, true, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
+          else
+            conv_kernel<CI, CO, CO, false, true, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
+        }
+        return;
+      }
+      if (a.x2) {
+        if ((long long)tiles * 4 < want_warps)
+          conv_kernel<CI, CO, 16, false, true><<<dim3(tiles, CO / 16), CONV_THREADS, 0, s>>>(a);
+        else
+          conv_kernel<CI, CO, CO, false, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
+        return;
+      }
     }
-  }
-  if constexpr (!TW && CI == 16) {  // layers reading phi: optional low half of the input
-    if (a.x2) {
-      if ((long long)tiles * 4 < want_warps)
-        conv_kernel<CI, CO, 16, TW, true><<<dim3(tiles, CO / 16), CONV_THREADS, 0, s>>>(a);
-      else
-        conv_kernel<CI, CO, CO, TW, true><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
-      return;
-    }
-  }
-  if constexpr (!TW) {
     // few enough blocks of 16 x 16 that about five per SM cover the layer: the coarse levels
-    if (!a.x2 && !a.w2 && (long long)((npix + 15) / 16) * (CO / 16) <= (long long)device_sms() * 5) {
+    if ((long long)((npix + 15) / 16) * (CO / 16) <= (long long)device_sms() * 5) {
       conv_splitk_kernel<CI, CO><<<dim3((npix + 15) / 16, CO / 16), SPLITK_THREADS, 0, s>>>(a);
       return;
     }
-  }
-  if constexpr (!TW && CO > 16) {
-    if ((long long)tiles * 4 < want_warps) {
-      conv_kernel<CI, CO, 16, TW, false><<<dim3(tiles, CO / 16), CONV_THREADS, 0, s>>>(a);
-      return;
+    // operands staged through shared memory; mid-size layers split the output channels into
+    // slices of 32 so that enough blocks run
+    if constexpr (CO > 16) {
+      if ((long long)tiles * 4 < want_warps) {
+        launch_smem<CI, CO, 32>(a, dim3(tiles, CO / 32), s);
+        return;
+      }
     }
+    launch_smem<CI, CO, CO>(a, dim3(tiles, 1), s);
   }
-  conv_kernel<CI, CO, CO, TW, false><<<dim3(tiles, 1), CONV_THREADS, 0, s>>>(a);
 }
 
 template <int CI, int CO>
@@ -692,27 +814,20 @@ void wgrad_t(const WgradArgs& a, cudaStream_t s) {
   wgrad_kernel<CI, CO><<<dim3((npix + a.chunk - 1) / a.chunk, 9), 128, 0, s>>>(a);
 }
 
-bool channels_ok(int c) { return c == 16 || c == 32 || c == 64 || c == 96; }
+bool channels_ok(int c) { return c == 16 || c == 64 || c == 96; }
 
-#define NOP_CH_SWITCH(CI, CO, CALL)                    \
-  switch (CI * 1000 + CO) {                            \
-    case 16016: CALL(16, 16); break;                   \
-    case 16032: CALL(16, 32); break;                   \
-    case 16064: CALL(16, 64); break;                   \
-    case 16096: CALL(16, 96); break;                   \
-    case 32016: CALL(32, 16); break;                   \
-    case 32032: CALL(32, 32); break;                   \
-    case 32064: CALL(32, 64); break;                   \
-    case 32096: CALL(32, 96); break;                   \
-    case 64016: CALL(64, 16); break;                   \
-    case 64032: CALL(64, 32); break;                   \
-    case 64064: CALL(64, 64); break;                   \
-    case 64096: CALL(64, 96); break;                   \
-    case 96016: CALL(96, 16); break;                   \
-    case 96032: CALL(96, 32); break;                   \
-    case 96064: CALL(96, 64); break;                   \
-    case 96096: CALL(96, 96); break;                   \
-    default: break;                                    \
+#define NOP_CH_SWITCH(CI, CO, CALL) \
+  switch (CI * 1000 + CO) {          \
+    case 16016: CALL(16, 16); break; \
+    case 16064: CALL(16, 64); break; \
+    case 16096: CALL(16, 96); break; \
+    case 64016: CALL(64, 16); break; \
+    case 64064: CALL(64, 64); break; \
+    case 64096: CALL(64, 96); break; \
+    case 96016: CALL(96, 16); break; \
+    case 96064: CALL(96, 64); break; \
+    case 96096: CALL(96, 96); break; \
+    default: break;                  \
   }
 
 void conv_launch(int ci, int co, bool tw, const ConvArgs& a, cudaStream_t s) {

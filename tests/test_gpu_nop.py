@@ -35,7 +35,7 @@ SHAPES = [(2, 8, 12), (1, 1, 5), (3, 7, 3), (1, 16, 20)]
 # Enough pixels (>= 152 x 16 warps of 16) that the kernel keeps every output channel in one
 # block instead of slicing them by 16: the path training takes on large batches.
 LARGE = (4, 96, 104)
-CHANNELS = [(16, 32), (32, 64), (64, 96), (96, 96), (96, 16), (32, 16), (16, 16), (96, 64)]
+CHANNELS = [(16, 64), (64, 64), (64, 96), (96, 96), (96, 16), (64, 16), (16, 16), (96, 64), (16, 96)]
 
 
 @pytest.mark.parametrize("ci,co", CHANNELS)
