@@ -95,8 +95,17 @@ lbch_status lbnop_backward(lbnop_ctx* c, const float* d_phi, const double* h_alp
 lbch_status lbnop_get_grads(lbnop_ctx* c, float* h_grad);     /* synchronises */
 
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with learning rate lr
- * on the gradient of the last lbnop_backward. Asynchronous. */
+ * on the gradient g of the last lbnop_backward, scaled first by min(1, max_norm / |g|)
+ * (|g| the L2 norm over all parameters) when a clip is set. Asynchronous. */
 lbch_status lbnop_adam(lbnop_ctx* c, double lr);
+
+/* Global-norm gradient clipping for the following Adam steps: max_norm > 0 clips, 0 (the
+ * default) turns it off; LBCH_EINVAL for a negative or non-finite value. */
+lbch_status lbnop_set_clip(lbnop_ctx* c, double max_norm);
+
+/* The L2 norm over all parameters of the last lbnop_backward's gradient, before any
+ * clipping. Synchronises. LBCH_EINVAL before the first backward. */
+lbch_status lbnop_grad_norm(lbnop_ctx* c, double* h_norm);
 
 /* lbnop_backward followed by lbnop_adam. */
 lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,

@@ -279,6 +279,15 @@ def backward(theta: np.ndarray, s: dict, dphi_out: np.ndarray, scale: float) -> 
     return pack(G)
 
 
+def clip_global_norm(grad, max_norm):
+    """Global-norm gradient clipping: grad scaled by min(1, max_norm / |grad|_2); max_norm 0
+    leaves it unchanged."""
+    nrm = float(np.sqrt(np.sum(np.asarray(grad, dtype=np.float64) ** 2)))
+    if max_norm > 0.0 and nrm > max_norm:
+        return grad * (max_norm / nrm)
+    return grad
+
+
 def adam(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam step (Kingma, Ba 2015, Algorithm 1); t counts from 1. Returns new arrays."""
     m = beta1 * m + (1.0 - beta1) * grad

@@ -692,16 +692,34 @@ __global__ void head_bwd_kernel(const float* __restrict__ phi_out, const float* 
   }
 }
 
-// Adam (Kingma and Ba 2015, Algorithm 1; c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)),
-// then the BF16 copies of every weight: wf[t][co][ci] and wb[t][ci][co] = W[8 - t][co][ci].
+// *norm = sqrt(sum_k grad[k]^2), the global L2 norm of the gradient (one block, fixed order).
+__global__ void grad_norm_kernel(const float* __restrict__ grad, long long n, double* __restrict__ norm) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+    const double g = grad[k];
+    s = fma(g, g, s);
+  }
+  s = block_sum_d(s, sh);
+  if (threadIdx.x == 0) *norm = sqrt(s);
+}
+
+// Adam (Kingma and Ba 2015, Algorithm 1; c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)) on
+// the gradient scaled by min(1, clip / |grad|) when clip > 0 (global-norm clipping), then the
+// BF16 copies of every weight: wf[t][co][ci] and wb[t][ci][co] = W[8 - t][co][ci].
 __global__ void adam_kernel(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
                             const float* __restrict__ grad, long long n, float lr, float c1, float c2, int update,
-                            const LayerTab tab, bf16* __restrict__ wf, bf16* __restrict__ wb,
-                            bf16* __restrict__ wlo) {
+                            const double* __restrict__ gnorm, double clip, const LayerTab tab,
+                            bf16* __restrict__ wf, bf16* __restrict__ wb, bf16* __restrict__ wlo) {
+  float gscale = 1.0f;
+  if (update && clip > 0.0) {
+    const double nrm = *gnorm;
+    if (nrm > clip) gscale = (float)(clip / nrm);
+  }
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     float th = theta[k];
     if (update) {
-      const float gk = grad[k];
+      const float gk = grad[k] * gscale;
       const float mk = fmaf(0.9f, m[k], 0.1f * gk);
       const float vk = fmaf(0.999f, v[k], 0.001f * gk * gk);
       m[k] = mk;
@@ -882,6 +900,8 @@ struct lbnop_ctx {
   float *g0a, *g0b, *g1a, *g1b, *g2a, *g2b, *g3a;
   float* zout;
   double *partial, *partial2, *mean, *loss, *sig;
+  double* gnorm;  // global L2 norm of the last gradient
+  double clip;    // Adam clips the gradient to this global norm; 0: off
   float *leap0, *leap1;
   float* phi_out;  // [max_batch][H][W], the training forward's output
   int* flags;
@@ -965,6 +985,7 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
   char* mean = take(LBNOP_MAX_BATCH * 8);
   char* sig = take(LBNOP_MAX_BATCH * 8);
   char* loss = take(8);
+  char* gnorm = take(8);
   char* leap0 = take((size_t)p->H * p->W * 4);
   char* leap1 = take((size_t)p->H * p->W * 4);
   char* phi_out = take((size_t)p->max_batch * p->H * p->W * 4);
@@ -1006,6 +1027,7 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
     c->mean = (double*)mean;
     c->sig = (double*)sig;
     c->loss = (double*)loss;
+    c->gnorm = (double*)gnorm;
     c->leap0 = (float*)leap0;
     c->leap1 = (float*)leap1;
     c->phi_out = (float*)phi_out;
@@ -1241,6 +1263,7 @@ void backward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, const 
   layer_bwd(c, E0B, d, c->a[E0A], c->g0a, alpha);
   make_dz(c, d, 0, kL[E0A].co, c->g0a, nullptr, c->z[E0A]);
   layer_bwd(c, E0A, d, c->x0, nullptr, alpha);
+  grad_norm_kernel<<<1, 1024, 0, s>>>(c->grad, c->n_params, c->gnorm);
   c->last_batch = batch;
 }
 
@@ -1252,8 +1275,8 @@ void refresh_or_update(lbnop_ctx* c, bool update, double lr) {
     c2 = (float)(1.0 / (1.0 - std::pow(0.999, (double)c->adam_t)));
   }
   adam_kernel<<<grid_for(c->n_params, 256), 256, 0, c->stream>>>(c->theta, c->m, c->v, c->grad, c->n_params,
-                                                                 (float)lr, c1, c2, update ? 1 : 0, c->tab, c->wf,
-                                                                 c->wb, c->wlo);
+                                                                 (float)lr, c1, c2, update ? 1 : 0, c->gnorm,
+                                                                 c->clip, c->tab, c->wf, c->wb, c->wlo);
 }
 
 lbch_status check_batch(lbnop_ctx* c, int batch, const double* h_alpha) {
@@ -1402,6 +1425,31 @@ lbch_status lbnop_adam(lbnop_ctx* c, double lr) {
   }
   refresh_or_update(c, true, lr);
   return done(c, "adam: launch");
+}
+
+lbch_status lbnop_set_clip(lbnop_ctx* c, double max_norm) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!(max_norm >= 0.0) || !std::isfinite(max_norm)) {
+    set_err(c, "set_clip: max_norm must be finite and >= 0");
+    return LBCH_EINVAL;
+  }
+  c->clip = max_norm;
+  return LBCH_OK;
+}
+
+lbch_status lbnop_grad_norm(lbnop_ctx* c, double* h_norm) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!h_norm) return LBCH_EINVAL;
+  if (c->last_batch == 0) {
+    set_err(c, "grad_norm: no gradient yet (call lbnop_backward first)");
+    return LBCH_EINVAL;
+  }
+  if (cuda_bad(c, cudaMemcpyAsync(h_norm, c->gnorm, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "gnorm") ||
+      cuda_bad(c, cudaStreamSynchronize(c->stream), "grad_norm: sync"))
+    return LBCH_ECUDA;
+  return LBCH_OK;
 }
 
 lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_alpha, const float* d_target,

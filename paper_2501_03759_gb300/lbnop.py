@@ -53,6 +53,10 @@ def load():
         lib.lbnop_backward.restype = ctypes.c_int
         lib.lbnop_adam.argtypes = [vp, ctypes.c_double]
         lib.lbnop_adam.restype = ctypes.c_int
+        lib.lbnop_set_clip.argtypes = [vp, ctypes.c_double]
+        lib.lbnop_set_clip.restype = ctypes.c_int
+        lib.lbnop_grad_norm.argtypes = [vp, dp]
+        lib.lbnop_grad_norm.restype = ctypes.c_int
         lib.lbnop_train_step.argtypes = [vp, vp, dp, vp, dp, i32, ctypes.c_double, dp]
         lib.lbnop_train_step.restype = ctypes.c_int
         lib.lbnop_leap_run.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64]
@@ -138,6 +142,16 @@ def lbnop_backward(ctx, d_phi: int, alpha, d_target: int, batch: int, want_loss:
 
 def lbnop_adam(ctx, lr: float) -> None:
     _check(ctx, load().lbnop_adam(ctx, float(lr)), "lbnop_adam")
+
+
+def lbnop_set_clip(ctx, max_norm: float) -> None:
+    _check(ctx, load().lbnop_set_clip(ctx, float(max_norm)), "lbnop_set_clip")
+
+
+def lbnop_grad_norm(ctx) -> float:
+    out = ctypes.c_double(float("nan"))
+    _check(ctx, load().lbnop_grad_norm(ctx, ctypes.byref(out)), "lbnop_grad_norm")
+    return out.value
 
 
 def lbnop_train_step(ctx, d_phi: int, alpha, d_target: int, batch: int, lr: float, want_loss: bool = False,
@@ -245,6 +259,15 @@ class Surrogate:
     def adam(self, lr: float) -> None:
         with self._on():
             lbnop_adam(self.ctx, lr)
+
+    def set_clip(self, max_norm: float) -> None:
+        """Global-norm gradient clipping for the following Adam steps (0: off)."""
+        lbnop_set_clip(self.ctx, max_norm)
+
+    def grad_norm(self) -> float:
+        """L2 norm of the last backward's gradient, before clipping (synchronises)."""
+        with self._on():
+            return lbnop_grad_norm(self.ctx)
 
     def train_step(self, phi, alpha, target, lr: float, want_loss: bool = False, weight=None):
         b = self._fields(phi, "phi")

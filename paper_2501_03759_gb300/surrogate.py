@@ -34,6 +34,9 @@ CORR = 50         # LBM correction steps after each leap
 SCALE = 0.01      # phi_out = phi + SCALE sig (D - mean D), sig the field's rms
 T_END = 50000
 WARMUP = 500      # plain LBM steps before the first leap (the noise of phi0 decays first)
+CLIP = 3.0        # training clips each gradient to CLIP x the median norm of recent steps
+CLIP_WINDOW = 200
+CLIP_START = 20
 # (c_in, c_out) of the network's layers, in the order of include/lbnop.h
 LAYERS = [(16, 96), (96, 96), (96, 64), (64, 64), (64, 96), (96, 96), (96, 96), (96, 96),
           (96, 96), (96, 64), (64, 64), (64, 96), (96, 96), (96, 16), (16, 16), (16, 16)]
@@ -88,10 +91,16 @@ def generate(runs, n: int = 512, t_end: int = T_END, every: int = EVERY):
 
 
 def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: float = 1e-5, seed: int = 0,
-          theta0=None, log_every: int = 200):
+          theta0=None, log_every: int = 200, clip: float = CLIP):
     """Adam on the leap error over random (run, t) pairs, each pair weighted by the inverse of
     its own mean squared change (so that the identity map scores 1 on every pair and small
-    late-time changes count as much as the early decay of the noise); cosine learning rate."""
+    late-time changes count as much as the early decay of the noise); cosine learning rate.
+
+    With clip > 0, each step's gradient is clipped to `clip` times the median global norm
+    of the last CLIP_WINDOW steps (from step CLIP_START on): a rare batch whose gradient is
+    orders of magnitude above the rest otherwise moves every weight by about 30 lr through
+    Adam's momentum, and the second-moment estimate it inflates then stalls learning for
+    thousands of steps."""
     import torch
 
     count, snaps, n, _ = data.shape
@@ -103,6 +112,8 @@ def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: f
     y = torch.empty_like(x)
     alphas = np.asarray(alphas, dtype=np.float64)
     log = []
+    norms = []
+    clipped = 0
     t0 = time.perf_counter()
     for it in range(iters):
         ri = r.integers(0, count, batch)
@@ -114,9 +125,14 @@ def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: f
         want = (it % log_every == 0) or it == iters - 1
         change = ((y - x) ** 2).mean(dim=(1, 2)).double().cpu().numpy()
         weight = 1.0 / np.maximum(change, 1e-30)
+        limit = clip * float(np.median(norms[-CLIP_WINDOW:])) if clip > 0 and len(norms) >= CLIP_START else 0.0
+        s.set_clip(limit)
         loss = s.train_step(x, alphas[ri], y, rate, want_loss=want, weight=weight)
+        norms.append(s.grad_norm())
+        clipped += int(0.0 < limit < norms[-1])
         if want:
-            log.append({"iter": it, "relative_loss": loss, "lr": rate, "seconds": time.perf_counter() - t0})
+            log.append({"iter": it, "relative_loss": loss, "lr": rate, "grad_norm": norms[-1], "clip": limit,
+                        "clipped_so_far": clipped, "seconds": time.perf_counter() - t0})
     torch.cuda.synchronize()
     theta = s.params_host()
     s.close()
@@ -216,6 +232,7 @@ def main(argv=None):
     t.add_argument("--iters", type=int, default=3000)
     t.add_argument("--batch", type=int, default=16)
     t.add_argument("--lr", type=float, default=1e-3)
+    t.add_argument("--clip", type=float, default=CLIP, help="clip factor over the median recent norm; 0: off")
     e = sub.add_parser("eval")
     e.add_argument("--theta", required=True)
     e.add_argument("--alpha", type=float, nargs="+", default=[0.3])
@@ -231,10 +248,11 @@ def main(argv=None):
         t0 = time.perf_counter()
         data = generate(runs, args.n)
         t_gen = time.perf_counter() - t0
-        theta, log = train(data, [a for a, _ in runs], args.iters, args.batch, args.lr)
+        theta, log = train(data, [a for a, _ in runs], args.iters, args.batch, args.lr, clip=args.clip)
         t_train = time.perf_counter() - t0 - t_gen
         np.save(os.path.join(args.out, "leap_theta.npy"), theta.astype(np.float32))
         report = {"runs": runs, "n": args.n, "iters": args.iters, "batch": args.batch, "lr": args.lr,
+                  "clip": args.clip,
                   "leap": LEAP, "every": EVERY, "scale": SCALE, "t_end": T_END,
                   "seconds_generate": t_gen, "seconds_train": t_train, "log": log}
         with open(os.path.join(args.out, "train_report.json"), "w") as fh:

@@ -163,6 +163,42 @@ def test_first_adam_step_is_the_closed_form():
     s.close()
 
 
+def test_clipped_adam_steps_match_oracle():
+    # Two Adam steps: the first unclipped, the second with the gradient clipped to half its
+    # global norm (the first step alone is scale-invariant, so the second one shows the clip).
+    B, H, Wd = 2, 32, 64
+    theta, phi, target, alpha = network_case(B, H, Wd, seed=9)
+    s = lbnop.Surrogate(H, Wd, max_batch=B, scale=0.05)
+    s.set_params(theta)
+    pd, td = torch.from_numpy(phi.astype(np.float32)).cuda(), torch.from_numpy(target.astype(np.float32)).cuda()
+    lr = 1e-3
+    s.backward(pd, alpha, td)
+    g1 = s.grads_host().astype(np.float64)
+    assert abs(s.grad_norm() - np.linalg.norm(g1)) <= 1e-9 * np.linalg.norm(g1)
+    th0 = s.params_host().astype(np.float64)
+    s.adam(lr)
+    th1 = s.params_host().astype(np.float64)
+    s.backward(pd, alpha, td)
+    g2 = s.grads_host().astype(np.float64)
+    n2 = s.grad_norm()
+    assert abs(n2 - np.linalg.norm(g2)) <= 1e-9 * np.linalg.norm(g2)
+    s.set_clip(0.5 * n2)
+    s.adam(lr)
+    th2 = s.params_host().astype(np.float64)
+    r1, m1, v1 = N.adam(th0, g1, np.zeros_like(g1), np.zeros_like(g1), 1, lr)
+    assert np.abs(th1 - r1).max() <= 1e-6
+    r2, _, _ = N.adam(th1, N.clip_global_norm(g2, 0.5 * n2), m1, v1, 2, lr)
+    r2u, _, _ = N.adam(th1, g2, m1, v1, 2, lr)
+    err, err_u = np.abs(th2 - r2).max(), np.abs(th2 - r2u).max()
+    print(f"clipped Adam: max |theta - oracle| {err:.2e} (unclipped oracle differs by {err_u:.2e})")
+    assert err <= 1e-6 and err_u > 10 * err
+    with pytest.raises(lbch.LbchError):
+        s.set_clip(-1.0)
+    with pytest.raises(lbch.LbchError):
+        s.set_clip(float("nan"))
+    s.close()
+
+
 def test_training_reduces_the_loss():
     B, H, Wd = 4, 64, 64
     teacher = W.surrogate_theta(7, out_scale=0.5)
@@ -223,6 +259,8 @@ def test_invalid_arguments():
         s.forward(phi, [0.1, 0.2, 0.3])  # batch 3 > max_batch 2
     with pytest.raises(lbch.LbchError):
         s.adam(1e-3)  # no gradient yet
+    with pytest.raises(lbch.LbchError):
+        s.grad_norm()  # no gradient yet
     bad = W.surrogate_theta(0)
     bad[5] = np.nan
     with pytest.raises(lbch.LbchError):
@@ -260,3 +298,28 @@ def test_conv_forward_mid_tiles(ci, co, shape):
     lbnop.lbnop_conv3x3(xd.data_ptr(), wd.data_ptr(), None, B, H, Wd, ci, co, y.data_ptr(), stream())
     ref = N.conv(x, w)
     assert np.abs(y.cpu().numpy() - ref).max() <= 1e-6 * (N.conv(np.abs(x), np.abs(w)).max() + 1.0)
+
+
+def test_network_backward_large_batch_matches_oracle():
+    # Large enough (level 0: 4 x 104 x 104 pixels) that the convolutions and their data
+    # gradients keep every output channel in one block, as training does.
+    B, H, Wd = 4, 416, 416
+    theta, phi, target, alpha = network_case(B, H, Wd, seed=5)
+    scale = 0.05
+    s = lbnop.Surrogate(H, Wd, max_batch=B, scale=scale)
+    s.set_params(theta)
+    pd, td = torch.from_numpy(phi.astype(np.float32)).cuda(), torch.from_numpy(target.astype(np.float32)).cuda()
+    loss = s.backward(pd, alpha, td)
+    g = s.grads_host().astype(np.float64)
+    out, saved = N.forward(theta, phi, alpha, scale, quantize=N.bf16)
+    loss_ref, dout = N.loss(out, target)
+    g_ref = N.backward(theta, saved, dout, scale)
+    assert abs(loss - loss_ref) <= 1e-4 * loss_ref
+    k, worst = 0, 0.0
+    for name, ci, co, _, _ in N.LAYERS:
+        n = 9 * co * ci + co + (co if name == "e0a" else 0)
+        worst = max(worst, rel_l2(g[k:k + n], g_ref[k:k + n]))
+        k += n
+    print(f"backward large: worst per-layer gradient rel L2 {worst:.2e}")
+    assert worst <= 2e-2
+    s.close()

@@ -171,3 +171,23 @@ def test_weighted_loss_and_gradient():
     e[1, 2, 3] = 1e-6
     fd = (N.loss(out + e, tgt, w)[0] - N.loss(out - e, tgt, w)[0]) / 2e-6
     assert abs(fd - g[1, 2, 3]) < 1e-8
+
+
+def test_global_norm_clipping():
+    # Above the threshold the clipped gradient keeps its direction and has norm max_norm;
+    # at or below it, or with max_norm 0, the gradient is unchanged. An element-wise clip or
+    # a division by the squared norm fails the norm and direction checks.
+    r = np.random.default_rng(31)
+    g = r.normal(size=1000) * np.exp(r.normal(size=1000))
+    nrm = np.sqrt(np.sum(g * g))
+    c = N.clip_global_norm(g, 0.25 * nrm)
+    assert abs(np.sqrt(np.sum(c * c)) - 0.25 * nrm) < 1e-12 * nrm
+    assert abs(np.dot(c, g) / (np.linalg.norm(c) * np.linalg.norm(g)) - 1.0) < 1e-12
+    assert np.allclose(c, 0.25 * g, rtol=1e-13, atol=0)
+    assert np.array_equal(N.clip_global_norm(g, 2.0 * nrm), g)
+    assert np.array_equal(N.clip_global_norm(g, 0.0), g)
+    # a gradient with one huge entry: every entry shrinks by the same factor
+    h = np.ones(100)
+    h[7] = 1e6
+    ch = N.clip_global_norm(h, 1.0)
+    assert abs(ch[7] / ch[0] - 1e6) < 1e-3 and abs(np.linalg.norm(ch) - 1.0) < 1e-12
