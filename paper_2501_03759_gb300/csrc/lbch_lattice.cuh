@@ -32,23 +32,46 @@ constexpr float F16_UNSCALE = 1.0f / 4096.0f;
 template <int ST>
 struct Dev;
 
+// Besides one value at a time (load, store), pairs packed in 32 bits with the first value
+// in the low half: pack2 rounds both in one conversion; raw2 widens both without the
+// storage scale, which the caller applies once to a sum (UNSCALE is a power of two, so
+// scaling a sum is exact).
 template <>
 struct Dev<ST_BF16> {
+  static constexpr float UNSCALE = 1.0f;
   __device__ __forceinline__ static float load(uint16_t b) {
     return __uint_as_float(static_cast<uint32_t>(b) << 16);  // exact widening
   }
   __device__ __forceinline__ static uint16_t store(float v) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
   }
+  __device__ __forceinline__ static uint32_t pack2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ __forceinline__ static void raw2(uint32_t u, float& lo, float& hi) {
+    lo = __uint_as_float(u << 16);
+    hi = __uint_as_float(u & 0xffff0000u);
+  }
 };
 
 template <>
 struct Dev<ST_F16> {
+  static constexpr float UNSCALE = F16_UNSCALE;
   __device__ __forceinline__ static float load(uint16_t b) {
     return __half2float(__ushort_as_half(b)) * F16_UNSCALE;
   }
   __device__ __forceinline__ static uint16_t store(float v) {
     return __half_as_ushort(__float2half_rn(v * F16_SCALE));
+  }
+  __device__ __forceinline__ static uint32_t pack2(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo * F16_SCALE, hi * F16_SCALE);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ __forceinline__ static void raw2(uint32_t u, float& lo, float& hi) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+    lo = f.x;
+    hi = f.y;
   }
 };
 

@@ -195,6 +195,66 @@ __device__ __forceinline__ void read_row(const float4* slot, int lane, float (&v
   }
 }
 
+// Pull shift along x of a per-column quantity of the strip: column j takes column j - 1
+// (c_x = 1) or column j + 1 (c_x = -1).
+__device__ __forceinline__ void from_left(float (&v)[4]) {
+  const float prev = __shfl_up_sync(FULL, v[3], 1);
+  v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
+}
+__device__ __forceinline__ void from_right(float (&v)[4]) {
+  const float next = __shfl_down_sync(FULL, v[0], 1);
+  v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
+}
+
+// Grouped deviation sums of a landed DEV row at this lane's 4 columns, pulled along x, in
+// storage units (FP16 values still carry their scale). The eight moving planes fall into
+// three groups by c_x: gp = d1 + d5 + d8 (c_x = 1), gm = d3 + d6 + d7 (c_x = -1) and
+// g0 = d2 + d4; with H also their c_y-signed parts hp = d5 - d8, hm = d6 - d7 and
+// h0 = d2 - d4. A group shares one pull shift, so it takes one shuffle instead of one per
+// plane. Every population arriving at a node is rebuilt on that node's anchor, the weights
+// w_1..w_8 sum to 5/9, and the anchor terms cancel in j_x and j_y, so
+//   phi = f*_0 + (5/9) anchor + (gp + gm + g0),  j_x = gp - gm,  j_y = hp + hm + h0.
+struct DevSums {
+  float gp[4], gm[4], g0[4], hp[4], hm[4], h0[4];
+};
+template <int ST, bool H>
+__device__ __forceinline__ void dev_sums(const float4* slot, int lane, DevSums& s) {
+  const uint2* ds = reinterpret_cast<const uint2*>(slot + 64);
+  float d[9][4];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const uint2 raw = ds[(i - 1) * 32 + lane];
+    Dev<ST>::raw2(raw.x, d[i][0], d[i][1]);
+    Dev<ST>::raw2(raw.y, d[i][2], d[i][3]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    s.gp[j] = (d[1][j] + d[5][j]) + d[8][j];
+    s.gm[j] = (d[3][j] + d[6][j]) + d[7][j];
+    s.g0[j] = d[2][j] + d[4][j];
+    if constexpr (H) {
+      s.hp[j] = d[5][j] - d[8][j];
+      s.hm[j] = d[6][j] - d[7][j];
+      s.h0[j] = d[2][j] - d[4][j];
+    }
+  }
+  from_left(s.gp);
+  from_right(s.gm);
+  if constexpr (H) {
+    from_left(s.hp);
+    from_right(s.hm);
+  }
+}
+
+// phi at column j of a landed DEV row from its rest population, anchor and group sums.
+template <int ST>
+__device__ __forceinline__ float dev_phi(const float4* slot, int lane, const DevSums& s, int j) {
+  const float4 r = slot[lane], m = slot[32 + lane];
+  const float rest = j == 0 ? r.x : (j == 1 ? r.y : (j == 2 ? r.z : r.w));
+  const float anc = j == 0 ? m.x : (j == 1 ? m.y : (j == 2 ? m.z : m.w));
+  return fmaf(5.0f / 9.0f, anc, rest) + Dev<ST>::UNSCALE * ((s.gp[j] + s.gm[j]) + s.g0[j]);
+}
+
 // Pointwise part at one node: Q (Eq. 15 reading), w, mu_alpha (Eq. 16) and the
 // local part A of mu_beta (Eq. 13 minus Eq. 16's mu_alpha).
 __device__ __forceinline__ void pointwise(const StepArgs& a, const Field& fd, float phi, float dx, float dy,
@@ -226,6 +286,31 @@ __device__ __forceinline__ void pointwise(const StepArgs& a, const Field& fd, fl
 // FAST: s_1 = s_2 = s_4 = s_6 = s_7 = s_8 = 1, so those moments take their (forced)
 // equilibrium and need not be formed; the result equals the general path's, whose
 // (1 - s_k) m_k terms are then exactly zero.
+// FAST collision from the three moments it needs, phi = m_0, j_x = m_3 and j_y = m_5 (the
+// others take their equilibrium): o[1..8] of f*; o[0] is left to the caller.
+__device__ __forceinline__ void collide_fast(const StepArgs& a, float phi, float m3, float m5, float mua, float gx,
+                                             float gy, float (&o)[9]) {
+  const float n0 = phi * (1.0f / 9.0f);
+  const float n1 = a.c1b * fmaf(2.0f, mua, -4.0f * phi);
+  const float n2 = a.c2b * fmaf(-3.0f, mua, 4.0f * phi);
+  const float n4 = a.c4g * gx, n6 = a.c6g * gy;
+  const float n3 = fmaf(a.c3a, m3, a.c3g * gx);
+  const float n5 = fmaf(a.c5a, m5, a.c5g * gy);
+  const float A0 = fmaf(-2.0f, n2, n0 - n1);
+  const float X = fmaf(-2.0f, n4, n3), Y = fmaf(-2.0f, n6, n5);
+  o[1] = A0 + X;
+  o[3] = A0 - X;
+  o[2] = A0 + Y;
+  o[4] = A0 - Y;
+  const float D0 = fmaf(2.0f, n1, n0 + n2);
+  const float U = n3 + n4, V = n5 + n6;
+  const float P = U + V, Mv = U - V;
+  o[5] = D0 + P;
+  o[7] = D0 - P;
+  o[6] = D0 - Mv;
+  o[8] = D0 + Mv;
+}
+
 template <bool FAST>
 __device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], float mua,
                                         float gx, float gy, float (&o)[9], float& phi_out) {
@@ -238,44 +323,38 @@ __device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], 
   const float p = f[5] - f[7], q = f[6] - f[8];
   const float pm = p - q, pp = p + q;
   const float m3 = x1 + pm, m5 = y1 + pp;
-  const float n0 = phi * (1.0f / 9.0f);
-  float n1, n2, n4, n6, n7, n8;
   if constexpr (FAST) {
-    n1 = a.c1b * fmaf(2.0f, mua, -4.0f * phi);
-    n2 = a.c2b * fmaf(-3.0f, mua, 4.0f * phi);
-    n4 = a.c4g * gx;
-    n6 = a.c6g * gy;
-    n7 = 0.0f;
-    n8 = 0.0f;
+    collide_fast(a, phi, m3, m5, mua, gx, gy, o);
   } else {
+    const float n0 = phi * (1.0f / 9.0f);
     const float m1 = fmaf(-4.0f, f[0], fmaf(2.0f, Sd, -Sa));
     const float m2 = fmaf(4.0f, f[0], fmaf(-2.0f, Sa, Sd));
     const float m4 = fmaf(-2.0f, x1, pm), m6 = fmaf(-2.0f, y1, pp);
     const float m7 = ab - bb, m8 = e - h;
-    n1 = fmaf(a.c1a, m1, a.c1b * fmaf(2.0f, mua, -4.0f * phi));
-    n2 = fmaf(a.c2a, m2, a.c2b * fmaf(-3.0f, mua, 4.0f * phi));
-    n4 = fmaf(a.c4a, m4, a.c4g * gx);
-    n6 = fmaf(a.c6a, m6, a.c6g * gy);
-    n7 = a.c7 * m7;
-    n8 = a.c8 * m8;
+    const float n1 = fmaf(a.c1a, m1, a.c1b * fmaf(2.0f, mua, -4.0f * phi));
+    const float n2 = fmaf(a.c2a, m2, a.c2b * fmaf(-3.0f, mua, 4.0f * phi));
+    const float n4 = fmaf(a.c4a, m4, a.c4g * gx);
+    const float n6 = fmaf(a.c6a, m6, a.c6g * gy);
+    const float n7 = a.c7 * m7;
+    const float n8 = a.c8 * m8;
+    const float n3 = fmaf(a.c3a, m3, a.c3g * gx);
+    const float n5 = fmaf(a.c5a, m5, a.c5g * gy);
+    const float A0 = fmaf(-2.0f, n2, n0 - n1);
+    const float B = A0 + n7, C = A0 - n7;
+    const float X = fmaf(-2.0f, n4, n3), Y = fmaf(-2.0f, n6, n5);
+    o[1] = B + X;
+    o[3] = B - X;
+    o[2] = C + Y;
+    o[4] = C - Y;
+    const float D0 = fmaf(2.0f, n1, n0 + n2);
+    const float E = D0 + n8, G = D0 - n8;
+    const float U = n3 + n4, V = n5 + n6;
+    const float P = U + V, Mv = U - V;
+    o[5] = E + P;
+    o[7] = E - P;
+    o[6] = G - Mv;
+    o[8] = G + Mv;
   }
-  const float n3 = fmaf(a.c3a, m3, a.c3g * gx);
-  const float n5 = fmaf(a.c5a, m5, a.c5g * gy);
-  const float A0 = fmaf(-2.0f, n2, n0 - n1);
-  const float B = A0 + n7, C = A0 - n7;
-  const float X = fmaf(-2.0f, n4, n3), Y = fmaf(-2.0f, n6, n5);
-  o[1] = B + X;
-  o[3] = B - X;
-  o[2] = C + Y;
-  o[4] = C - Y;
-  const float D0 = fmaf(2.0f, n1, n0 + n2);
-  const float E = D0 + n8, G = D0 - n8;
-  const float U = n3 + n4, V = n5 + n6;
-  const float P = U + V, Mv = U - V;
-  o[5] = E + P;
-  o[7] = E - P;
-  o[6] = G - Mv;
-  o[8] = G + Mv;
   // Row 0 of M^-1 m* would be n0 - 4 n1 + 4 n2, but FP32 n0 = phi/9 carries a fixed
   // relative bias. Since sum_i f*_i = sum_i f_i (m_0 is conserved, Eq. 34), the rest
   // population takes what the moving ones gave up: f*_0 = f_0 + sum_{i>=1} (f_i - f*_i).
@@ -308,19 +387,25 @@ __device__ __forceinline__ void store_row(const Field& fd, long long ro, long lo
     }
   } else {
     using D = Dev<ST>;
-    float rest[4];
-    uint16_t d[8][4];
+    // Columns (0, 1) and (2, 3) of each plane round in one conversion; f*_i as its reader
+    // rebuilds it (anchor term plus the stored deviation) closes the rest population.
+    float rest[4], sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    uint32_t pk[8][2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float sum = 0.0f;
+    for (int i = 1; i < 9; ++i) {
+      const float w = (float)wgt(i);
+      float dv[4], back[4];
 #pragma unroll
-      for (int i = 1; i < 9; ++i) {
-        const float w = (float)wgt(i);
-        d[i - 1][j] = D::store(o[i][j] - w * dmu[i - 1][j]);
-        sum += fmaf(w, dmu[i - 1][j], D::load(d[i - 1][j]));  // f*_i as its reader rebuilds it
-      }
-      rest[j] = phi[j] - sum;
+      for (int j = 0; j < 4; ++j) dv[j] = o[i][j] - w * dmu[i - 1][j];
+      pk[i - 1][0] = D::pack2(dv[0], dv[1]);
+      pk[i - 1][1] = D::pack2(dv[2], dv[3]);
+      D::raw2(pk[i - 1][0], back[0], back[1]);
+      D::raw2(pk[i - 1][1], back[2], back[3]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sum[j] += fmaf(w, dmu[i - 1][j], back[j] * D::UNSCALE);
     }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) rest[j] = phi[j] - sum[j];
     float* p0 = fd.dst.f32 + ro + col;
     float* pm = fd.dst.f32 + fd.ps + ro + col;
     if constexpr (VEC) {
@@ -337,12 +422,10 @@ __device__ __forceinline__ void store_row(const Field& fd, long long ro, long lo
     for (int i = 0; i < 8; ++i) {
       uint16_t* pd = fd.dst.dev + (long long)i * fd.ps + ro + col;
       if constexpr (VEC) {
-        *reinterpret_cast<uint2*>(pd) =
-            make_uint2(static_cast<uint32_t>(d[i][0]) | (static_cast<uint32_t>(d[i][1]) << 16),
-                       static_cast<uint32_t>(d[i][2]) | (static_cast<uint32_t>(d[i][3]) << 16));
+        *reinterpret_cast<uint2*>(pd) = make_uint2(pk[i][0], pk[i][1]);
       } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) pd[j] = d[i][j];
+        for (int j = 0; j < 4; ++j) pd[j] = static_cast<uint16_t>(pk[i][j >> 1] >> (16 * (j & 1)));
       }
     }
   }
@@ -387,25 +470,41 @@ __device__ __forceinline__ void collide_row(const StepArgs& a, const Field& fd, 
                                             bool store, int ocol0, int nvalid, const float (&mu_m)[4],
                                             const float (&mu_c)[4], const float (&mu_p)[4],
                                             const float (&gx)[4], const float (&gy)[4]) {
-  float fr[9][4];
-  read_row<ST, VEC, 0>(slot, lane, fr[0]);
-  read_row<ST, VEC, 1>(slot, lane, fr[1]);
-  read_row<ST, VEC, 2>(slot, lane, fr[2]);
-  read_row<ST, VEC, 3>(slot, lane, fr[3]);
-  read_row<ST, VEC, 4>(slot, lane, fr[4]);
-  read_row<ST, VEC, 5>(slot, lane, fr[5]);
-  read_row<ST, VEC, 6>(slot, lane, fr[6]);
-  read_row<ST, VEC, 7>(slot, lane, fr[7]);
-  read_row<ST, VEC, 8>(slot, lane, fr[8]);
   float o[9][4], phic[4];
+  if constexpr (VEC && FAST && ST != ST_F32) {  // phi, j_x and j_y straight from the deviations
+    DevSums ds;
+    dev_sums<ST, true>(slot, lane, ds);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    float f[9], oj[9];
+    for (int j = 0; j < 4; ++j) {
+      float oj[9];
+      phic[j] = dev_phi<ST>(slot, lane, ds, j);
+      const float m3 = Dev<ST>::UNSCALE * (ds.gp[j] - ds.gm[j]);
+      const float m5 = Dev<ST>::UNSCALE * ((ds.hp[j] + ds.hm[j]) + ds.h0[j]);
+      collide_fast(a, phic[j], m3, m5, mu_c[j], gx[j], gy[j], oj);
+      o[0][j] = 0.0f;  // the DEV store closes the rest population from phi
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = fr[i][j];
-    collide<FAST>(a, f, mu_c[j], gx[j], gy[j], oj, phic[j]);
+      for (int i = 1; i < 9; ++i) o[i][j] = oj[i];
+    }
+  } else {
+    float fr[9][4];
+    read_row<ST, VEC, 0>(slot, lane, fr[0]);
+    read_row<ST, VEC, 1>(slot, lane, fr[1]);
+    read_row<ST, VEC, 2>(slot, lane, fr[2]);
+    read_row<ST, VEC, 3>(slot, lane, fr[3]);
+    read_row<ST, VEC, 4>(slot, lane, fr[4]);
+    read_row<ST, VEC, 5>(slot, lane, fr[5]);
+    read_row<ST, VEC, 6>(slot, lane, fr[6]);
+    read_row<ST, VEC, 7>(slot, lane, fr[7]);
+    read_row<ST, VEC, 8>(slot, lane, fr[8]);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) o[i][j] = oj[i];
+    for (int j = 0; j < 4; ++j) {
+      float f[9], oj[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = fr[i][j];
+      collide<FAST>(a, f, mu_c[j], gx[j], gy[j], oj, phic[j]);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) o[i][j] = oj[i];
+    }
   }
   float dmu[8][4];
   if constexpr (ST != ST_F32) {  // anchors of the destination nodes x + c_i
@@ -498,7 +597,13 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
     // 3. Wait for row r; pull it and sum phi (Eq. 22).
     cp_async_wait<PF_DIST>();
     float ph[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    {
+    if constexpr (VEC && ST != ST_F32) {  // grouped: one shuffle per c_x group
+      const float4* slot = slots + s_cur * SLOT_F4;
+      DevSums ds;
+      dev_sums<ST, false>(slot, lane, ds);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) ph[j] = dev_phi<ST>(slot, lane, ds, j);
+    } else {
       const float4* slot = slots + s_cur * SLOT_F4;
       float v[4];
 #define LBCH_PULL(I)                    \
