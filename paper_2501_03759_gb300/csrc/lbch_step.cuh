@@ -33,16 +33,16 @@ constexpr int STRIP_W = 128;                 // columns per warp strip
 constexpr int HALO_W = 4;                    // halo columns on each side
 constexpr int OUT_W = STRIP_W - 2 * HALO_W;  // output columns per strip
 constexpr int STEP_WARPS = 4;                // warps per CTA
-// Pipeline depth per storage (measured on GB300 at 8192^2). FP32 rows are bandwidth
-// bound: fetch one row ahead and collide row r-3 right after its grad mu_beta. The
-// 16-bit storages are latency bound: collide row r-4 first thing in the iteration, so
-// that work covers the wait for row r, fetch no further ahead, and keep 12 warps per SM
-// (their landing slots are smaller).
+// Pipeline depth per storage (measured on GB300 at 8192^2): fetch one row ahead and collide
+// row r-3 right after its grad mu_beta. The 16-bit storages keep 12 warps per SM (their
+// landing slots are smaller); colliding row r-4 first in the iteration with no prefetch
+// instead ran 10% slower once their per-row instruction count had come down, and one row
+// of prefetch with r-4 needs a sixth slot, which costs a CTA per SM.
 template <int ST, bool VEC>
 struct Pipe {
   static constexpr bool DEV16 = ST != ST_F32;
-  static constexpr int PF_DIST = DEV16 ? 0 : 1;         // rows fetched ahead of the phi row
-  static constexpr int LAG = DEV16 ? 4 : 3;             // phi row r collides row r - LAG
+  static constexpr int PF_DIST = 1;                     // rows fetched ahead of the phi row
+  static constexpr int LAG = 3;                         // phi row r collides row r - LAG
   static constexpr int SLOTS = PF_DIST + 1 + LAG;       // rows held per warp: r-LAG .. r+PF_DIST
   // 16-byte units per slot: 9 per lane for FP32 planes (or pulled values on the scalar
   // path); rest + anchor + 8 half-width deviation planes = 6 per lane for vector DEV.
@@ -558,13 +558,12 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
   float Ax1[4], Ay1[4], Al1[4], Ax0[4], Ay0[4], Al0[4], php[4];
   float T1[4], T0[4];
   float Gx1[4], Gy1[4], Gx0[4], Gy0[4];
-  float mu1[4], mu2[4], mu3[4], mu4[4];  // mu_alpha of rows r-2, r-3, r-4, r-5
-  float gxc[4], gyc[4];          // grad mu_beta of row r-4 (computed one iteration earlier)
+  float mu1[4], mu2[4], mu3[4];  // mu_alpha of rows r-2, r-3, r-4
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     Ax1[j] = Ay1[j] = Al1[j] = Ax0[j] = Ay0[j] = Al0[j] = php[j] = 0.0f;
     T1[j] = T0[j] = Gx1[j] = Gy1[j] = Gx0[j] = Gy0[j] = 0.0f;
-    mu1[j] = mu2[j] = mu3[j] = mu4[j] = gxc[j] = gyc[j] = 0.0f;
+    mu1[j] = mu2[j] = mu3[j] = 0.0f;
   }
 
   // phi rows y0-3 .. ; row y collides at phi row y + COLLIDE_LAG.
@@ -587,14 +586,7 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
     // 1. Fetch row r + PF_DIST.
     if (it + PF_DIST < n_it) fetch_next(slots + s_pf * SLOT_F4);
     cp_async_commit();
-    // 2. With a lag of 4, collide row r-4 now: its inputs were all ready last iteration,
-    //    so this work overlaps the wait for row r.
-    if constexpr (COLLIDE_LAG == 4) {
-      if (it >= 3 + COLLIDE_LAG)
-        collide_row<ST, VEC, FAST>(a, fd, slots + s_col * SLOT_F4, lane, y0 + it - 3 - COLLIDE_LAG, lane_out,
-                                   ocol0, nvalid, mu4, mu3, mu2, gxc, gyc);
-    }
-    // 3. Wait for row r; pull it and sum phi (Eq. 22).
+    // 2. Wait for row r; pull it and sum phi (Eq. 22).
     cp_async_wait<PF_DIST>();
     float ph[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if constexpr (VEC && ST != ST_F32) {  // grouped: one shuffle per c_x group
@@ -613,7 +605,7 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
       LBCH_PULL(5) LBCH_PULL(6) LBCH_PULL(7) LBCH_PULL(8)
 #undef LBCH_PULL
     }
-    // 4. grad phi and lap phi of row r-1 (Eq. 26a, 26b), rolling over rows.
+    // 3. grad phi and lap phi of row r-1 (Eq. 26a, 26b), rolling over rows.
     float dx[4], dy[4], lp[4];
     {
       float s[4], d[4];
@@ -634,13 +626,13 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
         Al0[j] = t;
       }
     }
-    // 5. Pointwise at row r-1.
+    // 4. Pointwise at row r-1.
     float Qx[4], Qy[4], w[4], Aq[4], mun[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) pointwise(a, fd, php[j], dx[j], dy[j], lp[j], Qx[j], Qy[j], w[j], Aq[j], mun[j]);
 #pragma unroll
     for (int j = 0; j < 4; ++j) php[j] = ph[j];
-    // 6. mu_beta of row r-2: A - div Q + eps lap w (Eq. 26 on Q and w).
+    // 5. mu_beta of row r-2: A - div Q + eps lap w (Eq. 26 on Q and w).
     float mub[4];
     {
       float sx[4], dqx[4], sqy[4], dqy[4], sw[4], dw[4];
@@ -658,7 +650,7 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
         T0[j] = (bb - aa) + cc;
       }
     }
-    // 7. grad mu_beta of row r-3 (Eq. 26a).
+    // 6. grad mu_beta of row r-3 (Eq. 26a).
     float gx[4], gy[4];
     {
       float s[4], d[4];
@@ -675,20 +667,16 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
         Gy0[j] = -u;
       }
     }
-    // 8. With a lag of 3, collide row r-3 here.
-    if constexpr (COLLIDE_LAG == 3) {
-      if (it >= 6)
-        collide_row<ST, VEC, FAST>(a, fd, slots + s_col * SLOT_F4, lane, y0 + it - 6, lane_out, ocol0, nvalid,
-                                   mu3, mu2, mu1, gx, gy);
-    }
+    // 7. Collide row r-3.
+    static_assert(COLLIDE_LAG == 3, "row r-3 collides right after its grad mu_beta");
+    if (it >= 6)
+      collide_row<ST, VEC, FAST>(a, fd, slots + s_col * SLOT_F4, lane, y0 + it - 6, lane_out, ocol0, nvalid, mu3,
+                                 mu2, mu1, gx, gy);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      mu4[j] = mu3[j];
       mu3[j] = mu2[j];
       mu2[j] = mu1[j];
       mu1[j] = mun[j];
-      gxc[j] = gx[j];
-      gyc[j] = gy[j];
     }
     s_cur = s_cur + 1 == SLOTS ? 0 : s_cur + 1;
     s_pf = s_pf + 1 == SLOTS ? 0 : s_pf + 1;
