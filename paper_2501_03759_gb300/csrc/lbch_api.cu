@@ -189,9 +189,16 @@ void fill_step_consts(lbch_ctx* c) {
   a.c8 = (float)((1.0 - s[8]) / 4.0);
 }
 
+// f^eq of the FP64 phi0 in stage0 and its mu_alpha in stage1 into b; FP32 storage rounds
+// the two products w mu_alpha per node into scratch planes of the other population buffer.
 template <int ST>
 void launch_init(lbch_ctx* c, Buf b) {
-  init_state_kernel<ST><<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->stage0, c->stage1, b, grid_of(c));
+  float* eq_ax = c->buf[1].f32;
+  float* eq_dg = c->buf[1].f32 + c->ps;
+  init_state_kernel<ST><<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(c->stage0, c->stage1, b, grid_of(c), eq_ax,
+                                                                      eq_dg);
+  if constexpr (ST == ST_F32)
+    init_gather_kernel<<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(eq_ax, eq_dg, b, grid_of(c));
 }
 
 template <int ST>

@@ -24,19 +24,35 @@ __device__ __forceinline__ long long wrapped(const Grid& g, int x, int y) {
   return (long long)y * g.nx + x;
 }
 
-// Canonical f_i at node (x, y): f*_i of the node the population came from.
+// Canonical f_i at node (x, y): f*_i of the node the population came from (an FP32 value).
 template <int ST>
-__device__ __forceinline__ double pulled(const Buf& b, const Grid& g, int i, int x, int y) {
+__device__ __forceinline__ float pulled_f(const Buf& b, const Grid& g, int i, int x, int y) {
   const long long s = wrapped(g, x - cx(i), y - cy(i));
   if constexpr (ST == ST_F32) {
-    return (double)b.f32[(long long)i * g.ps + s];
+    return b.f32[(long long)i * g.ps + s];
   } else {
-    if (i == 0) return (double)b.f32[s];
+    if (i == 0) return b.f32[s];
     // w_i times this node's anchor plus the deviation stored at the source node.
     const long long own = (long long)y * g.nx + x;
-    return (double)fmaf((float)wgt(i), b.f32[g.ps + own], Dev<ST>::load(b.dev[(long long)(i - 1) * g.ps + s]));
+    return fmaf((float)wgt(i), b.f32[g.ps + own], Dev<ST>::load(b.dev[(long long)(i - 1) * g.ps + s]));
   }
 }
+template <int ST>
+__device__ __forceinline__ double pulled(const Buf& b, const Grid& g, int i, int x, int y) {
+  return (double)pulled_f<ST>(b, g, i, x, y);
+}
+
+// Compensated (Kahan) FP32 sum: the error stays at FP32 rounding of the total.
+struct KahanF32 {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 // mu_alpha = f(phi) - k lap phi (Eq. 16, Eq. 26b) in FP64 from an FP64 phi plane;
 // flags non-finite phi.
@@ -46,46 +62,59 @@ __global__ void widen_kernel(const float* __restrict__ in, long long n, double* 
     out[i] = (double)in[i];
 }
 
+// Rows are spread over blocks and columns over threads (no 64-bit division per node).
 __global__ void mu_alpha_kernel(const double* __restrict__ phi, double* __restrict__ mua, Grid g,
                                 double k, double beta4, int* bad) {
-  const long long n = (long long)g.nx * g.ny;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(id % g.nx), y = (int)(id / g.nx);
-    const double c = phi[id];
-    double lap = 0.0;
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      const long long id = (long long)y * g.nx + x;
+      const double c = phi[id];
+      double lap = 0.0;
 #pragma unroll
-    for (int i = 1; i < 9; ++i) lap += 2.0 * wgt(i) * (phi[wrapped(g, x + cx(i), y + cy(i))] - c);
-    lap *= 3.0;
-    mua[id] = beta4 * c * (c * c - 1.0) - k * lap;
-    if (!isfinite(c)) atomicOr(bad, 1);
-  }
+      for (int i = 1; i < 9; ++i) lap += 2.0 * wgt(i) * (phi[wrapped(g, x + cx(i), y + cy(i))] - c);
+      lap *= 3.0;
+      mua[id] = beta4 * c * (c * c - 1.0) - k * lap;
+      if (!isfinite(c)) atomicOr(bad, 1);
+    }
 }
 
-// f = f^eq(phi0, mu_alpha) (Eq. 18) written in the step kernel's pre-streaming form.
+// f = f^eq(phi0, mu_alpha) (Eq. 18) written in the step kernel's pre-streaming form, each
+// value the FP32 rounding of its FP64 definition. The node-local part: the rest population,
+// and for FP32 storage the two products every moving population takes, w mu_alpha(x) for the
+// axis (w = 1/9) and diagonal (w = 1/36) velocities, into the scratch planes eq_ax and eq_dg
+// (rounded once per node instead of once per population; init_gather_kernel places them).
 template <int ST>
 __global__ void init_state_kernel(const double* __restrict__ phi0, const double* __restrict__ mua,
-                                  Buf b, Grid g) {
-  const long long n = (long long)g.nx * g.ny;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(id % g.nx), y = (int)(id / g.nx);
-    const double m = mua[id];
-    const double rest = phi0[id] + (wgt(0) - 1.0) * m;
-    if constexpr (ST == ST_F32) {
+                                  Buf b, Grid g, float* __restrict__ eq_ax, float* __restrict__ eq_dg) {
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      const long long id = (long long)y * g.nx + x;
+      const double m = mua[id];
+      const double rest = phi0[id] + (wgt(0) - 1.0) * m;
       b.f32[id] = (float)rest;
+      if constexpr (ST == ST_F32) {
+        eq_ax[id] = (float)(wgt(1) * m);
+        eq_dg[id] = (float)(wgt(5) * m);
+      } else {
+        // A reader at y + c_i rebuilds w_i anchor(y + c_i) + d_i(y) = w_i mu_alpha(y + c_i),
+        // exactly f^eq_i there, with every deviation zero.
+        b.f32[g.ps + id] = (float)m;
 #pragma unroll
-      for (int i = 1; i < 9; ++i)  // f*_i(y) must stream to f_i(y + c_i) = w_i mu_alpha(y + c_i)
-        b.f32[(long long)i * g.ps + id] = (float)(wgt(i) * mua[wrapped(g, x + cx(i), y + cy(i))]);
-    } else {
-      // A reader at y + c_i rebuilds w_i anchor(y + c_i) + d_i(y) = w_i mu_alpha(y + c_i),
-      // exactly f^eq_i there, with every deviation zero.
-      b.f32[id] = (float)rest;
-      b.f32[g.ps + id] = (float)m;
-#pragma unroll
-      for (int i = 1; i < 9; ++i) b.dev[(long long)(i - 1) * g.ps + id] = Dev<ST>::store(0.0f);
+        for (int i = 1; i < 9; ++i) b.dev[(long long)(i - 1) * g.ps + id] = Dev<ST>::store(0.0f);
+      }
     }
-  }
+}
+
+// FP32 storage: f*_i(y) must stream to f_i(y + c_i) = w_i mu_alpha(y + c_i), the product
+// init_state_kernel rounded at y + c_i.
+__global__ void init_gather_kernel(const float* __restrict__ eq_ax, const float* __restrict__ eq_dg, Buf b, Grid g) {
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x)
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      const long long id = (long long)y * g.nx + x;
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        b.f32[(long long)i * g.ps + id] = (i <= 4 ? eq_ax : eq_dg)[wrapped(g, x + cx(i), y + cy(i))];
+    }
 }
 
 // One canonical plane f_i(x, t) in FP64.
@@ -187,31 +216,19 @@ __global__ void phi_kernel(Buf b, Grid g, double* __restrict__ phi_d, float* __r
   for (int y = blockIdx.x; y < g.ny; y += gridDim.x)
     for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
       const long long id = (long long)y * g.nx + x;
-      if (phi_d) {
-        double p = 0.0;
+      if (phi_d) {  // compensated FP32 sum (FP64 adds run at a small fraction of the FP32 rate)
+        KahanF32 p;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) p += pulled<ST>(b, g, i, x, y);
-        phi_d[id] = p;
+        for (int i = 0; i < 9; ++i) p.add(pulled_f<ST>(b, g, i, x, y));
+        phi_d[id] = p.value();
       } else {
         float p = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) p += (float)pulled<ST>(b, g, i, x, y);
+        for (int i = 0; i < 9; ++i) p += pulled_f<ST>(b, g, i, x, y);
         phi_f[id] = p;
       }
     }
 }
-
-// Compensated (Kahan) FP32 sum: the error stays at FP32 rounding of the total.
-struct KahanF32 {
-  float s = 0.0f, c = 0.0f;
-  __device__ __forceinline__ void add(float v) {
-    const float y = v - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
 
 // Total mass sum_x phi(x). Streaming only permutes populations, so this is the sum of
 // every stored population, no pull needed: 9 FP32 planes, or for 16-bit deviations
