@@ -236,15 +236,16 @@ def run_e2e(lbch, torch, phi0, n, steps, warmup):
             "wall_s": dt}
 
 
-def run_batch_sweep(lbch, torch, steps: int, count: int = 512, seed: int = 0):
+def run_batch_sweep(lbch, torch, steps: int, count: int = 512, seed: int = 0, storage: str = "f32"):
     """The parameter-sweep workload: count fields (edges from {64, 128, 256, 512}, alpha in
-    [0, 0.5], droplets and spinodal fields) stepped together, FP32 storage."""
+    [0, 0.5], droplets and spinodal fields) stepped together in the given storage."""
     import workloads
 
     specs = workloads.batch_sweep_specs(count, seed)
     n = [sp["n"] for sp in specs]
     sites = sum(v * v for v in n)
-    b = lbch.Batch(lbch.make_params(8, 8), n, n, [sp["alpha"] for sp in specs])
+    codes = {"f32": lbch.STORE_F32, "bf16_dev": lbch.STORE_BF16_DEV, "f16_dev": lbch.STORE_F16_DEV}
+    b = lbch.Batch(lbch.make_params(8, 8, storage=codes[storage]), n, n, [sp["alpha"] for sp in specs])
     for i, sp in enumerate(specs):
         b.init_field(i, workloads.batch_field(sp))
     b.step(64)  # warm-up (one graph replay)
@@ -257,7 +258,7 @@ def run_batch_sweep(lbch, torch, steps: int, count: int = 512, seed: int = 0):
     sec = e0.elapsed_time(e1) / 1e3
     out = {"value": steps * sites / sec / 1e6, "unit": "MLUPS", "fields": count, "nodes": sites,
            "steps": steps, "ms_per_step": sec / steps * 1e3, "rows_per_warp": b.rows_target,
-           "storage": "f32", "launch": "one kernel per step for all fields, CUDA graphs of 64 steps"}
+           "storage": storage, "launch": "one kernel per step for all fields, CUDA graphs of 64 steps"}
     b.close()
     return out
 
@@ -441,6 +442,11 @@ def main():
         peak_bw = measured_peaks()[0]
         batch["roofline_frac"] = 72 * batch["value"] * 1e6 / (peak_bw * 1e9)
         batch["value"] = job_rate(world, batch["value"], 1.0)  # replicas: rates add
+        if not args.no_variants:
+            bv = run_batch_sweep(lbch, torch, args.batch_steps, storage="bf16_dev")
+            bv["roofline_frac"] = 48 * bv["value"] * 1e6 / (peak_bw * 1e9)
+            bv["value"] = job_rate(world, bv["value"], 1.0)
+            batch["variants"] = {"bf16_dev": bv}
 
     d3 = None
     if not args.no_3d:
