@@ -3,9 +3,9 @@
  *
  * A periodic convolutional U-Net maps phi(t) on an H x W field to phi(t + K), K lattice
  * steps later (the surrogate is not part of arXiv 2501.03759; the scheme of its Section 3
- * generates its training data and judges it). The library holds the network, runs it
- * forward, trains it (mean squared error, Adam), and alternates leaps with steps of an
- * lbch context.
+ * generates its training data and is the reference it is checked against). The library
+ * holds the network, runs it forward, trains it (mean squared error, Adam), and alternates
+ * leaps with steps of an lbch context.
  *
  * Network (the flat parameter layout below follows this table, in this order):
  *   sig = root mean square of phi (1 for a zero field)

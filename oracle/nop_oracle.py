@@ -8,8 +8,8 @@ it; the two meet only through the flat parameter vector and the array layouts
 stated below, which each side implements on its own.
 
 The surrogate is not part of arXiv 2501.03759: it leaps K steps of the scheme of
-Section 3 (Eqs. 17-26), and the scheme itself judges it. Every operation here is
-written out from its textbook definition:
+Section 3 (Eqs. 17-26), and the scheme itself is what it is checked against. Every
+operation here is written out from its textbook definition:
   - 3x3 cross-correlation on a periodic grid, y(p) = sum_d W_d x(p + d) + b,
     and its two adjoints (data and weight gradients);
   - SiLU, z sigmoid(z) (Elfwing, Uchibe, Doya 2018);

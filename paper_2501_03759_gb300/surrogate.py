@@ -1,5 +1,5 @@
 """The learned leap's workflow: generate LBM trajectories, train the network, and run
-and judge the leap/LBM alternation against the plain LBM.
+and check the leap/LBM alternation against the plain LBM.
 
   python -m paper_2501_03759_gb300.surrogate train --out DIR   # data + training, writes DIR/leap_theta.npy
   python -m paper_2501_03759_gb300.surrogate eval --theta FILE  # gates against a held-out plain run
@@ -10,7 +10,7 @@ Eq. 6 spread over [0, 0.5]; the other parameters of Eq. 39), stepped together by
 batched lbch path; phi is copied on the device every `every` steps. A training pair is
 (phi(t), phi(t + leap)) for any stored t.
 
-Judge: from a held-out initial field, the plain LBM runs T = warmup + cycles (leap + corr)
+Evaluation: from a held-out initial field, the plain LBM runs T = warmup + cycles (leap + corr)
 steps; the surrogate run takes the same warmup LBM steps (the white noise of phi0 decays),
 then alternates one leap (K = leap steps) with corr LBM steps, cycles times.
 Reported: relative L2 error of phi at T, relative free-energy difference, mass drift, and
