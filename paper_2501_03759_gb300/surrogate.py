@@ -90,11 +90,25 @@ def generate(runs, n: int = 512, t_end: int = T_END, every: int = EVERY):
     return data
 
 
+def d4(t, k: int, flip: bool):
+    """One element of the square's symmetry group on a batch of periodic fields [B][n][n]: a
+    rotation by k quarter turns, then a reflection x -> -x if flip."""
+    import torch
+
+    t = torch.rot90(t, k, dims=(1, 2)) if k else t
+    return (torch.flip(t, dims=(2,)) if flip else t).contiguous()
+
+
 def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: float = 1e-5, seed: int = 0,
-          theta0=None, log_every: int = 200, clip: float = CLIP):
+          theta0=None, log_every: int = 200, clip: float = CLIP, augment: bool = True):
     """Adam on the leap error over random (run, t) pairs, each pair weighted by the inverse of
     its own mean squared change (so that the identity map scores 1 on every pair and small
     late-time changes count as much as the early decay of the noise); cosine learning rate.
+
+    With augment, each batch is turned by a random element of the square's symmetry group
+    (rotations by quarter turns, reflections). The scheme commutes with all eight: the
+    D2Q9 velocities and weights, gamma(n) of Eq. 6 and the relaxation rates (s_3 = s_5) are
+    invariant under them, so a turned pair is another exact pair of the same dynamics.
 
     With clip > 0, each step's gradient is clipped to `clip` times the median global norm
     of the last CLIP_WINDOW steps (from step CLIP_START on): a rare batch whose gradient is
@@ -121,13 +135,17 @@ def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: f
         ri_t, ki_t = torch.from_numpy(ri).cuda(), torch.from_numpy(ki).cuda()
         torch.index_select(data.view(count * snaps, n, n), 0, ri_t * snaps + ki_t, out=x)
         torch.index_select(data.view(count * snaps, n, n), 0, ri_t * snaps + ki_t + gap, out=y)
+        xs, ys = x, y
+        if augment:
+            k, flip = int(r.integers(0, 4)), bool(r.integers(0, 2))
+            xs, ys = d4(x, k, flip), d4(y, k, flip)
         rate = lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * it / max(1, iters - 1)))
         want = (it % log_every == 0) or it == iters - 1
-        change = ((y - x) ** 2).mean(dim=(1, 2)).double().cpu().numpy()
+        change = ((ys - xs) ** 2).mean(dim=(1, 2)).double().cpu().numpy()
         weight = 1.0 / np.maximum(change, 1e-30)
         limit = clip * float(np.median(norms[-CLIP_WINDOW:])) if clip > 0 and len(norms) >= CLIP_START else 0.0
         s.set_clip(limit)
-        loss = s.train_step(x, alphas[ri], y, rate, want_loss=want, weight=weight)
+        loss = s.train_step(xs, alphas[ri], ys, rate, want_loss=want, weight=weight)
         norms.append(s.grad_norm())
         clipped += int(0.0 < limit < norms[-1])
         if want:
@@ -227,12 +245,13 @@ def main(argv=None):
     sub = ap.add_subparsers(dest="cmd", required=True)
     t = sub.add_parser("train")
     t.add_argument("--out", required=True)
-    t.add_argument("--runs", type=int, default=16)
+    t.add_argument("--runs", type=int, default=32)
     t.add_argument("--n", type=int, default=512)
-    t.add_argument("--iters", type=int, default=3000)
-    t.add_argument("--batch", type=int, default=16)
+    t.add_argument("--iters", type=int, default=24000)
+    t.add_argument("--batch", type=int, default=32)
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--clip", type=float, default=CLIP, help="clip factor over the median recent norm; 0: off")
+    t.add_argument("--no-augment", action="store_true", help="train without the symmetry-group turns")
     e = sub.add_parser("eval")
     e.add_argument("--theta", required=True)
     e.add_argument("--alpha", type=float, nargs="+", default=[0.3])
@@ -248,11 +267,12 @@ def main(argv=None):
         t0 = time.perf_counter()
         data = generate(runs, args.n)
         t_gen = time.perf_counter() - t0
-        theta, log = train(data, [a for a, _ in runs], args.iters, args.batch, args.lr, clip=args.clip)
+        theta, log = train(data, [a for a, _ in runs], args.iters, args.batch, args.lr, clip=args.clip,
+                           augment=not args.no_augment)
         t_train = time.perf_counter() - t0 - t_gen
         np.save(os.path.join(args.out, "leap_theta.npy"), theta.astype(np.float32))
         report = {"runs": runs, "n": args.n, "iters": args.iters, "batch": args.batch, "lr": args.lr,
-                  "clip": args.clip,
+                  "clip": args.clip, "augment": not args.no_augment,
                   "leap": LEAP, "every": EVERY, "scale": SCALE, "t_end": T_END,
                   "seconds_generate": t_gen, "seconds_train": t_train, "log": log}
         with open(os.path.join(args.out, "train_report.json"), "w") as fh:

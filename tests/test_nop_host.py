@@ -1,5 +1,6 @@
 """Host-side checks of the learned leap's C-ABI (no GPU): parameter count, workspace
-sizing and parameter validation."""
+sizing and parameter validation, and the symmetry turns of the training data."""
+import numpy as np
 import pytest
 
 from oracle import nop_oracle as N
@@ -23,3 +24,22 @@ def test_workspace_grows_with_batch_and_size():
     assert 0 < a < b < c
     # parameters, Adam state and gradients alone: 4 FP32 copies
     assert a > 4 * 4 * N.param_count()
+
+
+def test_d4_turns_form_the_square_group():
+    # The eight training turns are distinct, are numpy's rot90 / flip, and compose as the group.
+    import torch
+    from paper_2501_03759_gb300.surrogate import d4
+
+    x = torch.arange(2 * 6 * 6, dtype=torch.float32).reshape(2, 6, 6)
+    seen = set()
+    for k in range(4):
+        for flip in (False, True):
+            y = d4(x, k, flip)
+            ref = np.rot90(x.numpy(), k, axes=(1, 2))
+            ref = ref[:, :, ::-1] if flip else ref
+            assert np.array_equal(y.numpy(), ref) and y.is_contiguous()
+            seen.add(y.numpy().tobytes())
+    assert len(seen) == 8
+    assert torch.equal(d4(d4(x, 1, False), 3, False), x)
+    assert torch.equal(d4(d4(x, 0, True), 0, True), x)
