@@ -100,7 +100,7 @@ def d4(t, k: int, flip: bool):
 
 
 def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: float = 1e-5, seed: int = 0,
-          theta0=None, log_every: int = 200, clip: float = CLIP, augment: bool = True):
+          theta0=None, log_every: int = 200, clip: float = CLIP, augment: bool = True, alpha_weight: float = 0.0):
     """Adam on the leap error over random (run, t) pairs, each pair weighted by the inverse of
     its own mean squared change (so that the identity map scores 1 on every pair and small
     late-time changes count as much as the early decay of the noise); cosine learning rate.
@@ -109,6 +109,9 @@ def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: f
     (rotations by quarter turns, reflections). The scheme commutes with all eight: the
     D2Q9 velocities and weights, gamma(n) of Eq. 6 and the relaxation rates (s_3 = s_5) are
     invariant under them, so a turned pair is another exact pair of the same dynamics.
+
+    With alpha_weight > 0, run i is drawn with probability proportional to
+    1 + alpha_weight alpha_i (uniform otherwise).
 
     With clip > 0, each step's gradient is clipped to `clip` times the median global norm
     of the last CLIP_WINDOW steps (from step CLIP_START on): a rare batch whose gradient is
@@ -129,8 +132,12 @@ def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: f
     norms = []
     clipped = 0
     t0 = time.perf_counter()
+    p_run = None
+    if alpha_weight > 0:
+        p_run = 1.0 + alpha_weight * alphas
+        p_run = p_run / p_run.sum()
     for it in range(iters):
-        ri = r.integers(0, count, batch)
+        ri = r.integers(0, count, batch) if p_run is None else r.choice(count, size=batch, p=p_run)
         ki = r.integers(WARMUP // EVERY, snaps - gap, batch)
         ri_t, ki_t = torch.from_numpy(ri).cuda(), torch.from_numpy(ki).cuda()
         torch.index_select(data.view(count * snaps, n, n), 0, ri_t * snaps + ki_t, out=x)
@@ -247,11 +254,12 @@ def main(argv=None):
     t.add_argument("--out", required=True)
     t.add_argument("--runs", type=int, default=32)
     t.add_argument("--n", type=int, default=512)
-    t.add_argument("--iters", type=int, default=24000)
+    t.add_argument("--iters", type=int, default=48000)
     t.add_argument("--batch", type=int, default=32)
     t.add_argument("--lr", type=float, default=1e-3)
     t.add_argument("--clip", type=float, default=CLIP, help="clip factor over the median recent norm; 0: off")
     t.add_argument("--no-augment", action="store_true", help="train without the symmetry-group turns")
+    t.add_argument("--alpha-weight", type=float, default=0.0, help="draw run i with weight 1 + this * alpha_i")
     e = sub.add_parser("eval")
     e.add_argument("--theta", required=True)
     e.add_argument("--alpha", type=float, nargs="+", default=[0.3])
@@ -268,11 +276,11 @@ def main(argv=None):
         data = generate(runs, args.n)
         t_gen = time.perf_counter() - t0
         theta, log = train(data, [a for a, _ in runs], args.iters, args.batch, args.lr, clip=args.clip,
-                           augment=not args.no_augment)
+                           augment=not args.no_augment, alpha_weight=args.alpha_weight)
         t_train = time.perf_counter() - t0 - t_gen
         np.save(os.path.join(args.out, "leap_theta.npy"), theta.astype(np.float32))
         report = {"runs": runs, "n": args.n, "iters": args.iters, "batch": args.batch, "lr": args.lr,
-                  "clip": args.clip, "augment": not args.no_augment,
+                  "clip": args.clip, "augment": not args.no_augment, "alpha_weight": args.alpha_weight,
                   "leap": LEAP, "every": EVERY, "scale": SCALE, "t_end": T_END,
                   "seconds_generate": t_gen, "seconds_train": t_train, "log": log}
         with open(os.path.join(args.out, "train_report.json"), "w") as fh:
