@@ -117,8 +117,12 @@ lbch_status lbch_init_field_device(lbch_ctx* ctx, const float* d_phi0);
  * Asynchronous. */
 lbch_status lbch_get_phi_device(lbch_ctx* ctx, float* d_phi);
 
-/* Advances the state n >= 0 time steps of Eq. 17. Asynchronous: enqueues n kernel
- * launches on the stream and returns. LBCH_EINVAL before any init/set_state. */
+/* Advances the state n >= 0 time steps of Eq. 17. Asynchronous: enqueues the n step
+ * kernels on the stream and returns. From the first call with n >= 16 on, runs of 16 steps
+ * are replayed from a CUDA graph that the context captures once on a private stream and
+ * keeps (with its driver resources) until lbch_destroy; the results are those of
+ * single launches, bit for bit. While the caller is capturing the stream itself, the
+ * kernels are launched one by one. LBCH_EINVAL before any init/set_state. */
 lbch_status lbch_step(lbch_ctx* ctx, int64_t n);
 
 /* Total mass sum_x phi(x) (Eq. 22), accumulated in FP64 on the GPU. Synchronises. */

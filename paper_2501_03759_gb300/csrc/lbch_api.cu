@@ -45,6 +45,8 @@ struct lbch_ctx {
   bool fast;  // s_1 = s_2 = s_4 = s_6 = s_7 = s_8 = 1: reduced collision
   int step_blocks;
   int aux_blocks;
+  cudaGraphExec_t graph;  // GRAPH_STEPS step launches from buffer 0, captured at first use
+  bool graph_off;         // capture failed once, or the caller's stream is being captured
   bool failed;
   char err[512];
 };
@@ -123,19 +125,19 @@ const void* step_entry(bool vec, bool fast) {
 }
 
 template <int ST>
-void launch_step(lbch_ctx* c, const Field& f) {
+void launch_step(lbch_ctx* c, const Field& f, cudaStream_t s) {
   const dim3 g(c->step_blocks), b(STEP_WARPS * 32);
   const StepArgs& a = c->sa;
   if (c->vec) {
     if (c->fast)
-      step_kernel<ST, true, true><<<g, b, step_smem<ST, true>(), c->stream>>>(a, f, c->n_warps);
+      step_kernel<ST, true, true><<<g, b, step_smem<ST, true>(), s>>>(a, f, c->n_warps);
     else
-      step_kernel<ST, true, false><<<g, b, step_smem<ST, true>(), c->stream>>>(a, f, c->n_warps);
+      step_kernel<ST, true, false><<<g, b, step_smem<ST, true>(), s>>>(a, f, c->n_warps);
   } else {
     if (c->fast)
-      step_kernel<ST, false, true><<<g, b, step_smem<ST, false>(), c->stream>>>(a, f, c->n_warps);
+      step_kernel<ST, false, true><<<g, b, step_smem<ST, false>(), s>>>(a, f, c->n_warps);
     else
-      step_kernel<ST, false, false><<<g, b, step_smem<ST, false>(), c->stream>>>(a, f, c->n_warps);
+      step_kernel<ST, false, false><<<g, b, step_smem<ST, false>(), s>>>(a, f, c->n_warps);
   }
 }
 
@@ -239,6 +241,48 @@ void launch_set_dev(lbch_ctx* c, int i) {
 lbch_status finish(lbch_ctx* c, const char* what) {
   if (cuda_failed(c, cudaGetLastError(), what)) return LBCH_ECUDA;
   return LBCH_OK;
+}
+
+// One time step from buffer `cur` on stream s.
+void launch_one_step(lbch_ctx* c, int cur, cudaStream_t s) {
+  Field f = c->fld;
+  f.src = c->buf[cur];
+  f.dst = c->buf[cur ^ 1];
+  DISPATCH(c->p.storage, launch_step, c, f, s);
+}
+
+// Steps are replayed from a CUDA graph of GRAPH_STEPS launches (an even number, so the
+// buffer parity returns): on small fields a step takes a few microseconds, comparable to
+// the launch overhead the graph removes. The graph is captured on a private stream at the
+// first call that can use it; a failed capture falls back to direct launches for good.
+constexpr int GRAPH_STEPS = 16;
+
+bool ensure_graph(lbch_ctx* c) {
+  if (c->graph) return true;
+  if (c->graph_off) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;  // the caller is capturing this stream: plain launches join its graph
+  }
+  cudaStream_t cap = nullptr;
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok) ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    for (int k = 0; k < GRAPH_STEPS; ++k) launch_one_step(c, k & 1, cap);
+    ok = cudaStreamEndCapture(cap, &g) == cudaSuccess;
+  }
+  if (ok) ok = cudaGraphInstantiate(&c->graph, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (cap) cudaStreamDestroy(cap);
+  if (!ok) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_off = true;
+    cudaGetLastError();  // a failed capture is not an error of the context
+  }
+  return ok;
 }
 
 lbch_status sync_flag(lbch_ctx* c, int* host_flag, const char* what) {
@@ -427,11 +471,18 @@ lbch_status lbch_step(lbch_ctx* c, int64_t n) {
     set_err(c, "step: n must be >= 0");
     return LBCH_EINVAL;
   }
-  for (int64_t t = 0; t < n; ++t) {
-    Field f = c->fld;
-    f.src = c->buf[c->cur];
-    f.dst = c->buf[c->cur ^ 1];
-    DISPATCH(c->p.storage, launch_step, c, f);
+  int64_t left = n;
+  if (left >= GRAPH_STEPS + (c->cur ? 1 : 0) && ensure_graph(c)) {
+    if (c->cur == 1) {  // back to parity 0, where the graph starts
+      launch_one_step(c, 1, c->stream);
+      c->cur = 0;
+      --left;
+    }
+    for (; left >= GRAPH_STEPS; left -= GRAPH_STEPS)
+      if (cuda_failed(c, cudaGraphLaunch(c->graph, c->stream), "step: graph launch")) return LBCH_ECUDA;
+  }
+  for (; left > 0; --left) {
+    launch_one_step(c, c->cur, c->stream);
     c->cur ^= 1;
   }
   c->steps += n;
@@ -664,7 +715,10 @@ lbch_status lbch_free_energy_static(const lbch_params* p, const float* d_f9, int
 
 const char* lbch_last_error(const lbch_ctx* c) { return c ? c->err : "context is NULL"; }
 
-void lbch_destroy(lbch_ctx* c) { delete c; }
+void lbch_destroy(lbch_ctx* c) {
+  if (c && c->graph) cudaGraphExecDestroy(c->graph);
+  delete c;
+}
 
 }  // extern "C"
 
