@@ -692,15 +692,22 @@ __global__ void head_bwd_kernel(const float* __restrict__ phi_out, const float* 
   }
 }
 
-// *norm = sqrt(sum_k grad[k]^2), the global L2 norm of the gradient (one block, fixed order).
-__global__ void grad_norm_kernel(const float* __restrict__ grad, long long n, double* __restrict__ norm) {
+// The global L2 norm of the gradient, in FP64 and a fixed order: grad_sq_kernel (grid of
+// HEAD_BLOCKS) leaves one partial sum of grad^2 per block (FP64 runs at a small fraction of
+// the FP32 rate, so the sum is spread over the SMs), then grad_norm_kernel (one warp) adds the
+// partials and takes the square root.
+__global__ void grad_sq_kernel(const float* __restrict__ grad, long long n, double* __restrict__ partial) {
   __shared__ double sh[32];
   double s = 0.0;
-  for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const double g = grad[k];
     s = fma(g, g, s);
   }
   s = block_sum_d(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+__global__ void grad_norm_kernel(const double* __restrict__ partial, double* __restrict__ norm) {
+  const double s = warp_partials(partial, threadIdx.x);
   if (threadIdx.x == 0) *norm = sqrt(s);
 }
 
@@ -1263,7 +1270,8 @@ void backward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, const 
   layer_bwd(c, E0B, d, c->a[E0A], c->g0a, alpha);
   make_dz(c, d, 0, kL[E0A].co, c->g0a, nullptr, c->z[E0A]);
   layer_bwd(c, E0A, d, c->x0, nullptr, alpha);
-  grad_norm_kernel<<<1, 1024, 0, s>>>(c->grad, c->n_params, c->gnorm);
+  grad_sq_kernel<<<HEAD_BLOCKS, 256, 0, s>>>(c->grad, c->n_params, c->partial);
+  grad_norm_kernel<<<1, 32, 0, s>>>(c->partial, c->gnorm);
   c->last_batch = batch;
 }
 
