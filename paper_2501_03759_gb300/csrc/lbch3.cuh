@@ -389,18 +389,25 @@ __device__ __forceinline__ float back(const float (&n)[15]) {
   }
 }
 
-template <int K>
+// FAST: s_k = 1 for every moment but phi (k = 0) and j (k = 3, 5, 7), so those others take
+// m* = m^eq + F_m / 2 and need not be formed from f.
+template <int K, bool FAST>
 __device__ __forceinline__ void relax(const float (&f)[15], float phi, float m_a, float gx, float gy, float gz,
                                       const Consts3& c, float (&nk)[15]) {
-  const float m = moment<K>(f);
   // m^eq = (phi, -2 phi + mu_a, 16 phi - 15 mu_a, 0, ...) (Eq. 18 in the Eq. 24 basis);
   // F_m = M F is nonzero on j (-g/3) and q (7 g/9) only (Eq. 19).
   const float meq = K == 0 ? phi : (K == 1 ? fmaf(-2.0f, phi, m_a) : (K == 2 ? fmaf(16.0f, phi, -15.0f * m_a) : 0.0f));
   const float gk = (K == 3 || K == 4) ? gx : ((K == 5 || K == 6) ? gy : gz);
   const float Fm = (K == 3 || K == 5 || K == 7) ? -gk * (1.0f / 3.0f) : ((K == 4 || K == 6 || K == 8) ? gk * (7.0f / 9.0f) : 0.0f);
-  const float ms = fmaf(-c.s[K], m - meq, m) + (1.0f - 0.5f * c.s[K]) * Fm;  // Eq. 17 in moments
+  float ms;
+  if constexpr (FAST && K != 0 && K != 3 && K != 5 && K != 7) {
+    ms = fmaf(0.5f, Fm, meq);
+  } else {
+    const float m = moment<K>(f);
+    ms = fmaf(-c.s[K], m - meq, m) + (1.0f - 0.5f * c.s[K]) * Fm;  // Eq. 17 in moments
+  }
   nk[K] = ms * (1.0f / (float)MN<K>::v);
-  if constexpr (K + 1 < 15) relax<K + 1>(f, phi, m_a, gx, gy, gz, c, nk);
+  if constexpr (K + 1 < 15) relax<K + 1, FAST>(f, phi, m_a, gx, gy, gz, c, nk);
 }
 
 template <int I>
@@ -409,6 +416,7 @@ __device__ __forceinline__ void unproject(const float (&nk)[15], float (&o)[15])
   if constexpr (I + 1 < 15) unproject<I + 1>(nk, o);
 }
 
+template <bool FAST>
 __global__ void __launch_bounds__(NX3) collide3_kernel(const float* __restrict__ src, const float* __restrict__ mub,
                                                        const float* __restrict__ mua, Grid3 g, Consts3 c,
                                                        float* __restrict__ dst) {
@@ -423,7 +431,7 @@ __global__ void __launch_bounds__(NX3) collide3_kernel(const float* __restrict__
 #pragma unroll
   for (int i = 0; i < 15; ++i) phi += f[i];
   float nk[15], o[15];
-  relax<0>(f, phi, mua[s.id], gx, gy, gz, c, nk);
+  relax<0, FAST>(f, phi, mua[s.id], gx, gy, gz, c, nk);
   unproject<0>(nk, o);
   // Rest population closes the mass exactly (sum_i f* = sum_i f, Eq. 34).
   float d = 0.0f;
@@ -526,6 +534,7 @@ struct lbch3_ctx {
   int red_blocks;  // blocks for the reductions
   lbch3::MuTiles mt;
   int mu_blocks;   // blocks of mu3_kernel
+  bool fast;       // s_k = 1 except for phi and j: the reduced collision
   bool has_state, failed;
   char err[512];
 };
@@ -632,6 +641,9 @@ lbch_status lbch3_create(const lbch3_params* p, void* d_workspace, size_t bytes,
   k.cfp = p->regularization == LBCH_REG_WILLMORE ? (float)eps : 0.0f;
   k.cnk = (float)(nested ? c->k : 0.0);
   for (int i = 0; i < 15; ++i) k.s[i] = (float)c->s[i];
+  c->fast = true;
+  for (int i = 1; i < 15; ++i)
+    if (i != 3 && i != 5 && i != 7 && c->s[i] != 1.0) c->fast = false;
   c->blocks = segs * p->ny * p->nz;  // < 2^31: segs * nx-rows <= (nx + 127) / 128 * ny * nz
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -699,7 +711,10 @@ lbch_status lbch3_step(lbch3_ctx* c, int64_t n) {
     float* dst = c->buf[c->cur ^ 1];
     lbch3::phi3_kernel<<<c->blocks, lbch3::NX3, 0, c->stream>>>(src, c->g, c->phi);
     lbch3::mu3_kernel<<<c->mu_blocks, lbch3::MU_THREADS, 0, c->stream>>>(c->phi, c->g, c->cs, c->mt, c->mua, c->mub);
-    lbch3::collide3_kernel<<<c->blocks, lbch3::NX3, 0, c->stream>>>(src, c->mub, c->mua, c->g, c->cs, dst);
+    if (c->fast)
+      lbch3::collide3_kernel<true><<<c->blocks, lbch3::NX3, 0, c->stream>>>(src, c->mub, c->mua, c->g, c->cs, dst);
+    else
+      lbch3::collide3_kernel<false><<<c->blocks, lbch3::NX3, 0, c->stream>>>(src, c->mub, c->mua, c->g, c->cs, dst);
     c->cur ^= 1;
   }
   if (cuda3_failed(c, cudaGetLastError(), "step: launch")) return LBCH_ECUDA;
