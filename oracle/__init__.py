@@ -126,7 +126,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # LBCH_ORACLE_LIB names a prebuilt copy instead (the mutation tests load
+            # oracles with a planted mistake this way, each in its own process).
+            lib = ctypes.CDLL(os.environ.get("LBCH_ORACLE_LIB") or build())
             dp = ctypes.POINTER(ctypes.c_double)
             pp = ctypes.POINTER(_Params)
             lib.orc_derive.argtypes = [pp, ctypes.POINTER(_Derived)]

@@ -18,12 +18,20 @@
  *   orc_collide_site   single-relaxation reduction (all s_i equal).
  *   orc_step           mass conservation (Eq. 34), energy decay, isotropic tanh
  *                      profile (Eq. 40 with Eq. 5), continuum linear dispersion
- *                      (Eqs. 10, 13, 15, 16, 38), lattice rotation/mirror
- *                      equivariance, constant-field fixed point.
- *   orc_energy         Eq. 7 with Eq. 9 on fields with closed-form sums.
+ *                      (Eqs. 10, 13, 15, 16, 38) on the axes, the diagonals and a
+ *                      generic angle (gamma of Eq. 6 between its extremes), with
+ *                      Willmore (Eq. 13) and linear (Eq. 12) regularisation, lattice
+ *                      rotation/mirror equivariance, constant-field fixed point.
+ *   orc_fields         mu_beta on a circular interface converges at second order to
+ *                      the continuum value of Eqs. 2, 6, 15, 16 (the tangential term
+ *                      with and without k: readings C1 and ORC_Q_LITERAL); the
+ *                      ORC_MU_NESTED difference equals k (lap - div grad) phi from
+ *                      Fourier symbols of Eq. 26; the n = 0 guard fires only in bulk.
+ *   orc_energy         Eq. 7 with Eq. 9 or Eq. 8 on fields with closed-form sums.
+ * Each of these pins fails under planted mistakes in its branch (a mutation test
+ * builds altered copies of this oracle and runs the pins against them).
  * Parity unpinned: the absolute shapes and energy curves of the paper's figures
- * (their values are not printed), and the k factor of the second term of Eq. 15
- * off the lattice axes (only equivariance and energy decay constrain it).
+ * (their values are not printed).
  */
 #ifndef LBCH_ORACLE_H
 #define LBCH_ORACLE_H

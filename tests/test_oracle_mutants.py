@@ -1,0 +1,115 @@
+"""Planted mistakes in the FP64 oracle: each must make its pin fail.
+
+A pin that passes whatever the oracle computes pins nothing. Each case below copies
+oracle/lbch_oracle.cpp with one plausible mistake in one branch (a wrong factor, a
+flipped sign, a dropped term, a wrong reading), builds that copy with g++, and runs
+the named pins of tests/test_oracle_pins.py against it in a separate process
+(LBCH_ORACLE_LIB points the oracle package at the copy). The case passes only if
+those pins FAIL on the planted mistake; the unmodified oracle passes them in
+test_oracle_pins.py itself.
+
+Everything here runs on the CPU; no mistake is ever planted in the CUDA library.
+"""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "lbch_oracle.cpp")
+PINS = "tests/test_oracle_pins.py"
+
+# (name, original text, planted text, pins expected to fail). Each original text must occur
+# exactly once in the 2D part of the oracle source.
+MUTANTS = [
+    # Linear regularisation, Eq. 12 (mu) and Eq. 8 (energy).
+    ("linear_mu_doubled", "reg = sc.eps * F.lap2[id];  // Eq. 12",
+     "reg = 2.0 * sc.eps * F.lap2[id];", ["test_linear_regularisation_visible"]),
+    ("linear_mu_sign", "reg = sc.eps * F.lap2[id];  // Eq. 12",
+     "reg = -sc.eps * F.lap2[id];", ["test_linear_regularisation_visible"]),
+    ("linear_energy_factor", "e += 0.5 * sc.eps * lap * lap;  // Eq. 8\n      }",
+     "e += sc.eps * lap * lap;\n      }", ["test_energy_closed_form_cosines_linear_regularisation"]),
+    ("linear_energy_willmore_g",
+     "e += 0.5 * sc.eps * lap * lap;  // Eq. 8\n      }",
+     "e += 0.5 * sc.eps * (lap - bulk_f(sc, phi[id])) * (lap - bulk_f(sc, phi[id]));\n      }",
+     ["test_energy_closed_form_cosines_linear_regularisation"]),
+    # Nested mu_beta (reading C2, literal Eq. 16).
+    ("nested_as_split", "const double iso = nested ? a.gamma : (a.gamma - 1.0);\n      F.Qx",
+     "const double iso = a.gamma - 1.0;\n      F.Qx",
+     ["test_nested_mu_beta_isotropic_cosine_symbol", "test_nested_minus_split_is_lattice_commutator"]),
+    ("nested_minus_f_only", "F.mub[id] = mu - F.mua[id];",
+     "F.mub[id] = mu - fb;",
+     ["test_nested_mu_beta_isotropic_cosine_symbol", "test_nested_minus_split_is_lattice_commutator"]),
+    # The tangential term k |grad phi| P grad_n gamma of Eq. 15 (reading C1) and its literal form.
+    ("tangential_drops_k", "const double kq = literal_q ? 1.0 : sc.k;  // factor",
+     "const double kq = 1.0;  // factor", ["test_tangential_term_curved_interface"]),
+    ("literal_keeps_k", "const double kq = literal_q ? 1.0 : sc.k;  // factor",
+     "const double kq = sc.k;  // factor", ["test_tangential_term_curved_interface"]),
+    ("projector_sign", "const double P11 = 1.0 - n1 * n1, P12 = -n1 * n2, P22 = 1.0 - n2 * n2;",
+     "const double P11 = 1.0 + n1 * n1, P12 = n1 * n2, P22 = 1.0 + n2 * n2;",
+     ["test_tangential_term_curved_interface"]),
+    ("grad_n_gamma_12_alpha",
+     "const double gn1 = 16.0 * sc.alpha * n1 * n1 * n1;       // grad_n gamma\n"
+     "  const double gn2 = 16.0 * sc.alpha * n2 * n2 * n2;",
+     "const double gn1 = 12.0 * sc.alpha * n1 * n1 * n1;\n"
+     "  const double gn2 = 12.0 * sc.alpha * n2 * n2 * n2;",
+     ["test_tangential_term_curved_interface"]),
+    ("grad_n_gamma_swapped",
+     "const double gn1 = 16.0 * sc.alpha * n1 * n1 * n1;       // grad_n gamma\n"
+     "  const double gn2 = 16.0 * sc.alpha * n2 * n2 * n2;",
+     "const double gn1 = 16.0 * sc.alpha * n2 * n2 * n2;\n"
+     "  const double gn2 = 16.0 * sc.alpha * n1 * n1 * n1;",
+     ["test_tangential_term_curved_interface"]),
+    # gamma(theta) of Eq. 6 between the axis and diagonal values: c |c| equals c = cos 4 theta
+    # at c = +-1 (axes and diagonals), so only a generic angle can tell them apart.
+    ("gamma_generic_angle",
+     "a.gamma = 1.0 + sc.alpha * (4.0 * (n1_4 + n2_4) - 3.0);  // Eq. 6, d = 2",
+     "a.gamma = 1.0 + sc.alpha * (4.0 * (n1_4 + n2_4) - 3.0) * std::fabs(4.0 * (n1_4 + n2_4) - 3.0);",
+     ["test_linear_dispersion_generic_angle"]),
+    # The n = 0 guard (reading C3) at a threshold that reaches interface nodes.
+    ("guard_too_high", "const double GUARD = 1e-12;", "const double GUARD = 1e-6;",
+     ["test_guard_fires_only_in_the_bulk"]),
+]
+
+
+def _planted_source(old, new):
+    src = open(SRC).read()
+    cut = src.index("// 3D: D3Q15")  # plant in the 2D scheme only
+    head, tail = src[:cut], src[cut:]
+    assert head.count(old) == 1, old
+    return head.replace(old, new) + tail
+
+
+def _build_and_run(tmp, name, old, new, pins):
+    d = os.path.join(tmp, name)
+    os.makedirs(d, exist_ok=True)
+    cpp = os.path.join(d, "lbch_oracle.cpp")
+    with open(cpp, "w") as fh:
+        fh.write(_planted_source(old, new))
+    lib = os.path.join(d, "liboracle.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
+                    "-fPIC", "-shared", "-I", os.path.join(ROOT, "oracle"), cpp, "-o", lib], check=True)
+    env = dict(os.environ, LBCH_ORACLE_LIB=lib, OMP_NUM_THREADS="2")
+    rc = {}
+    for pin in pins:
+        r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
+                            f"{PINS}::{pin}"], cwd=ROOT, env=env, capture_output=True, text=True)
+        rc[pin] = (r.returncode, r.stdout[-2000:])
+    return rc
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    tmp = str(tmp_path_factory.mktemp("oracle_mutants"))
+    with ThreadPoolExecutor(max(1, min(len(MUTANTS), (os.cpu_count() or 2) // 2))) as ex:
+        futs = {m[0]: ex.submit(_build_and_run, tmp, *m) for m in MUTANTS}
+        return {k: f.result() for k, f in futs.items()}
+
+
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(outcomes, name):
+    for pin, (code, out) in outcomes[name].items():
+        # pytest exit code 1: tests ran and at least one failed (not a build or collection error).
+        assert code == 1, f"{name}: pin {pin} did not fail (exit {code})\n{out}"

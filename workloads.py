@@ -49,17 +49,20 @@ def noise(nx: int, ny: int, amplitude: float, seed: int, mean: float = 0.0) -> n
     return mean + rng.uniform(-amplitude, amplitude, size=(ny, nx))
 
 
-def cosine_mode(nx: int, ny: int, mx: int, my: int, amplitude: float, mean: float) -> np.ndarray:
+def cosine_mode(nx: int, ny: int, mx: int, my: int, amplitude: float, mean: float,
+                shift: float | None = None) -> np.ndarray:
     """mean + A cos(q . x + shift), q = 2 pi (mx/nx, my/ny).
 
-    The shift of half a node along the dominant axis (pi |m|/n) keeps every node off the
-    zeros of the gradient, so no node has grad phi = 0.
+    The default shift of half a node along the dominant axis (pi |m|/n) keeps every node
+    off the zeros of the gradient for modes along an axis or a diagonal, so no node has
+    grad phi = 0. Other directions pass their own shift.
     """
     y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64),
                        indexing="ij")
-    m = max(abs(mx), abs(my))
-    n = nx if abs(mx) >= abs(my) else ny
-    shift = np.pi * m / n
+    if shift is None:
+        m = max(abs(mx), abs(my))
+        n = nx if abs(mx) >= abs(my) else ny
+        shift = np.pi * m / n
     return mean + amplitude * np.cos(2 * np.pi * (mx * x / nx + my * y / ny) + shift)
 
 
