@@ -9,7 +9,11 @@ are far larger than L2, so no flush is needed between steps.
 
 Prints one JSON line. The metric is MLUPS (million lattice-node updates per
 second), with the step kernel's HBM roofline fraction for FP32 storage and, as
-variants, the BF16- and FP16-deviation storages.
+variants, the BF16- and FP16-deviation storages. Beside it: the 64^2 droplet
+(single launches and graph replay), the 256^2 spinodal run of 20000 steps in every
+storage with its energy law and error against the FP64 oracle, the error of every
+storage against the oracle per workload, the batched sweep, the D3Q15 cube, the
+learned leap with its online judge, and the oracle's own rates on the host cores.
 
 --impl reference times the FP64 CPU oracle (the test suite's reference) on the
 host cores instead, on a 2048x2048 sample of the same workload.
@@ -57,6 +61,9 @@ def parse():
     ap.add_argument("--no-3d", action="store_true", help="skip the D3Q15 measurement")
     ap.add_argument("--n3", type=int, default=256, help="edge of the D3Q15 spinodal cube (default 256)")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-leap time-to-t measurement")
+    ap.add_argument("--no-small-configs", action="store_true",
+                    help="skip the 64^2 droplet and 256^2 spinodal legs and the oracle comparisons")
+    ap.add_argument("--config2-steps", type=int, default=20000, help="steps of the 256^2 spinodal run")
     ap.add_argument("--storage", choices=["f32", "bf16_dev", "f16_dev"], default="f32",
                     help="population storage of the main timed line")
     return ap.parse_args()
@@ -110,6 +117,21 @@ def max_over_ranks(dist, v: float) -> float:
 def job_rate(world: int, units_per_rank: float, max_seconds: float) -> float:
     """Whole-job throughput of independent replicas: all units over the slowest rank's time."""
     return world * units_per_rank / max_seconds
+
+
+NOMINAL_HBM_GBS = 8000.0  # the GB300's nominal HBM3e bandwidth, about 8 TB/s
+
+
+def sig(v, digits: int = 4):
+    """Rounds floats (also inside dicts and lists) to a few significant digits, so the JSON
+    line stays short."""
+    if isinstance(v, float):
+        return float(f"{v:.{digits}g}") if np.isfinite(v) else v
+    if isinstance(v, dict):
+        return {k: sig(x, digits) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [sig(x, digits) for x in v]
+    return v
 
 
 def measured_peaks():
@@ -285,6 +307,173 @@ def run_3d(lbch, torch, n: int, steps: int):
             "launch": "three kernels per step (phi; mu_alpha and mu_beta by a z-sweep; collide and store)"}
 
 
+def run_config1(lbch, torch, steps: int = 2000):
+    """The 64^2 droplet workload (radius 20, profile tanh((R - r)/(sqrt(2) 1.5)), alpha 0.3),
+    FP32: the time per step with one launch per lbch_step call and with the context's graph
+    replay (launch-bound: 4096 nodes per step, labelled, not a roofline number), and phi
+    after `steps` steps in every storage for the oracle comparison."""
+    import workloads
+
+    n = 64
+    phi0 = workloads.droplet_workload(n)
+    out, fields = {"workload": f"droplet-{n}x{n} alpha {ALPHA}", "steps": steps}, {}
+    s = lbch.Solver(lbch.make_params(n, n, alpha=ALPHA))
+    for mode in ("single", "graph"):
+        s.init_field(phi0)
+        s.step(32)
+        s.init_field(phi0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        if mode == "single":
+            for _ in range(steps):
+                s.step(1)
+        else:
+            s.step(steps)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        out[f"us_per_step_{mode}"] = sec / steps * 1e6
+        out[f"mlups_{mode}"] = steps * n * n / sec / 1e6
+    fields["f32"] = s.field()
+    s.close()
+    for name, st in (("bf16_dev", lbch.STORE_BF16_DEV), ("f16_dev", lbch.STORE_F16_DEV)):
+        v = lbch.Solver(lbch.make_params(n, n, alpha=ALPHA, storage=st))
+        v.init_field(phi0)
+        v.step(steps)
+        fields[name] = v.field()
+        v.close()
+    out["bound"] = "launch/latency (L2-resident, 4096 nodes per step)"
+    return out, fields
+
+
+def run_config2(lbch, torch, steps: int = 20000, every: int = 100, alpha: float = 0.2, n: int = 256):
+    """The 256^2 spinodal workload (U[-0.05, 0.05], seed 0, alpha 0.2): `steps` steps in each
+    storage with mass and free energy logged every `every` steps on the device (read back
+    once), phi at 1000 and at `steps` steps. Returns per storage the MLUPS of the whole
+    logged run, the logs and the two fields."""
+    import workloads
+
+    phi0 = workloads.noise(n, n, NOISE, SEED)
+    res = {}
+    for name, st in (("f32", lbch.STORE_F32), ("bf16_dev", lbch.STORE_BF16_DEV), ("f16_dev", lbch.STORE_F16_DEV)):
+        s = lbch.Solver(lbch.make_params(n, n, alpha=alpha, storage=st))
+        s.init_field(phi0)
+        s.step(64)  # warm-up: the graph is captured, clocks up
+        s.init_field(phi0)
+        k = steps // every
+        log = torch.zeros((k + 1, 2), dtype=torch.float64, device=s.device)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.mass_device(log[0, 0:1])
+        s.free_energy_device(log[0, 1:2])
+        phi1000 = None
+        for j in range(1, k + 1):
+            s.step(every)
+            s.mass_device(log[j, 0:1])
+            s.free_energy_device(log[j, 1:2])
+            if j * every == 1000:
+                phi1000 = s.phi_device().clone()
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        res[name] = {"mlups": steps * n * n / sec / 1e6, "us_per_step": sec / steps * 1e6,
+                     "log": log.cpu().numpy(), "phi1000": phi1000.cpu().numpy().astype(np.float64),
+                     "phi_end": s.field()}
+        s.close()
+    return res
+
+
+def energy_law(E, rise_tol: float = 1e-4, trend: float = 0.9):
+    """The energy gate of the small-noise spinodal at alpha > 0: rises between samples of at
+    most rise_tol |E| (Eq. 15 is the exact gradient flow only at an interface) and a falling
+    trend (the last sample below trend times the first)."""
+    E = np.asarray(E, dtype=np.float64)
+    rise = float(np.max(np.diff(E) / np.abs(E[:-1])))
+    ok = bool(rise <= rise_tol and E[-1] < trend * E[0])
+    return {"max_rise_rel": rise, "end_over_start": float(E[-1] / E[0]), "gate": f"rise<={rise_tol:g}, end<{trend:g} start",
+            "pass": ok}
+
+
+def full_size_window_errors(lbch, phi0, n: int, steps: int = 5, wsz: int = 32):
+    """max |phi - phi_oracle| of each storage on the 8192^2 workload after `steps` steps, on
+    eight windows (corners, the periodic seam, strip and segment boundaries), the oracle
+    running each window with a halo of the steps' footprint (exact on the window)."""
+    import oracle
+
+    p = oracle.Params(n, n, alpha=ALPHA)
+    corners = [(0, 0), (n - wsz, n - wsz), (n - wsz, 0), (0, n - wsz), (4000, 4090), (116, 7000),
+               (120 * 34 - 16, 482 * 9 - 16), (8150, 470)]
+    refs = [oracle.run_window(p, phi0, x0, y0, wsz, wsz, steps) for (x0, y0) in corners]
+    out = {}
+    for name, st in (("f32", lbch.STORE_F32), ("bf16_dev", lbch.STORE_BF16_DEV), ("f16_dev", lbch.STORE_F16_DEV)):
+        s = lbch.Solver(lbch.make_params(n, n, alpha=ALPHA, storage=st))
+        s.init_field(phi0)
+        s.step(steps)
+        g = s.field()
+        s.close()
+        out[name] = max(float(np.abs(g[y0:y0 + wsz, x0:x0 + wsz] - r).max()) for (x0, y0), r in zip(corners, refs))
+        del g
+    return out
+
+
+def timed_oracle(p, f, steps: int, threads: int):
+    """Runs the oracle `steps` steps on `threads` host threads; returns (state, seconds)."""
+    import oracle
+
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    g = oracle.step(p, f, steps)
+    return g, time.perf_counter() - t0
+
+
+def oracle_legs(c1_fields, c2, full_windows, c1_steps: int = 2000, c2_steps: int = 20000):
+    """The FP64 oracle on the host cores: the reference results of the 64^2 droplet (2000
+    steps) and of the 256^2 spinodal run (1000 and 20000 steps), with the errors of every
+    storage against them, and the oracle's own rates single-threaded and on all cores
+    (configs 1 and 2 in full on all cores; single-threaded samples of 300 and 1000 steps;
+    the 8192^2 workload from a 2048^2 sample)."""
+    import oracle
+    import workloads
+
+    cores = os.cpu_count() or 1
+    rates = {}
+    # 64^2 droplet, alpha 0.3
+    p1 = oracle.Params(64, 64, alpha=ALPHA)
+    f1 = oracle.init(p1, workloads.droplet_workload(64))
+    g1, dt = timed_oracle(p1, f1, c1_steps, cores)
+    rates["droplet64"] = {"all_cores": c1_steps * 64 * 64 / dt / 1e6}
+    _, dt = timed_oracle(p1, f1, c1_steps, 1)
+    rates["droplet64"]["one_core"] = c1_steps * 64 * 64 / dt / 1e6
+    ref1 = oracle.phi(p1, g1)
+    # 256^2 spinodal, alpha 0.2
+    p2 = oracle.Params(256, 256, alpha=0.2)
+    f2 = oracle.init(p2, workloads.noise(256, 256, NOISE, SEED))
+    _, dt = timed_oracle(p2, f2, 300, 1)
+    rates["spinodal256"] = {"one_core": 300 * 256 * 256 / dt / 1e6, "one_core_sample_steps": 300}
+    g2a, dta = timed_oracle(p2, f2, 1000, cores)
+    g2b, dtb = timed_oracle(p2, g2a, c2_steps - 1000, cores)
+    rates["spinodal256"]["all_cores"] = c2_steps * 256 * 256 / (dta + dtb) / 1e6
+    ref2a, ref2b = oracle.phi(p2, g2a), oracle.phi(p2, g2b)
+    e2_end = oracle.energy(p2, g2b)
+    # 8192^2 workload: per-node rate from a 2048^2 sample
+    p4 = oracle.Params(2048, 2048, alpha=ALPHA)
+    f4 = oracle.init(p4, workloads.noise(2048, 2048, NOISE, SEED))
+    _, dt = timed_oracle(p4, f4, 1, 1)
+    rates["spinodal8192_from_2048_sample"] = {"one_core": 2048 * 2048 / dt / 1e6}
+    oracle.set_threads(cores)
+    errs = {}
+    for name in ("f32", "bf16_dev", "f16_dev"):
+        errs[name] = {
+            f"droplet64_{c1_steps}": float(np.abs(c1_fields[name] - ref1).max()),
+            "spinodal256_1000": float(np.abs(c2[name]["phi1000"] - ref2a).max()),
+            f"spinodal256_{c2_steps}": float(np.abs(c2[name]["phi_end"] - ref2b).max()),
+            "spinodal8192_5_windows": full_windows[name],
+        }
+    return {"errors": errs, "rates": rates, "cores": cores, "energy_oracle_spinodal256_end": e2_end}
+
+
 SURROGATE_THETA = os.path.join(ROOT, "paper_2501_03759_gb300", "weights", "leap512_k500.npy")
 
 
@@ -301,15 +490,27 @@ def run_surrogate(alphas=(0.1, 0.3, 0.45), seed: int = 777):
     runs = []
     for a in alphas:
         r = surrogate.evaluate(theta, a, seed)
-        r["pass"] = bool(r["phi_rel_l2"] <= gates["phi_rel_l2_max"] and
-                         r["energy_rel_diff"] <= gates["energy_rel_diff_max"] and r["speedup"] >= gates["speedup_min"])
-        runs.append(r)
-    return {"workload": "spinodal-512x512 learned leap K=500 + 50 LBM steps to t=50000, held-out seed",
-            "weights": os.path.relpath(SURROGATE_THETA, ROOT), "gates": gates, "by_alpha": runs,
-            "speedup": min(r["speedup"] for r in runs)}
+        j = r["judge"]
+        runs.append({"alpha": a, "phi_rel_l2": r["phi_rel_l2"], "energy_rel_diff": r["energy_rel_diff"],
+                     "mass_drift_abs": r["mass_drift_abs"], "s_plain": r["seconds_plain"],
+                     "s_leap": r["seconds_leap"], "speedup": r["speedup"],
+                     "judge": [j["accepted"], j["rejected"], j["rejected_energy"], j["rejected_mass"],
+                               j["rejected_nonfinite"]],
+                     "max_rise": [j["max_leap_rise"], j["max_corr_rise"]],
+                     "pass": bool(r["phi_rel_l2"] <= gates["phi_rel_l2_max"] and
+                                  r["energy_rel_diff"] <= gates["energy_rel_diff_max"] and
+                                  r["speedup"] >= gates["speedup_min"])})
+    return {"workload": "spinodal-512^2 K=500 leap + 50 LBM steps to t=50000, held-out seed 777, judged",
+            "judge": f"lbnop_leap_run_judged: energy_rtol {surrogate.JUDGE['energy_rtol']:g}, "
+                     f"mass_atol {surrogate.JUDGE['mass_atol']:g}/node; judge = [accepted, rejected, "
+                     "by energy, by mass, non-finite]; max_rise = largest relative energy rise across a "
+                     "leap and across its 50 correction steps",
+            "network": "96/64/96/96 channels, 826,096 parameters: wider than the configured 32 base "
+                       "channels (~0.5M), which left the rollout error 2-4x above the gate",
+            "gates": gates, "by_alpha": runs, "speedup": min(r["speedup"] for r in runs)}
 
 
-def cpu_oracle_rate(target_s: float = 12.0, n_sample: int = 2048):
+def cpu_oracle_rate(target_s: float = 8.0, n_sample: int = 2048):
     """The FP64 oracle, as it stands, on the host cores: MLUPS on an n_sample^2 spinodal
     sample of the workload (alpha 0.3, noise 0.05, seed 0)."""
     import oracle
@@ -341,11 +542,9 @@ def reference_arm(args, rank, world):
     cores = oracle.set_threads(os.cpu_count() or 1)
     p = oracle.Params(n_sample, n_sample, alpha=ALPHA)
     f = oracle.init(p, workloads.noise(n_sample, n_sample, NOISE, SEED))
-    for _ in range(args.warmup):
-        f = oracle.step(p, f, 1)
+    f = oracle.step(p, f, args.warmup)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        f = oracle.step(p, f, 1)
+    f = oracle.step(p, f, args.steps)  # one call: the oracle allocates its field passes once
     dt = time.perf_counter() - t0
     value = args.steps * n_sample * n_sample / dt / 1e6
     line = {
@@ -403,13 +602,18 @@ def main():
     value = job_rate(world, lu_per_rank, total) / 1e6
 
     peak, peak_kind = measured_peaks()
-    bpl = lbch.ALGORITHMIC_BYTES_PER_LU[main_st]
-    achieved = bpl * n * n / per_launch / 1e9
-    traffic = profiled_traffic(args.storage)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None if traffic is None else traffic * n * n,
-                "peak_kind": peak_kind, "kernel": f"lbch::step_kernel<{args.storage}, vec, fast rates>",
-                "algorithmic_bytes_per_launch": bpl * n * n, "launch_ms": per_launch * 1e3}
+
+    def roofline_of(st, name, launch_s):
+        b = lbch.ALGORITHMIC_BYTES_PER_LU[st]
+        ach = b * n * n / launch_s / 1e9
+        tr = profiled_traffic(name)
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "frac_of_nominal_8tbs": ach / NOMINAL_HBM_GBS,
+                "traffic": None if tr is None else tr * n * n, "peak_kind": peak_kind,
+                "kernel": f"lbch::step_kernel<{name}, vec, fast rates>", "algorithmic_bytes_per_launch": b * n * n,
+                "launch_ms": launch_s * 1e3}
+
+    roofline = roofline_of(main_st, args.storage, per_launch)
 
     variants = {}
     if not args.no_variants:
@@ -418,19 +622,15 @@ def main():
                 continue
             r = time_storage(lbch, torch, phi0, n, st, args.steps, args.warmup)
             pl = max_over_ranks(dist, r["kernel_s_per_launch"])
-            b = lbch.ALGORITHMIC_BYTES_PER_LU[st]
-            ach = b * n * n / pl / 1e9
+            rf = roofline_of(st, name, pl)
             variants[name] = {"value": job_rate(world, lu_per_rank, max_over_ranks(dist, r["total_s"])) / 1e6,
-                              "unit": "MLUPS", "launch_ms": pl * 1e3,
-                              "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                                           "frac": ach / peak, "traffic": None if profiled_traffic(name) is None
-                                           else profiled_traffic(name) * n * n, "peak_kind": peak_kind},
-                              "kernel_only_mlups": n * n / pl / 1e6 * world,
+                              "launch_ms": pl * 1e3, "frac": rf["frac"], "frac_of_nominal_8tbs": rf["frac_of_nominal_8tbs"],
+                              "traffic": rf["traffic"],
                               "mass_drift_rel": abs(r["mass_last"] - r["mass_first"]) / max(1e-300, abs(r["mass_first"]))}
 
     e2e = None
     if not args.no_e2e:
-        e = run_e2e(lbch, torch, phi0, n, max(1, min(args.steps, 5)), 1)
+        e = run_e2e(lbch, torch, phi0, n, args.steps, 1)
         barrier()
         e2e = {"value": job_rate(world, e["lu"], max_over_ranks(dist, e["wall_s"])) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": e["h2d_bytes_per_step"], "d2h_bytes_per_step": e["d2h_bytes_per_step"],
@@ -442,20 +642,50 @@ def main():
         peak_bw = measured_peaks()[0]
         batch["roofline_frac"] = 72 * batch["value"] * 1e6 / (peak_bw * 1e9)
         batch["value"] = job_rate(world, batch["value"], 1.0)  # replicas: rates add
+        batch.pop("launch", None)
         if not args.no_variants:
             bv = run_batch_sweep(lbch, torch, args.batch_steps, storage="bf16_dev")
-            bv["roofline_frac"] = 48 * bv["value"] * 1e6 / (peak_bw * 1e9)
-            bv["value"] = job_rate(world, bv["value"], 1.0)
-            batch["variants"] = {"bf16_dev": bv}
+            batch["bf16_dev"] = {"value": job_rate(world, bv["value"], 1.0), "ms_per_step": bv["ms_per_step"],
+                                 "rows_per_warp": bv["rows_per_warp"],
+                                 "roofline_frac": 48 * bv["value"] * 1e6 / (peak_bw * 1e9)}
 
     d3 = None
     if not args.no_3d:
         d3 = run_3d(lbch, torch, args.n3, 50)
         d3["paper_100"] = run_3d(lbch, torch, 100, 200)["value"]
+        d3.pop("launch", None)
 
     leap = None
     if not args.no_surrogate and rank == 0:
         leap = run_surrogate()
+
+    cfg1 = cfg2 = errors = cpu_rates = None
+    if rank == 0 and world == 1 and not args.no_small_configs:
+        cfg1, c1_fields = run_config1(lbch, torch)
+        c2 = run_config2(lbch, torch, args.config2_steps)
+        windows = full_size_window_errors(lbch, phi0, n) if not args.no_cpu_baseline else None
+        cfg2 = {"workload": "spinodal-256x256 alpha 0.2", "steps": args.config2_steps,
+                "log_every": 100}
+        for name, r in c2.items():
+            cfg2[name] = {"mlups": r["mlups"], "us_per_step": r["us_per_step"],
+                          "energy_law": energy_law(r["log"][:, 1]),
+                          "mass_drift_per_node": float(abs(r["log"][-1, 0] - r["log"][0, 0]) / (256 * 256))}
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        csv = os.path.join(ROOT, "gpurun_out", "config2_spinodal256_mass_energy.csv")
+        with open(csv, "w") as fh:
+            fh.write("step," + ",".join(f"mass_{k},energy_{k}" for k in c2) + "\n")
+            for j in range(c2["f32"]["log"].shape[0]):
+                fh.write(f"{j * 100}," + ",".join(f"{c2[k]['log'][j, 0]:.12e},{c2[k]['log'][j, 1]:.12e}"
+                                                    for k in c2) + "\n")
+        cfg2["csv"] = os.path.relpath(csv, ROOT)
+        if not args.no_cpu_baseline:
+            o = oracle_legs(c1_fields, c2, windows, c2_steps=args.config2_steps)
+            errors = o["errors"]
+            cpu_rates = o["rates"]
+            cpu_rates["cores"] = o["cores"]
+            cfg2["energy_end_vs_oracle_rel"] = {
+                k: abs(float(c2[k]["log"][-1, 1]) - o["energy_oracle_spinodal256_end"]) /
+                abs(o["energy_oracle_spinodal256_end"]) for k in c2}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -473,10 +703,16 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline,
             "kernel_only_mlups": world * n * n / per_launch / 1e6,
-            "variants": variants,
             "batch_sweep": batch,
             "d3q15": d3,
             "surrogate": leap,
+            "config1_droplet64": cfg1,
+            "config2_spinodal256": cfg2,
+            "variants": variants,
+            "max_abs_dphi_vs_fp64_oracle": errors,
+            "oracle_error_bounds": {"f32": "1e-6 after 1 step, 1e-4 after 1000 steps (gated in tests)",
+                                    "bf16_dev/f16_dev": "reported; tests hold measured maxima x2"},
+            "cpu_oracle_rates_mlups": cpu_rates,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk.summary(),
@@ -484,7 +720,9 @@ def main():
             "mass_drift_rel": abs(r32["mass_last"] - r32["mass_first"]) / max(1e-300, abs(r32["mass_first"])),
             "energy_first_last": [r32["energy_first"], r32["energy_last"]],
         }
-        print(json.dumps(line), flush=True)
+        line = {k: (sig(v, 6) if k in ("value", "ms_per_step", "energy_first_last") else sig(v))
+                for k, v in line.items()}
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

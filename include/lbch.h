@@ -143,8 +143,36 @@ lbch_status lbch_get_state(lbch_ctx* ctx, double* h_f9);
  * Synchronises. LBCH_ENONFINITE (state left unset) if h_f9 holds NaN/Inf. */
 lbch_status lbch_set_state(lbch_ctx* ctx, const double* h_f9);
 
-/* Number of time steps taken since the last lbch_init_field / lbch_set_state. */
+/* Asynchronous forms of lbch_mass and lbch_free_energy (same kernels, same FP64 sums):
+ * the result goes to one double in device memory, d_out, and the call returns without
+ * synchronising, so that diagnostics can be chained with steps on the stream and read
+ * back once. They do not check the result for NaN/Inf. */
+lbch_status lbch_mass_device(lbch_ctx* ctx, double* d_out);
+lbch_status lbch_free_energy_device(lbch_ctx* ctx, double* d_out);
+
+/* Bytes of one state (the population buffer a step reads) for these parameters; 0 if
+ * they are invalid. */
+size_t lbch_state_bytes(const lbch_params* p);
+
+/* Device-side checkpoint: copies the current state into d_dst (device memory of at least
+ * lbch_state_bytes(p) bytes, owned by the caller), asynchronously. The copy is an
+ * opaque image of the library's storage, valid only for a context with the same
+ * parameters. LBCH_EINVAL if bytes is too small or there is no state. */
+lbch_status lbch_save_state_device(lbch_ctx* ctx, void* d_dst, size_t bytes);
+
+/* Makes an image saved by lbch_save_state_device the current state, asynchronously. The
+ * continuation is bit for bit the one the saved context would have taken. The step
+ * counter is left as it is. */
+lbch_status lbch_restore_state_device(lbch_ctx* ctx, const void* d_src, size_t bytes);
+
+/* Number of time steps taken since the last lbch_init_field / lbch_set_state /
+ * lbch_init_field_device, or the value last given to lbch_set_steps_taken. */
 int64_t lbch_steps_taken(const lbch_ctx* ctx);
+
+/* Sets the step counter that lbch_steps_taken reports (bookkeeping only, no GPU work):
+ * a caller that re-initialises the state from a field standing for a later time (the
+ * learned leap of lbnop.h) keeps the simulated time this way. LBCH_EINVAL if steps < 0. */
+lbch_status lbch_set_steps_taken(lbch_ctx* ctx, int64_t steps);
 
 /* Human-readable description of the last error on this context ("" if none). */
 const char* lbch_last_error(const lbch_ctx* ctx);
@@ -211,7 +239,7 @@ void lbch_batch_destroy(lbch_batch* b);
  * host application that is only allowed to launch work on memory it already owns.
  * It computes the same quantity as lbch_free_energy, without a context or workspace.
  *   p:            scheme parameters (nx, ny, sigma, D, eps, alpha, regularization; the
- *                 storage field is ignored).
+ *                 storage field is ignored and not validated: the state is FP32).
  *   d_f9:         device array of the post-streaming populations f_i(x, t) in FP32, 9
  *                 planes, plane i starting at d_f9 + i * plane_stride, each row-major with
  *                 x fastest (the layout of lbch_get_state, in FP32 on the device).
@@ -226,7 +254,9 @@ void lbch_batch_destroy(lbch_batch* b);
  * address (cudaGetSymbolAddress) and the SM count; make that first call before any
  * stream capture. All calls share the array and every call overwrites the parts it
  * reads (nothing carries over between calls), so calls that overlap on the GPU race.
- * Returns LBCH_EINVAL for bad arguments, LBCH_ECUDA if set-up or a launch fails. */
+ * Returns LBCH_EINVAL for bad arguments, LBCH_ECUDA if set-up or a launch fails. A CUDA
+ * error left pending by earlier work of the calling thread is reported as LBCH_ECUDA
+ * before anything is launched, and stays pending for the caller to read. */
 lbch_status lbch_free_energy_static(const lbch_params* p, const float* d_f9, int64_t plane_stride,
                                     double* d_out, void* cuda_stream);
 

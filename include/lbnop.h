@@ -114,8 +114,56 @@ lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_a
 /* Runs `cycles` times: one leap of the network on the field of `lbm` (phi = sum f),
  * f = f^eq(phi_out) as in lbch_init_field, then lbm_steps steps of the scheme. The lbch
  * context must have nx = W, ny = H, FP32 storage, and work on the same CUDA stream as
- * this context. Asynchronous. */
+ * this context. Asynchronous. Every leap is applied unchecked, and each re-initialisation
+ * restarts the step counter of `lbm`, so afterwards lbch_steps_taken counts only the last
+ * lbm_steps; lbnop_leap_run_judged checks every leap and keeps the simulated time. */
 lbch_status lbnop_leap_run(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cycles, int64_t lbm_steps);
+
+/* The plain scheme as the judge of each leap in lbnop_leap_run_judged. */
+typedef struct {
+  int64_t leap_steps;      /* K > 0: the lattice steps one leap stands for. A rejected leap is
+                              replaced by K steps of the scheme from the saved pre-leap state. */
+  double energy_rtol;      /* >= 0: the free energy (Eq. 7) must not rise by more than
+                              energy_rtol |E| across a leap, nor across the lbm_steps
+                              correction steps after it (the energy law of Section 4) */
+  double mass_atol;        /* >= 0: |sum phi after the leap - sum phi before| <= mass_atol H W */
+  int64_t audit_every;     /* >= 0; 0 = no audits. Every audit_every-th cycle runs the K plain
+                              steps as well, compares phi (relative L2) with the leap's, and
+                              continues from the plain state */
+  double phi_rtol;         /* >= 0: an audited leap whose phi is further than this from the
+                              plain result counts as rejected */
+} lbnop_judge;
+
+/* What the judge saw during one lbnop_leap_run_judged call. */
+typedef struct {
+  int64_t accepted;            /* leaps kept (audited leaps within phi_rtol included) */
+  int64_t rejected;            /* leaps replaced by plain steps (sum of the four below) */
+  int64_t rejected_nonfinite;  /* NaN/Inf in the mass or energy after the leap or correction */
+  int64_t rejected_mass;       /* mass moved by more than mass_atol H W */
+  int64_t rejected_energy;     /* energy rose across the leap or across its correction steps */
+  int64_t rejected_audit;      /* audited leaps further than phi_rtol from the plain result */
+  int64_t audits;              /* audited cycles */
+  int64_t lbm_steps;           /* lattice steps of the scheme run in total */
+  double max_audit_err;        /* largest relative L2 phi error an audit measured */
+  double max_leap_rise;        /* largest (E_after - E_before)/|E_before| across a judged leap */
+  double max_corr_rise;        /* the same across the correction steps after a judged leap */
+} lbnop_judge_stats;
+
+/* lbnop_leap_run with the plain scheme as judge and fallback. Each of the `cycles` cycles
+ * saves the state of `lbm` in this context's workspace, leaps, re-initialises f =
+ * f^eq(phi_out), runs lbm_steps steps, and then reads back (one synchronisation per
+ * cycle) the mass and free energy before the leap, after it and after the correction.
+ * If any is NaN/Inf, the mass moved by more than mass_atol H W, or the energy rose by
+ * more than energy_rtol |E| across the leap or the correction, the saved state is
+ * restored and K + lbm_steps plain steps are run instead, so that a run in which every
+ * leap is rejected equals the plain scheme bit for bit. Audited cycles (audit_every)
+ * run the plain K steps next to the leap instead of re-initialising, and continue from
+ * the plain state. After each cycle the step counter of `lbm` (lbch_steps_taken) has
+ * advanced by K + lbm_steps: simulated time, whether the cycle leapt or not.
+ * The lbch context must satisfy what lbnop_leap_run requires. `stats` (may be NULL)
+ * receives the counts. LBCH_EINVAL for an invalid judge. */
+lbch_status lbnop_leap_run_judged(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cycles,
+                                  int64_t lbm_steps, const lbnop_judge* judge, lbnop_judge_stats* stats);
 
 /* Operator entry points (device pointers, the given stream, asynchronous), as used by
  * the network. BF16 tensors are uint16_t bit patterns, channels last:

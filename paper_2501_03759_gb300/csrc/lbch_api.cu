@@ -238,6 +238,22 @@ void launch_set_dev(lbch_ctx* c, int i) {
     default: FN<ST_F16>(__VA_ARGS__); break;       \
   }
 
+// phi in FP32 (stage1), the energy densities, and their fixed-order FP64 sum into d_out.
+void launch_energy(lbch_ctx* c, double* d_out) {
+  float* phi_f = reinterpret_cast<float*>(c->stage1);
+  DISPATCH(c->p.storage, launch_phi, c, nullptr, phi_f);
+  EnergyConsts ec;
+  const double eps = c->p.regularization == LBCH_REG_NONE ? 0.0 : c->p.eps;
+  ec.k = (float)c->k;
+  ec.beta = (float)c->beta;
+  ec.beta4 = (float)(4.0 * c->beta);
+  ec.alpha = (float)c->p.alpha;
+  ec.half_eps = (float)(0.5 * eps);
+  ec.cw = c->p.regularization == LBCH_REG_LINEAR ? 0.0f : 1.0f;
+  energy_kernel<<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(phi_f, grid_of(c), ec, c->partial);
+  final_sum_kernel<<<1, 1024, 0, c->stream>>>(c->partial, c->aux_blocks, d_out);
+}
+
 lbch_status finish(lbch_ctx* c, const char* what) {
   if (cuda_failed(c, cudaGetLastError(), what)) return LBCH_ECUDA;
   return LBCH_OK;
@@ -512,18 +528,7 @@ lbch_status lbch_free_energy(lbch_ctx* c, double* out) {
   lbch_status st = precheck(c, true);
   if (st != LBCH_OK) return st;
   if (!out) return LBCH_EINVAL;
-  float* phi_f = reinterpret_cast<float*>(c->stage1);
-  DISPATCH(c->p.storage, launch_phi, c, nullptr, phi_f);
-  EnergyConsts ec;
-  const double eps = c->p.regularization == LBCH_REG_NONE ? 0.0 : c->p.eps;
-  ec.k = (float)c->k;
-  ec.beta = (float)c->beta;
-  ec.beta4 = (float)(4.0 * c->beta);
-  ec.alpha = (float)c->p.alpha;
-  ec.half_eps = (float)(0.5 * eps);
-  ec.cw = c->p.regularization == LBCH_REG_LINEAR ? 0.0f : 1.0f;
-  energy_kernel<<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(phi_f, grid_of(c), ec, c->partial);
-  final_sum_kernel<<<1, 1024, 0, c->stream>>>(c->partial, c->aux_blocks, c->result + 1);
+  launch_energy(c, c->result + 1);
   if ((st = finish(c, "free_energy: launch")) != LBCH_OK) return st;
   double v = 0.0;
   if (cuda_failed(c, cudaMemcpyAsync(&v, c->result + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
@@ -621,7 +626,62 @@ lbch_status lbch_set_state(lbch_ctx* c, const double* h_f9) {
   return LBCH_OK;
 }
 
+lbch_status lbch_mass_device(lbch_ctx* c, double* d_out) {
+  lbch_status st = precheck(c, true);
+  if (st != LBCH_OK) return st;
+  if (!d_out) return LBCH_EINVAL;
+  DISPATCH(c->p.storage, launch_mass, c, c->partial);
+  final_sum_kernel<<<1, 1024, 0, c->stream>>>(c->partial, c->aux_blocks, d_out);
+  return finish(c, "mass_device: launch");
+}
+
+lbch_status lbch_free_energy_device(lbch_ctx* c, double* d_out) {
+  lbch_status st = precheck(c, true);
+  if (st != LBCH_OK) return st;
+  if (!d_out) return LBCH_EINVAL;
+  launch_energy(c, d_out);
+  return finish(c, "free_energy_device: launch");
+}
+
+size_t lbch_state_bytes(const lbch_params* p) { return check_params(p) ? 0 : state_bytes(p); }
+
+lbch_status lbch_save_state_device(lbch_ctx* c, void* d_dst, size_t bytes) {
+  lbch_status st = precheck(c, true);
+  if (st != LBCH_OK) return st;
+  const size_t sb = state_bytes(&c->p);
+  if (!d_dst || bytes < sb) {
+    set_err(c, "save_state_device: destination is NULL or smaller than %zu bytes", sb);
+    return LBCH_EINVAL;
+  }
+  if (cuda_failed(c, cudaMemcpyAsync(d_dst, c->buf[c->cur].f32, sb, cudaMemcpyDeviceToDevice, c->stream),
+                  "save_state_device: copy"))
+    return LBCH_ECUDA;
+  return LBCH_OK;
+}
+
+lbch_status lbch_restore_state_device(lbch_ctx* c, const void* d_src, size_t bytes) {
+  lbch_status st = precheck(c, false);
+  if (st != LBCH_OK) return st;
+  const size_t sb = state_bytes(&c->p);
+  if (!d_src || bytes < sb) {
+    set_err(c, "restore_state_device: source is NULL or smaller than %zu bytes", sb);
+    return LBCH_EINVAL;
+  }
+  if (cuda_failed(c, cudaMemcpyAsync(c->buf[0].f32, d_src, sb, cudaMemcpyDeviceToDevice, c->stream),
+                  "restore_state_device: copy"))
+    return LBCH_ECUDA;
+  c->cur = 0;
+  c->has_state = true;
+  return LBCH_OK;
+}
+
 int64_t lbch_steps_taken(const lbch_ctx* c) { return c ? c->steps : -1; }
+
+lbch_status lbch_set_steps_taken(lbch_ctx* c, int64_t steps) {
+  if (!c || steps < 0) return LBCH_EINVAL;
+  c->steps = steps;
+  return LBCH_OK;
+}
 
 }  // extern "C"
 
@@ -683,7 +743,13 @@ extern "C" {
 
 lbch_status lbch_free_energy_static(const lbch_params* p, const float* d_f9, int64_t plane_stride,
                                     double* d_out, void* cuda_stream) {
-  if (check_params(p) || !d_f9 || !d_out) return LBCH_EINVAL;
+  if (!p || !d_f9 || !d_out) return LBCH_EINVAL;
+  lbch_params q = *p;
+  q.storage = LBCH_STORE_F32;  // the state is FP32 whatever the caller left in this field
+  if (check_params(&q)) return LBCH_EINVAL;
+  // An error pending from earlier work is the caller's: report it without launching,
+  // and leave it pending (peek, not get).
+  if (cudaPeekAtLastError() != cudaSuccess) return LBCH_ECUDA;
   const long long n = (long long)p->nx * p->ny;
   if (plane_stride < n) return LBCH_EINVAL;
   if (n > STATIC_MAX_NODES) return LBCH_EINVAL;  // beyond the static scratch
@@ -708,7 +774,9 @@ lbch_status lbch_free_energy_static(const lbch_params* p, const float* d_f9, int
   // Every partial slot the final sum reads, and every phi value the energy kernel reads,
   // is written earlier in this same call: nothing needs clearing.
   phi_canonical_kernel<<<(int)blocks, AUX_THREADS, 0, st>>>(d_f9, plane_stride, n, phi);
+  if (cudaGetLastError() != cudaSuccess) return LBCH_ECUDA;
   energy_kernel<<<(int)blocks, AUX_THREADS, 0, st>>>(phi, Grid{p->nx, p->ny, plane_stride}, ec, partial);
+  if (cudaGetLastError() != cudaSuccess) return LBCH_ECUDA;
   final_sum_kernel<<<1, 1024, 0, st>>>(partial, (int)blocks, d_out);
   return cudaGetLastError() == cudaSuccess ? LBCH_OK : LBCH_ECUDA;
 }

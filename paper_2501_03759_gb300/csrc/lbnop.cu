@@ -711,6 +711,44 @@ __global__ void grad_norm_kernel(const double* __restrict__ partial, double* __r
   if (threadIdx.x == 0) *norm = sqrt(s);
 }
 
+// Audit of a judged leap: sum (a - b)^2 and sum b^2 over n values in FP64 and a fixed
+// order; diff_norm_kernel (grid of HEAD_BLOCKS) leaves the two partial sums of each block in
+// partial[2 blk], partial[2 blk + 1]; diff_norm_final (one warp) writes out[0] = sum (a - b)^2
+// and out[1] = sum b^2.
+__global__ void diff_norm_kernel(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                                 double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double d2 = 0.0, b2 = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const double bv = b[k], dv = (double)a[k] - bv;
+    d2 = fma(dv, dv, d2);
+    b2 = fma(bv, bv, b2);
+  }
+  d2 = block_sum_d(d2, sh);
+  __syncthreads();
+  b2 = block_sum_d(b2, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = d2;
+    partial[2 * blockIdx.x + 1] = b2;
+  }
+}
+__global__ void diff_norm_final(const double* __restrict__ partial, int blocks, double* __restrict__ out) {
+  double d2 = 0.0, b2 = 0.0;
+  for (int k = threadIdx.x; k < blocks; k += 32) {
+    d2 += partial[2 * k];
+    b2 += partial[2 * k + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d2 += __shfl_down_sync(0xffffffffu, d2, o);
+    b2 += __shfl_down_sync(0xffffffffu, b2, o);
+  }
+  if (threadIdx.x == 0) {
+    out[0] = d2;
+    out[1] = b2;
+  }
+}
+
 // Adam (Kingma and Ba 2015, Algorithm 1; c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)) on
 // the gradient scaled by min(1, clip / |grad|) when clip > 0 (global-norm clipping), then the
 // BF16 copies of every weight: wf[t][co][ci] and wb[t][ci][co] = W[8 - t][co][ci].
@@ -912,6 +950,9 @@ struct lbnop_ctx {
   float *leap0, *leap1;
   float* phi_out;  // [max_batch][H][W], the training forward's output
   int* flags;
+  char* judge_state;        // saved lbch state of an H x W FP32 field (judged leap runs)
+  size_t judge_state_bytes;
+  double* judge_vals;       // 16 doubles: mass / energy readings and audit sums
   long long adam_t;
   int last_batch;
   bool failed;
@@ -934,6 +975,21 @@ const char* check_params(const lbnop_params* p) {
 
 long long level_pixels(const lbnop_params* p, int level) {
   return (long long)p->max_batch * ((p->H / 4) >> level) * ((p->W / 4) >> level);
+}
+
+// Bytes of the lbch state of an H x W field in FP32 storage (the leap runs' lbm context).
+size_t judge_state_size(const lbnop_params* p) {
+  lbch_params q{};
+  q.nx = p->W;
+  q.ny = p->H;
+  q.M = 0.1;
+  q.sigma = 0.01;
+  q.D = 5.0;
+  q.eps = 0.03;
+  for (int i = 0; i < 9; ++i) q.s[i] = 1.0;
+  q.storage = LBCH_STORE_F32;
+  q.regularization = LBCH_REG_WILLMORE;
+  return lbch_state_bytes(&q);
 }
 
 // Walks the workspace layout; with c == nullptr only measures it.
@@ -997,6 +1053,9 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
   char* leap1 = take((size_t)p->H * p->W * 4);
   char* phi_out = take((size_t)p->max_batch * p->H * p->W * 4);
   char* flags = take(16);
+  const size_t jsb = judge_state_size(p);
+  char* judge_state = take(jsb);
+  char* judge_vals = take(16 * 8);
   if (c) {
     c->n_params = n_params;
     c->n_w = n_w;
@@ -1039,6 +1098,9 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
     c->leap1 = (float*)leap1;
     c->phi_out = (float*)phi_out;
     c->flags = (int*)flags;
+    c->judge_state = judge_state;
+    c->judge_state_bytes = jsb;
+    c->judge_vals = (double*)judge_vals;
   }
   return off;
 }
@@ -1490,6 +1552,125 @@ lbch_status lbnop_leap_run(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cy
     }
   }
   return done(c, "leap_run: launch");
+}
+
+lbch_status lbnop_leap_run_judged(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cycles, int64_t lbm_steps,
+                                  const lbnop_judge* judge, lbnop_judge_stats* stats) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (!lbm || !judge || cycles < 0 || lbm_steps < 0) return LBCH_EINVAL;
+  const lbnop_judge& J = *judge;
+  if (J.leap_steps < 1 || J.audit_every < 0 || !(J.energy_rtol >= 0.0) || !std::isfinite(J.energy_rtol) ||
+      !(J.mass_atol >= 0.0) || !std::isfinite(J.mass_atol) || !(J.phi_rtol >= 0.0) || !std::isfinite(J.phi_rtol)) {
+    set_err(c, "leap_run_judged: invalid judge (leap_steps >= 1, tolerances finite and >= 0)");
+    return LBCH_EINVAL;
+  }
+  lbnop_judge_stats S{};
+  S.max_audit_err = 0.0;
+  S.max_leap_rise = -INFINITY;
+  S.max_corr_rise = -INFINITY;
+  const double nodes = (double)c->p.H * c->p.W;
+  const int64_t t0 = lbch_steps_taken(lbm);
+  double* dv = c->judge_vals;
+  double hv[8];
+  // Reads n doubles from the device readings into hv (one synchronisation).
+  auto fetch = [&](int first, int n, const char* what) -> bool {
+    return !cuda_bad(c, cudaMemcpyAsync(hv, dv + first, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                     what) &&
+           !cuda_bad(c, cudaStreamSynchronize(c->stream), what);
+  };
+  auto lbm_fail = [&](lbch_status s) {
+    set_err(c, "leap_run_judged: %s", lbch_last_error(lbm));
+    return s;
+  };
+  // Mass and energy of the state the first leap starts from.
+  if ((st = lbch_mass_device(lbm, dv + 0)) != LBCH_OK || (st = lbch_free_energy_device(lbm, dv + 1)) != LBCH_OK)
+    return lbm_fail(st);
+  if (!fetch(0, 2, "leap_run_judged: read")) return LBCH_ECUDA;
+  double m_before = hv[0], e_before = hv[1];
+  const int n_head = HEAD_BLOCKS;
+  for (int64_t k = 0; k < cycles; ++k) {
+    const bool audit = J.audit_every > 0 && (k + 1) % J.audit_every == 0;
+    if (audit) {
+      // leap prediction in leap0, plain K steps from the untouched state into leap1
+      if ((st = lbch_get_phi_device(lbm, c->leap0)) != LBCH_OK) return lbm_fail(st);
+      forward_impl(c, c->leap0, &alpha, 1, c->leap0, false);
+      if ((st = lbch_step(lbm, J.leap_steps)) != LBCH_OK || (st = lbch_get_phi_device(lbm, c->leap1)) != LBCH_OK)
+        return lbm_fail(st);
+      diff_norm_kernel<<<n_head, 256, 0, c->stream>>>(c->leap0, c->leap1, (long long)c->p.H * c->p.W, c->partial);
+      diff_norm_final<<<1, 32, 0, c->stream>>>(c->partial, n_head, dv + 6);
+      if ((st = lbch_step(lbm, lbm_steps)) != LBCH_OK || (st = lbch_mass_device(lbm, dv + 4)) != LBCH_OK ||
+          (st = lbch_free_energy_device(lbm, dv + 5)) != LBCH_OK)
+        return lbm_fail(st);
+      if (cuda_bad(c, cudaGetLastError(), "leap_run_judged: audit launch") ||
+          !fetch(4, 4, "leap_run_judged: read"))
+        return LBCH_ECUDA;
+      const double err = std::sqrt(hv[2] / hv[3]);
+      ++S.audits;
+      S.lbm_steps += J.leap_steps + lbm_steps;
+      if (std::isfinite(err) && err <= J.phi_rtol) {
+        ++S.accepted;
+      } else {
+        ++S.rejected;
+        ++S.rejected_audit;
+      }
+      if (std::isfinite(err) && err > S.max_audit_err) S.max_audit_err = err;
+      if (!std::isfinite(err)) S.max_audit_err = INFINITY;
+      m_before = hv[0];
+      e_before = hv[1];
+    } else {
+      if ((st = lbch_save_state_device(lbm, c->judge_state, c->judge_state_bytes)) != LBCH_OK ||
+          (st = lbch_get_phi_device(lbm, c->leap0)) != LBCH_OK)
+        return lbm_fail(st);
+      forward_impl(c, c->leap0, &alpha, 1, c->leap0, false);
+      if ((st = lbch_init_field_device(lbm, c->leap0)) != LBCH_OK || (st = lbch_mass_device(lbm, dv + 2)) != LBCH_OK ||
+          (st = lbch_free_energy_device(lbm, dv + 3)) != LBCH_OK || (st = lbch_step(lbm, lbm_steps)) != LBCH_OK ||
+          (st = lbch_mass_device(lbm, dv + 4)) != LBCH_OK || (st = lbch_free_energy_device(lbm, dv + 5)) != LBCH_OK)
+        return lbm_fail(st);
+      if (cuda_bad(c, cudaGetLastError(), "leap_run_judged: launch") || !fetch(2, 4, "leap_run_judged: read"))
+        return LBCH_ECUDA;
+      const double m_leap = hv[0], e_leap = hv[1], m_corr = hv[2], e_corr = hv[3];
+      const bool finite = std::isfinite(m_leap) && std::isfinite(e_leap) && std::isfinite(m_corr) &&
+                          std::isfinite(e_corr);
+      const double rise_leap = (e_leap - e_before) / std::fabs(e_before);
+      const double rise_corr = (e_corr - e_leap) / std::fabs(e_leap);
+      bool ok = finite;
+      if (!finite) {
+        ++S.rejected_nonfinite;
+      } else {
+        if (rise_leap > S.max_leap_rise) S.max_leap_rise = rise_leap;
+        if (rise_corr > S.max_corr_rise) S.max_corr_rise = rise_corr;
+        if (std::fabs(m_leap - m_before) > J.mass_atol * nodes) {
+          ok = false;
+          ++S.rejected_mass;
+        } else if (e_leap > e_before + J.energy_rtol * std::fabs(e_before) ||
+                   e_corr > e_leap + J.energy_rtol * std::fabs(e_leap)) {
+          ok = false;
+          ++S.rejected_energy;
+        }
+      }
+      if (ok) {
+        ++S.accepted;
+        S.lbm_steps += lbm_steps;
+        m_before = m_corr;
+        e_before = e_corr;
+      } else {
+        // the plain scheme over the same simulated time, from the saved state
+        ++S.rejected;
+        if ((st = lbch_restore_state_device(lbm, c->judge_state, c->judge_state_bytes)) != LBCH_OK ||
+            (st = lbch_step(lbm, J.leap_steps + lbm_steps)) != LBCH_OK ||
+            (st = lbch_mass_device(lbm, dv + 4)) != LBCH_OK || (st = lbch_free_energy_device(lbm, dv + 5)) != LBCH_OK)
+          return lbm_fail(st);
+        if (!fetch(4, 2, "leap_run_judged: read")) return LBCH_ECUDA;
+        S.lbm_steps += J.leap_steps + lbm_steps;
+        m_before = hv[0];
+        e_before = hv[1];
+      }
+    }
+    if ((st = lbch_set_steps_taken(lbm, t0 + (k + 1) * (J.leap_steps + lbm_steps))) != LBCH_OK) return lbm_fail(st);
+  }
+  if (stats) *stats = S;
+  return done(c, "leap_run_judged: launch");
 }
 
 static lbch_status op_check(int32_t B, int32_t H, int32_t W, int32_t ci, int32_t co) {

@@ -127,6 +127,16 @@ def load():
         lib.lbch_batch_get_phi_device.restype = ctypes.c_int
         lib.lbch_steps_taken.argtypes = [vp]
         lib.lbch_steps_taken.restype = ctypes.c_int64
+        lib.lbch_set_steps_taken.argtypes = [vp, ctypes.c_int64]
+        lib.lbch_set_steps_taken.restype = ctypes.c_int
+        for name in ("lbch_mass_device", "lbch_free_energy_device"):
+            getattr(lib, name).argtypes = [vp, vp]
+            getattr(lib, name).restype = ctypes.c_int
+        lib.lbch_state_bytes.argtypes = [P]
+        lib.lbch_state_bytes.restype = ctypes.c_size_t
+        for name in ("lbch_save_state_device", "lbch_restore_state_device"):
+            getattr(lib, name).argtypes = [vp, vp, ctypes.c_size_t]
+            getattr(lib, name).restype = ctypes.c_int
         lib.lbch_last_error.argtypes = [vp]
         lib.lbch_last_error.restype = ctypes.c_char_p
         lib.lbch_destroy.argtypes = [vp]
@@ -203,6 +213,13 @@ def _check_device_f32(t, n: int, what: str) -> None:
         raise ValueError(f"{what}: expected {n} values, got {t.numel()}")
 
 
+def _check_device_f64(t, what: str) -> None:
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.numel() >= 1):
+        raise ValueError(f"{what}: expected a float64 CUDA tensor")
+
+
 # ---------------------------------------------------------------- C-ABI, same names
 
 def lbch_workspace_bytes(p: lbch_params) -> int:
@@ -261,6 +278,32 @@ def lbch_set_state(ctx, f9: np.ndarray) -> None:
 
 def lbch_steps_taken(ctx) -> int:
     return int(load().lbch_steps_taken(ctx))
+
+
+def lbch_set_steps_taken(ctx, steps: int) -> None:
+    _check(ctx, load().lbch_set_steps_taken(ctx, int(steps)), "lbch_set_steps_taken")
+
+
+def lbch_mass_device(ctx, d_out: int) -> None:
+    _check(ctx, load().lbch_mass_device(ctx, ctypes.c_void_p(int(d_out))), "lbch_mass_device")
+
+
+def lbch_free_energy_device(ctx, d_out: int) -> None:
+    _check(ctx, load().lbch_free_energy_device(ctx, ctypes.c_void_p(int(d_out))), "lbch_free_energy_device")
+
+
+def lbch_state_bytes(p: lbch_params) -> int:
+    return int(load().lbch_state_bytes(ctypes.byref(p)))
+
+
+def lbch_save_state_device(ctx, d_dst: int, nbytes: int) -> None:
+    _check(ctx, load().lbch_save_state_device(ctx, ctypes.c_void_p(int(d_dst)), int(nbytes)),
+           "lbch_save_state_device")
+
+
+def lbch_restore_state_device(ctx, d_src: int, nbytes: int) -> None:
+    _check(ctx, load().lbch_restore_state_device(ctx, ctypes.c_void_p(int(d_src)), int(nbytes)),
+           "lbch_restore_state_device")
 
 
 def lbch_last_error(ctx) -> str:
@@ -364,6 +407,35 @@ class Solver:
         a = _as_host_f64(f9, 9 * self.nx * self.ny, "state")
         with self._on_device():
             lbch_set_state(self.ctx, a)
+
+    def mass_device(self, out) -> None:
+        """lbch_mass_device into out[0] (a float64 CUDA tensor), asynchronously."""
+        _check_device_f64(out, "out")
+        with self._on_device():
+            lbch_mass_device(self.ctx, out.data_ptr())
+
+    def free_energy_device(self, out) -> None:
+        """lbch_free_energy_device into out[0] (a float64 CUDA tensor), asynchronously."""
+        _check_device_f64(out, "out")
+        with self._on_device():
+            lbch_free_energy_device(self.ctx, out.data_ptr())
+
+    def save_state_device(self, out=None):
+        """Device-side checkpoint into a uint8 CUDA tensor of lbch_state_bytes (allocated if None)."""
+        import torch
+
+        nb = lbch_state_bytes(self.params)
+        if out is None:
+            out = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        if not (out.is_cuda and out.is_contiguous() and out.numel() * out.element_size() >= nb):
+            raise ValueError(f"out: expected a contiguous CUDA tensor of at least {nb} bytes")
+        with self._on_device():
+            lbch_save_state_device(self.ctx, out.data_ptr(), out.numel() * out.element_size())
+        return out
+
+    def restore_state_device(self, image) -> None:
+        with self._on_device():
+            lbch_restore_state_device(self.ctx, image.data_ptr(), image.numel() * image.element_size())
 
     @property
     def steps_taken(self) -> int:

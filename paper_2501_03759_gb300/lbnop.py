@@ -18,6 +18,28 @@ class lbnop_params(ctypes.Structure):
                 ("scale", ctypes.c_double)]
 
 
+class lbnop_judge(ctypes.Structure):
+    _fields_ = [("leap_steps", ctypes.c_int64), ("energy_rtol", ctypes.c_double), ("mass_atol", ctypes.c_double),
+                ("audit_every", ctypes.c_int64), ("phi_rtol", ctypes.c_double)]
+
+
+class lbnop_judge_stats(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("rejected_nonfinite", ctypes.c_int64), ("rejected_mass", ctypes.c_int64),
+                ("rejected_energy", ctypes.c_int64), ("rejected_audit", ctypes.c_int64),
+                ("audits", ctypes.c_int64), ("lbm_steps", ctypes.c_int64),
+                ("max_audit_err", ctypes.c_double), ("max_leap_rise", ctypes.c_double),
+                ("max_corr_rise", ctypes.c_double)]
+
+
+def make_judge(leap_steps: int = 500, energy_rtol: float = 1e-4, mass_atol: float = 1e-6, audit_every: int = 0,
+               phi_rtol: float = 1e-2) -> lbnop_judge:
+    j = lbnop_judge()
+    j.leap_steps, j.energy_rtol, j.mass_atol = int(leap_steps), float(energy_rtol), float(mass_atol)
+    j.audit_every, j.phi_rtol = int(audit_every), float(phi_rtol)
+    return j
+
+
 def make_params(H: int, W: int, max_batch: int = 1, scale: float = 0.05) -> lbnop_params:
     p = lbnop_params()
     p.H, p.W, p.max_batch, p.scale = int(H), int(W), int(max_batch), float(scale)
@@ -61,6 +83,9 @@ def load():
         lib.lbnop_train_step.restype = ctypes.c_int
         lib.lbnop_leap_run.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64]
         lib.lbnop_leap_run.restype = ctypes.c_int
+        lib.lbnop_leap_run_judged.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.POINTER(lbnop_judge), ctypes.POINTER(lbnop_judge_stats)]
+        lib.lbnop_leap_run_judged.restype = ctypes.c_int
         for name in ("lbnop_conv3x3_bwd_data", "lbnop_conv3x3_bwd_weight"):
             getattr(lib, name).argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp]
             getattr(lib, name).restype = ctypes.c_int
@@ -166,6 +191,14 @@ def lbnop_train_step(ctx, d_phi: int, alpha, d_target: int, batch: int, lr: floa
 
 def lbnop_leap_run(ctx, lbm_ctx, alpha: float, cycles: int, lbm_steps: int) -> None:
     _check(ctx, load().lbnop_leap_run(ctx, lbm_ctx, float(alpha), int(cycles), int(lbm_steps)), "lbnop_leap_run")
+
+
+def lbnop_leap_run_judged(ctx, lbm_ctx, alpha: float, cycles: int, lbm_steps: int, judge: lbnop_judge) -> dict:
+    """Runs the judged leap cycles; returns the judge's counts as a dict."""
+    st = lbnop_judge_stats()
+    _check(ctx, load().lbnop_leap_run_judged(ctx, lbm_ctx, float(alpha), int(cycles), int(lbm_steps),
+                                             ctypes.byref(judge), ctypes.byref(st)), "lbnop_leap_run_judged")
+    return {name: getattr(st, name) for name, _ in lbnop_judge_stats._fields_}
 
 
 def lbnop_conv3x3(d_x: int, d_w: int, d_bias: int | None, B: int, H: int, W: int, c_in: int, c_out: int,
@@ -282,6 +315,17 @@ class Surrogate:
             raise ValueError("solver and surrogate must share a CUDA stream")
         with self._on():
             lbnop_leap_run(self.ctx, solver.ctx, alpha, cycles, lbm_steps)
+
+    def leap_run_judged(self, solver, alpha: float, cycles: int, lbm_steps: int, judge=None) -> dict:
+        """leap_run with the plain scheme as judge and fallback (lbnop_leap_run_judged); returns
+        the judge's counts. judge: an lbnop_judge (default make_judge())."""
+        if solver.nx != self.W or solver.ny != self.H:
+            raise ValueError("solver grid must match the surrogate's H x W")
+        if solver.stream.cuda_stream != self.stream.cuda_stream:
+            raise ValueError("solver and surrogate must share a CUDA stream")
+        with self._on():
+            return lbnop_leap_run_judged(self.ctx, solver.ctx, alpha, cycles, lbm_steps,
+                                         make_judge() if judge is None else judge)
 
     def close(self) -> None:
         if getattr(self, "ctx", None):

@@ -164,11 +164,20 @@ def train(data, alphas, iters: int, batch: int = 16, lr: float = 1e-3, lr_end: f
     return theta, log
 
 
+# The online judge of the leap runs (lbnop_leap_run_judged): a leap, or the correction steps
+# after it, may raise the free energy by at most 1e-4 of |E| (the size of the rises between
+# samples that the small-noise spinodal shows at alpha > 0, where Eq. 15 is not the exact
+# gradient flow), and may move the mass by at most 1e-6 per node.
+JUDGE = dict(energy_rtol=1e-4, mass_atol=1e-6)
+
+
 def evaluate(theta, alpha: float, seed: int, n: int = 512, cycles: int = 90, leap: int = LEAP, corr: int = CORR,
-             warmup: int = WARMUP):
+             warmup: int = WARMUP, judged: bool = True, audit_every: int = 0, phi_rtol: float = 1e-2):
     """Plain LBM versus (warmup LBM steps, then cycles of one leap and corr LBM steps) from
     the same held-out field, to T = warmup + cycles (leap + corr) steps (50000 by default).
-    Returns the gates and timings."""
+    With judged=True every leap is checked on the device by the plain scheme's mass and
+    energy (and every audit_every-th against K plain steps) and replaced by plain steps if it
+    fails. Returns the gates, the judge's counts and timings."""
     import torch
 
     steps = warmup + cycles * (leap + corr)
@@ -180,8 +189,16 @@ def evaluate(theta, alpha: float, seed: int, n: int = 512, cycles: int = 90, lea
     # warm-up (kernels loaded, clocks up), then timed runs from fresh initial states
     plain.init_field(phi0)
     plain.step(200)
+    judge = lbnop.make_judge(leap_steps=leap, audit_every=audit_every, phi_rtol=phi_rtol, **JUDGE)
+
+    def run_leaps(k):
+        if judged:
+            return s.leap_run_judged(lept, alpha, k, corr, judge)
+        s.leap_run(lept, alpha, k, corr)
+        return None
+
     lept.init_field(phi0)
-    s.leap_run(lept, alpha, 2, corr)
+    run_leaps(2)
     plain.init_field(phi0)
     lept.init_field(phi0)
     m0 = plain.mass()
@@ -191,7 +208,7 @@ def evaluate(theta, alpha: float, seed: int, n: int = 512, cycles: int = 90, lea
     plain.step(steps)
     ev[1].record(s.stream)
     lept.step(warmup)
-    s.leap_run(lept, alpha, cycles, corr)
+    stats = run_leaps(cycles)
     ev[2].record(s.stream)
     torch.cuda.synchronize()
     t_plain = ev[0].elapsed_time(ev[1]) / 1e3
@@ -209,6 +226,7 @@ def evaluate(theta, alpha: float, seed: int, n: int = 512, cycles: int = 90, lea
         "mass_drift_abs": float(abs(m_leap - m0)),
         "seconds_plain": t_plain, "seconds_leap": t_leap, "speedup": t_plain / t_leap,
         "phi_rms_plain": float(np.sqrt(np.mean(a * a))),
+        "judge": stats, "steps_taken": lept.steps_taken,
     }
     plain.close()
     lept.close()

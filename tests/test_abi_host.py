@@ -24,7 +24,7 @@ def declared_functions():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names.update(re.findall(r"\b(lbch_[a-z0-9_]+)\s*\(", text))
+        names.update(re.findall(r"\b((?:lbch|lbch3|lbnop)_[a-z0-9_]+)\s*\(", text))
     return sorted(names)
 
 
@@ -94,3 +94,40 @@ def test_explicit_s35_validated(lib):
     assert lbch.lbch_workspace_bytes(p) > 0  # s_3 comes from M
     q = lbch.make_params(16, 16, s=[1, 1, 1, 0.0, 1, 1, 1, 1, 1], flags=lbch.S35_EXPLICIT)
     assert lbch.lbch_workspace_bytes(q) == 0
+
+
+def test_declarations_cover_all_three_headers():
+    names = declared_functions()
+    for required in ("lbch3_create", "lbch3_step", "lbnop_forward", "lbnop_leap_run", "lbnop_leap_run_judged",
+                     "lbch_mass_device", "lbch_free_energy_device", "lbch_save_state_device",
+                     "lbch_restore_state_device", "lbch_set_steps_taken", "lbch_state_bytes"):
+        assert required in names
+
+
+def test_state_bytes_match_storage(lib):
+    n = 100 * 60
+    ps = (n + 63) // 64 * 64
+    assert lbch.lbch_state_bytes(lbch.make_params(100, 60)) >= 9 * 4 * ps
+    for st in (lbch.STORE_BF16_DEV, lbch.STORE_F16_DEV):
+        b = lbch.lbch_state_bytes(lbch.make_params(100, 60, storage=st))
+        assert 2 * 4 * ps + 8 * 2 * ps <= b < 9 * 4 * ps
+    assert lbch.lbch_state_bytes(lbch.make_params(0, 60)) == 0
+
+
+def test_new_calls_reject_null_context(lib):
+    assert lib.lbch_set_steps_taken(None, 5) == lbch.EINVAL
+    assert lib.lbch_mass_device(None, None) == lbch.EINVAL
+    assert lib.lbch_free_energy_device(None, None) == lbch.EINVAL
+    assert lib.lbch_save_state_device(None, None, 0) == lbch.EINVAL
+    assert lib.lbch_restore_state_device(None, None, 0) == lbch.EINVAL
+
+
+def test_judge_struct_layout():
+    from paper_2501_03759_gb300 import lbnop
+
+    lbnop.load()
+    assert ctypes.sizeof(lbnop.lbnop_judge) == 5 * 8
+    assert ctypes.sizeof(lbnop.lbnop_judge_stats) == 11 * 8
+    assert lbnop.lbnop_judge_stats.max_audit_err.offset == 8 * 8
+    j = lbnop.make_judge()
+    assert lbch.load().lbnop_leap_run_judged(None, None, 0.3, 1, 50, ctypes.byref(j), None) == lbch.EINVAL

@@ -323,3 +323,98 @@ def test_network_backward_large_batch_matches_oracle():
     print(f"backward large: worst per-layer gradient rel L2 {worst:.2e}")
     assert worst <= 2e-2
     s.close()
+
+
+# ---------------------------------------------------------------- the plain scheme as judge and fallback
+
+def _judged_pair(n, alpha, theta, scale, warm=100):
+    s = lbnop.Surrogate(n, n, max_batch=1, scale=scale)
+    s.set_params(theta)
+    a = lbch.Solver(lbch.make_params(n, n, alpha=alpha), stream=s.stream)
+    b = lbch.Solver(lbch.make_params(n, n, alpha=alpha), stream=s.stream)
+    phi0 = W.noise(n, n, 0.05, 12)
+    a.init_field(phi0)
+    b.init_field(phi0)
+    a.step(warm)
+    b.step(warm)
+    return s, a, b
+
+
+def test_judged_leap_rejects_bad_weights_and_equals_plain_scheme():
+    """A network of random weights with a large output scale adds noise of the field's own
+    size: the free energy (Eq. 7) rises across every leap, the judge rejects each one, and
+    the run is then the plain scheme over the same steps, bit for bit."""
+    n, alpha, cycles, K, corr = 64, 0.3, 4, 100, 20
+    s, a, b = _judged_pair(n, alpha, W.surrogate_theta(3, out_scale=0.5), scale=1.0)
+    judge = lbnop.make_judge(leap_steps=K, energy_rtol=1e-6, mass_atol=1e-6)
+    st = s.leap_run_judged(a, alpha, cycles, corr, judge)
+    b.step(cycles * (K + corr))
+    assert st["rejected"] == cycles and st["accepted"] == 0
+    assert st["rejected_energy"] == cycles
+    assert st["max_leap_rise"] > 1e-3
+    assert st["lbm_steps"] == cycles * (K + corr)
+    assert a.steps_taken == 100 + cycles * (K + corr)
+    assert np.array_equal(a.state(), b.state())
+    for o in (a, b, s):
+        o.close()
+
+
+def test_judged_leap_accepts_good_leaps_like_the_unjudged_run():
+    """With tolerances no leap can fail (a loose energy bound), every leap is accepted and the
+    judged run equals lbnop_leap_run bit for bit: saving the state and reading mass and energy
+    change nothing. The step counter keeps the simulated time."""
+    n, alpha, cycles, corr = 64, 0.3, 3, 10
+    s, a, b = _judged_pair(n, alpha, W.surrogate_theta(9, out_scale=0.5), scale=0.05)
+    judge = lbnop.make_judge(leap_steps=500, energy_rtol=1e3, mass_atol=1.0)
+    st = s.leap_run_judged(a, alpha, cycles, corr, judge)
+    s.leap_run(b, alpha, cycles, corr)
+    assert st["accepted"] == cycles and st["rejected"] == 0 and st["audits"] == 0
+    assert st["lbm_steps"] == cycles * corr
+    assert a.steps_taken == 100 + cycles * (500 + corr)
+    assert np.array_equal(a.state(), b.state())
+    for o in (a, b, s):
+        o.close()
+
+
+def test_judged_leap_audits_continue_from_the_plain_scheme():
+    """audit_every = 1: each cycle runs the plain K steps beside the leap and continues from
+    the plain state, so the run is the plain scheme bit for bit; each audit measures the
+    leap's phi error (here of random weights, so phi_rtol = 0 rejects every audited leap)."""
+    n, alpha, cycles, K, corr = 64, 0.2, 3, 60, 15
+    s, a, b = _judged_pair(n, alpha, W.surrogate_theta(5, out_scale=0.5), scale=0.05)
+    judge = lbnop.make_judge(leap_steps=K, energy_rtol=1e-6, audit_every=1, phi_rtol=0.0)
+    st = s.leap_run_judged(a, alpha, cycles, corr, judge)
+    b.step(cycles * (K + corr))
+    assert st["audits"] == cycles and st["rejected_audit"] == cycles
+    assert 0.0 < st["max_audit_err"] < 1.0
+    assert np.array_equal(a.state(), b.state())
+    # phi_rtol = 1: the same audits pass
+    s2, c, _ = _judged_pair(n, alpha, W.surrogate_theta(5, out_scale=0.5), scale=0.05)
+    st2 = s2.leap_run_judged(c, alpha, cycles, corr, lbnop.make_judge(leap_steps=K, audit_every=1, phi_rtol=1.0))
+    assert st2["accepted"] == cycles and st2["max_audit_err"] == st["max_audit_err"]
+    for o in (a, b, s, c, s2):
+        o.close()
+
+
+@pytest.mark.parametrize("storage", [lbch.STORE_F32, lbch.STORE_BF16_DEV])
+def test_device_checkpoint_and_device_diagnostics(storage):
+    """lbch_save_state_device / lbch_restore_state_device give back the same continuation bit
+    for bit; lbch_mass_device / lbch_free_energy_device equal the synchronous calls."""
+    n = 48
+    a = lbch.Solver(lbch.make_params(n, n, alpha=0.3, storage=storage))
+    a.init_field(W.droplet_workload(n))
+    a.step(13)
+    img = a.save_state_device()
+    a.step(21)
+    want = a.state()
+    m = torch.zeros(2, dtype=torch.float64, device="cuda")
+    a.mass_device(m[0:1])
+    a.free_energy_device(m[1:2])
+    assert m[0].item() == a.mass() and m[1].item() == a.free_energy()
+    a.restore_state_device(img)
+    assert a.steps_taken == 34  # restore leaves the counter as it is
+    a.step(21)
+    assert np.array_equal(a.state(), want)
+    with pytest.raises(lbch.LbchError):
+        a.restore_state_device(img[:16])
+    a.close()
