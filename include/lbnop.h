@@ -180,6 +180,13 @@ lbch_status lbnop_conv3x3_bwd_data(const uint16_t* d_dy, const uint16_t* d_w, in
 lbch_status lbnop_conv3x3_bwd_weight(const uint16_t* d_x, const uint16_t* d_dy, int32_t B, int32_t H, int32_t W,
                                      int32_t c_in, int32_t c_out, float* d_dw, void* cuda_stream);
 
+/* Number of convolutions this process has run on the tcgen05 tensor-core path (operands
+ * staged by TMA, FP32 accumulators in tensor memory) since the library was loaded. That path
+ * takes every convolution whose rows are a multiple of 128 pixels long (H a multiple of 4,
+ * one input tensor); the others run on mma.sync kernels. A diagnostic for tests and
+ * benchmarks. */
+int64_t lbnop_tc_launches(void);
+
 const char* lbnop_last_error(const lbnop_ctx* c);
 void lbnop_destroy(lbnop_ctx* c);
 

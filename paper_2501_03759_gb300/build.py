@@ -12,7 +12,7 @@ LIB = os.path.join(HERE, "liblbch.so")
 CSRC = os.path.join(HERE, "csrc")
 SOURCES = [os.path.join(CSRC, "lbch_api.cu"), os.path.join(CSRC, "lbnop.cu")]
 DEPENDS = SOURCES + [os.path.join(CSRC, n) for n in
-                     ("lbch_step.cuh", "lbch_aux.cuh", "lbch_lattice.cuh", "lbch_batch.cuh", "lbch3.cuh")] + [
+                     ("lbch_step.cuh", "lbch_aux.cuh", "lbch_lattice.cuh", "lbch_f2.cuh", "lbch_batch.cuh", "lbch3.cuh", "lbnop_tc.cuh")] + [
     os.path.join(ROOT, "include", n) for n in ("lbch.h", "lbch3.h", "lbnop.h")]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -25,6 +25,7 @@
 // adds with constant +-1/+-2 entries.
 #pragma once
 
+#include "lbch_f2.cuh"
 #include "lbch_lattice.cuh"
 
 namespace lbch {
@@ -81,18 +82,17 @@ __device__ __forceinline__ int imod(int v, int n) {
   return r < 0 ? r + n : r;
 }
 
-// Left/right neighbour sums and differences of a per-column quantity over the strip.
-__device__ __forceinline__ void neighbours(const float (&q)[4], float (&s)[4], float (&d)[4]) {
-  const float left = __shfl_up_sync(FULL, q[3], 1);
-  const float right = __shfl_down_sync(FULL, q[0], 1);
-  s[0] = left + q[1];
-  d[0] = q[1] - left;
-  s[1] = q[0] + q[2];
-  d[1] = q[2] - q[0];
-  s[2] = q[1] + q[3];
-  d[2] = q[3] - q[1];
-  s[3] = q[2] + right;
-  d[3] = right - q[2];
+// Left/right neighbour sums and differences of a per-column quantity over the strip:
+// s_j = q_{j-1} + q_{j+1}, d_j = q_{j+1} - q_{j-1} for this lane's columns j = 0..3 (pairs
+// (0, 1) and (2, 3)), with the outer neighbours from the adjacent lanes.
+__device__ __forceinline__ void neighbours(const F2 (&q)[2], F2 (&s)[2], F2 (&d)[2]) {
+  const float left = __shfl_up_sync(FULL, q[1].y, 1);
+  const float right = __shfl_down_sync(FULL, q[0].x, 1);
+  const F2 A = f2(left, q[0].x), B = f2(q[0].y, q[1].x), C = f2(q[1].y, right);
+  s[0] = A + B;
+  s[1] = B + C;
+  d[0] = B - A;
+  d[1] = C - B;
 }
 
 // Per-lane addressing of the strip.
@@ -162,48 +162,53 @@ __device__ __forceinline__ void issue_row(const Field& fd, float4* slot, int lan
 #undef LBCH_RO
 }
 
+// Pull shift along x of a per-column quantity of the strip: column j takes column j - 1
+// (c_x = 1) or column j + 1 (c_x = -1).
+__device__ __forceinline__ void from_left(F2 (&v)[2]) {
+  const float prev = __shfl_up_sync(FULL, v[1].y, 1);
+  v[1] = f2(v[0].y, v[1].x);
+  v[0] = f2(prev, v[0].x);
+}
+__device__ __forceinline__ void from_right(F2 (&v)[2]) {
+  const float next = __shfl_down_sync(FULL, v[0].x, 1);
+  v[0] = f2(v[0].y, v[1].x);
+  v[1] = f2(v[1].y, next);
+}
+
+__device__ __forceinline__ void to_pairs(const float4 t, F2 (&v)[2]) {
+  v[0] = f2(t.x, t.y);
+  v[1] = f2(t.z, t.w);
+}
+
 // f_in,I at this lane's 4 columns from a landed slot.
 template <int ST, bool VEC, int I>
-__device__ __forceinline__ void read_row(const float4* slot, int lane, float (&v)[4]) {
+__device__ __forceinline__ void read_row(const float4* slot, int lane, F2 (&v)[2]) {
   constexpr bool REBUILD = VEC && ST != ST_F32 && I != 0;
   if constexpr (!REBUILD) {
-    const float4 t = slot[I * 32 + lane];
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    to_pairs(slot[I * 32 + lane], v);
   } else {  // deviations of the source nodes (row r - c_Iy), shifted below
     const uint2 raw = reinterpret_cast<const uint2*>(slot + 64)[(I - 1) * 32 + lane];
-    v[0] = Dev<ST>::load(static_cast<uint16_t>(raw.x & 0xffffu));
-    v[1] = Dev<ST>::load(static_cast<uint16_t>(raw.x >> 16));
-    v[2] = Dev<ST>::load(static_cast<uint16_t>(raw.y & 0xffffu));
-    v[3] = Dev<ST>::load(static_cast<uint16_t>(raw.y >> 16));
+    Dev<ST>::raw2(raw.x, v[0].x, v[0].y);
+    Dev<ST>::raw2(raw.y, v[1].x, v[1].y);
+    if constexpr (Dev<ST>::UNSCALE != 1.0f) {
+      v[0] = splat(Dev<ST>::UNSCALE) * v[0];
+      v[1] = splat(Dev<ST>::UNSCALE) * v[1];
+    }
   }
   if constexpr (VEC) {  // the pull shift along x happens here, one shuffle per plane
-    if constexpr (cx(I) == 1) {  // take the column to the left
-      const float prev = __shfl_up_sync(FULL, v[3], 1);
-      v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
-    } else if constexpr (cx(I) == -1) {  // take the column to the right
-      const float next = __shfl_down_sync(FULL, v[0], 1);
-      v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
+    if constexpr (cx(I) == 1) {
+      from_left(v);
+    } else if constexpr (cx(I) == -1) {
+      from_right(v);
     }
   }
   if constexpr (REBUILD) {  // f*_I(y - c_I) = w_I anchor(y) + d_I(y - c_I)
-    const float w = (float)wgt(I);
-    const float4 m = slot[32 + lane];
-    v[0] = fmaf(w, m.x, v[0]);
-    v[1] = fmaf(w, m.y, v[1]);
-    v[2] = fmaf(w, m.z, v[2]);
-    v[3] = fmaf(w, m.w, v[3]);
+    const F2 w = splat((float)wgt(I));
+    F2 m[2];
+    to_pairs(slot[32 + lane], m);
+    v[0] = fma2(w, m[0], v[0]);
+    v[1] = fma2(w, m[1], v[1]);
   }
-}
-
-// Pull shift along x of a per-column quantity of the strip: column j takes column j - 1
-// (c_x = 1) or column j + 1 (c_x = -1).
-__device__ __forceinline__ void from_left(float (&v)[4]) {
-  const float prev = __shfl_up_sync(FULL, v[3], 1);
-  v[3] = v[2]; v[2] = v[1]; v[1] = v[0]; v[0] = prev;
-}
-__device__ __forceinline__ void from_right(float (&v)[4]) {
-  const float next = __shfl_down_sync(FULL, v[0], 1);
-  v[0] = v[1]; v[1] = v[2]; v[2] = v[3]; v[3] = next;
 }
 
 // Grouped deviation sums of a landed DEV row at this lane's 4 columns, pulled along x, in
@@ -215,27 +220,27 @@ __device__ __forceinline__ void from_right(float (&v)[4]) {
 // w_1..w_8 sum to 5/9, and the anchor terms cancel in j_x and j_y, so
 //   phi = f*_0 + (5/9) anchor + (gp + gm + g0),  j_x = gp - gm,  j_y = hp + hm + h0.
 struct DevSums {
-  float gp[4], gm[4], g0[4], hp[4], hm[4], h0[4];
+  F2 gp[2], gm[2], g0[2], hp[2], hm[2], h0[2];
 };
 template <int ST, bool H>
 __device__ __forceinline__ void dev_sums(const float4* slot, int lane, DevSums& s) {
   const uint2* ds = reinterpret_cast<const uint2*>(slot + 64);
-  float d[9][4];
+  F2 d[9][2];
 #pragma unroll
   for (int i = 1; i < 9; ++i) {
     const uint2 raw = ds[(i - 1) * 32 + lane];
-    Dev<ST>::raw2(raw.x, d[i][0], d[i][1]);
-    Dev<ST>::raw2(raw.y, d[i][2], d[i][3]);
+    Dev<ST>::raw2(raw.x, d[i][0].x, d[i][0].y);
+    Dev<ST>::raw2(raw.y, d[i][1].x, d[i][1].y);
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    s.gp[j] = (d[1][j] + d[5][j]) + d[8][j];
-    s.gm[j] = (d[3][j] + d[6][j]) + d[7][j];
-    s.g0[j] = d[2][j] + d[4][j];
+  for (int k = 0; k < 2; ++k) {
+    s.gp[k] = (d[1][k] + d[5][k]) + d[8][k];
+    s.gm[k] = (d[3][k] + d[6][k]) + d[7][k];
+    s.g0[k] = d[2][k] + d[4][k];
     if constexpr (H) {
-      s.hp[j] = d[5][j] - d[8][j];
-      s.hm[j] = d[6][j] - d[7][j];
-      s.h0[j] = d[2][j] - d[4][j];
+      s.hp[k] = d[5][k] - d[8][k];
+      s.hm[k] = d[6][k] - d[7][k];
+      s.h0[k] = d[2][k] - d[4][k];
     }
   }
   from_left(s.gp);
@@ -246,41 +251,48 @@ __device__ __forceinline__ void dev_sums(const float4* slot, int lane, DevSums& 
   }
 }
 
-// phi at column j of a landed DEV row from its rest population, anchor and group sums.
+// phi at this lane's columns of a landed DEV row from its rest population, anchor and
+// group sums.
 template <int ST>
-__device__ __forceinline__ float dev_phi(const float4* slot, int lane, const DevSums& s, int j) {
-  const float4 r = slot[lane], m = slot[32 + lane];
-  const float rest = j == 0 ? r.x : (j == 1 ? r.y : (j == 2 ? r.z : r.w));
-  const float anc = j == 0 ? m.x : (j == 1 ? m.y : (j == 2 ? m.z : m.w));
-  return fmaf(5.0f / 9.0f, anc, rest) + Dev<ST>::UNSCALE * ((s.gp[j] + s.gm[j]) + s.g0[j]);
+__device__ __forceinline__ void dev_phi(const float4* slot, int lane, const DevSums& s, F2 (&ph)[2]) {
+  F2 rest[2], anc[2];
+  to_pairs(slot[lane], rest);
+  to_pairs(slot[32 + lane], anc);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    F2 g = (s.gp[k] + s.gm[k]) + s.g0[k];
+    if constexpr (Dev<ST>::UNSCALE != 1.0f) g = splat(Dev<ST>::UNSCALE) * g;
+    ph[k] = fma2(splat(5.0f / 9.0f), anc[k], rest[k]) + g;
+  }
 }
 
-// Pointwise part at one node: Q (Eq. 15 reading), w, mu_alpha (Eq. 16) and the
-// local part A of mu_beta (Eq. 13 minus Eq. 16's mu_alpha).
-__device__ __forceinline__ void pointwise(const StepArgs& a, const Field& fd, float phi, float dx, float dy,
-                                          float lap, float& Qx, float& Qy, float& w, float& A,
-                                          float& mua) {
-  const float g2 = fmaf(dx, dx, dy * dy);
-  const bool ok = g2 >= 1e-12f;  // n = 0, gamma = 1 below this
-  const float rs = rsqrtf(ok ? g2 : 1.0f);
-  const float n1 = dx * rs, n2 = dy * rs;  // Eq. 2
-  const float n1s = n1 * n1, n2s = n2 * n2;
-  const float S4 = fmaf(n1s, n1s, n2s * n2s);
-  const float gm1 = ok ? fd.alpha * fmaf(4.0f, S4, -3.0f) : 0.0f;  // gamma - 1, Eq. 6
+// Pointwise part at two nodes: Q (Eq. 15 reading), w, mu_alpha (Eq. 16) and the local part A
+// of mu_beta (Eq. 13 minus Eq. 16's mu_alpha).
+__device__ __forceinline__ void pointwise(const StepArgs& a, const Field& fd, F2 phi, F2 dx, F2 dy, F2 lap,
+                                          F2& Qx, F2& Qy, F2& w, F2& A, F2& mua) {
+  const F2 g2 = fma2(dx, dx, dy * dy);
+  const bool okx = g2.x >= 1e-12f, oky = g2.y >= 1e-12f;  // n = 0, gamma = 1 below this
+  const F2 rs = f2(rsqrtf(okx ? g2.x : 1.0f), rsqrtf(oky ? g2.y : 1.0f));
+  const F2 n1 = dx * rs, n2 = dy * rs;  // Eq. 2
+  const F2 n1s = n1 * n1, n2s = n2 * n2;
+  const F2 S4 = fma2(n1s, n1s, n2s * n2s);
+  F2 gm1 = splat(fd.alpha) * fma2(splat(4.0f), S4, splat(-3.0f));  // gamma - 1, Eq. 6
   // k_q |grad phi| P grad_n gamma with grad_n gamma = 16 alpha n^3, P = I - n n^T.
-  const float t = ok ? a.kq * fd.a16 * (g2 * rs) : 0.0f;
-  const float kg = fmaf(a.k, gm1, a.kiso);
-  Qx = fmaf(kg, dx, t * (n1 * (n1s - S4)));
-  Qy = fmaf(kg, dy, t * (n2 * (n2s - S4)));
-  const float phi2 = phi * phi;
-  const float fb = a.beta4 * phi * (phi2 - 1.0f);  // f = F'(phi), Eq. 9
-  const float fp = fmaf(a.beta12, phi2, -a.beta4); // f'(phi), Eq. 13
-  w = fmaf(-a.cw, fb, lap);
-  mua = fmaf(-a.k, lap, fb);
-  A = fmaf(gm1, fb, fmaf(-a.cfp * fp, w, a.cnk * lap));
+  F2 t = splat(a.kq * fd.a16) * (g2 * rs);
+  if (!okx) gm1.x = t.x = 0.0f;
+  if (!oky) gm1.y = t.y = 0.0f;
+  const F2 kg = fma2(splat(a.k), gm1, splat(a.kiso));
+  Qx = fma2(kg, dx, t * (n1 * (n1s - S4)));
+  Qy = fma2(kg, dy, t * (n2 * (n2s - S4)));
+  const F2 phi2 = phi * phi;
+  const F2 fb = (splat(a.beta4) * phi) * (phi2 - splat(1.0f));  // f = F'(phi), Eq. 9
+  const F2 fp = fma2(splat(a.beta12), phi2, splat(-a.beta4));   // f'(phi), Eq. 13
+  w = fma2(splat(-a.cw), fb, lap);
+  mua = fma2(splat(-a.k), lap, fb);
+  A = fma2(gm1, fb, fma2(splat(-a.cfp) * fp, w, splat(a.cnk) * lap));
 }
 
-// Eq. 17 at one node in moment space (Eqs. 23, 25) with the closed forms
+// Eq. 17 at two nodes in moment space (Eqs. 23, 25) with the closed forms
 // m^eq = (phi, -4 phi + 2 mu_a, 4 phi - 3 mu_a, 0, ...) and
 // M F = (0, 0, 0, -g_x/3, g_x/3, -g_y/3, g_y/3, 0, 0), and M^-1 = M^T diag(1/|row|^2).
 // FAST: s_1 = s_2 = s_4 = s_6 = s_7 = s_8 = 1, so those moments take their (forced)
@@ -288,23 +300,23 @@ __device__ __forceinline__ void pointwise(const StepArgs& a, const Field& fd, fl
 // (1 - s_k) m_k terms are then exactly zero.
 // FAST collision from the three moments it needs, phi = m_0, j_x = m_3 and j_y = m_5 (the
 // others take their equilibrium): o[1..8] of f*; o[0] is left to the caller.
-__device__ __forceinline__ void collide_fast(const StepArgs& a, float phi, float m3, float m5, float mua, float gx,
-                                             float gy, float (&o)[9]) {
-  const float n0 = phi * (1.0f / 9.0f);
-  const float n1 = a.c1b * fmaf(2.0f, mua, -4.0f * phi);
-  const float n2 = a.c2b * fmaf(-3.0f, mua, 4.0f * phi);
-  const float n4 = a.c4g * gx, n6 = a.c6g * gy;
-  const float n3 = fmaf(a.c3a, m3, a.c3g * gx);
-  const float n5 = fmaf(a.c5a, m5, a.c5g * gy);
-  const float A0 = fmaf(-2.0f, n2, n0 - n1);
-  const float X = fmaf(-2.0f, n4, n3), Y = fmaf(-2.0f, n6, n5);
+__device__ __forceinline__ void collide_fast(const StepArgs& a, F2 phi, F2 m3, F2 m5, F2 mua, F2 gx, F2 gy,
+                                             F2 (&o)[9]) {
+  const F2 n0 = phi * splat(1.0f / 9.0f);
+  const F2 n1 = splat(a.c1b) * fma2(splat(2.0f), mua, splat(-4.0f) * phi);
+  const F2 n2 = splat(a.c2b) * fma2(splat(-3.0f), mua, splat(4.0f) * phi);
+  const F2 n4 = splat(a.c4g) * gx, n6 = splat(a.c6g) * gy;
+  const F2 n3 = fma2(splat(a.c3a), m3, splat(a.c3g) * gx);
+  const F2 n5 = fma2(splat(a.c5a), m5, splat(a.c5g) * gy);
+  const F2 A0 = fma2(splat(-2.0f), n2, n0 - n1);
+  const F2 X = fma2(splat(-2.0f), n4, n3), Y = fma2(splat(-2.0f), n6, n5);
   o[1] = A0 + X;
   o[3] = A0 - X;
   o[2] = A0 + Y;
   o[4] = A0 - Y;
-  const float D0 = fmaf(2.0f, n1, n0 + n2);
-  const float U = n3 + n4, V = n5 + n6;
-  const float P = U + V, Mv = U - V;
+  const F2 D0 = fma2(splat(2.0f), n1, n0 + n2);
+  const F2 U = n3 + n4, V = n5 + n6;
+  const F2 P = U + V, Mv = U - V;
   o[5] = D0 + P;
   o[7] = D0 - P;
   o[6] = D0 - Mv;
@@ -312,44 +324,44 @@ __device__ __forceinline__ void collide_fast(const StepArgs& a, float phi, float
 }
 
 template <bool FAST>
-__device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], float mua,
-                                        float gx, float gy, float (&o)[9], float& phi_out) {
-  const float ab = f[1] + f[3], bb = f[2] + f[4];
-  const float Sa = ab + bb;
-  const float e = f[5] + f[7], h = f[6] + f[8];
-  const float Sd = e + h;
-  const float phi = f[0] + Sa + Sd;
-  const float x1 = f[1] - f[3], y1 = f[2] - f[4];
-  const float p = f[5] - f[7], q = f[6] - f[8];
-  const float pm = p - q, pp = p + q;
-  const float m3 = x1 + pm, m5 = y1 + pp;
+__device__ __forceinline__ void collide(const StepArgs& a, const F2 (&f)[9], F2 mua, F2 gx, F2 gy, F2 (&o)[9],
+                                        F2& phi_out) {
+  const F2 ab = f[1] + f[3], bb = f[2] + f[4];
+  const F2 Sa = ab + bb;
+  const F2 e = f[5] + f[7], h = f[6] + f[8];
+  const F2 Sd = e + h;
+  const F2 phi = (f[0] + Sa) + Sd;
+  const F2 x1 = f[1] - f[3], y1 = f[2] - f[4];
+  const F2 p = f[5] - f[7], q = f[6] - f[8];
+  const F2 pm = p - q, pp = p + q;
+  const F2 m3 = x1 + pm, m5 = y1 + pp;
   if constexpr (FAST) {
     collide_fast(a, phi, m3, m5, mua, gx, gy, o);
   } else {
-    const float n0 = phi * (1.0f / 9.0f);
-    const float m1 = fmaf(-4.0f, f[0], fmaf(2.0f, Sd, -Sa));
-    const float m2 = fmaf(4.0f, f[0], fmaf(-2.0f, Sa, Sd));
-    const float m4 = fmaf(-2.0f, x1, pm), m6 = fmaf(-2.0f, y1, pp);
-    const float m7 = ab - bb, m8 = e - h;
-    const float n1 = fmaf(a.c1a, m1, a.c1b * fmaf(2.0f, mua, -4.0f * phi));
-    const float n2 = fmaf(a.c2a, m2, a.c2b * fmaf(-3.0f, mua, 4.0f * phi));
-    const float n4 = fmaf(a.c4a, m4, a.c4g * gx);
-    const float n6 = fmaf(a.c6a, m6, a.c6g * gy);
-    const float n7 = a.c7 * m7;
-    const float n8 = a.c8 * m8;
-    const float n3 = fmaf(a.c3a, m3, a.c3g * gx);
-    const float n5 = fmaf(a.c5a, m5, a.c5g * gy);
-    const float A0 = fmaf(-2.0f, n2, n0 - n1);
-    const float B = A0 + n7, C = A0 - n7;
-    const float X = fmaf(-2.0f, n4, n3), Y = fmaf(-2.0f, n6, n5);
+    const F2 n0 = phi * splat(1.0f / 9.0f);
+    const F2 m1 = fma2(splat(-4.0f), f[0], fma2(splat(2.0f), Sd, splat(0.0f) - Sa));
+    const F2 m2 = fma2(splat(4.0f), f[0], fma2(splat(-2.0f), Sa, Sd));
+    const F2 m4 = fma2(splat(-2.0f), x1, pm), m6 = fma2(splat(-2.0f), y1, pp);
+    const F2 m7 = ab - bb, m8 = e - h;
+    const F2 n1 = fma2(splat(a.c1a), m1, splat(a.c1b) * fma2(splat(2.0f), mua, splat(-4.0f) * phi));
+    const F2 n2 = fma2(splat(a.c2a), m2, splat(a.c2b) * fma2(splat(-3.0f), mua, splat(4.0f) * phi));
+    const F2 n4 = fma2(splat(a.c4a), m4, splat(a.c4g) * gx);
+    const F2 n6 = fma2(splat(a.c6a), m6, splat(a.c6g) * gy);
+    const F2 n7 = splat(a.c7) * m7;
+    const F2 n8 = splat(a.c8) * m8;
+    const F2 n3 = fma2(splat(a.c3a), m3, splat(a.c3g) * gx);
+    const F2 n5 = fma2(splat(a.c5a), m5, splat(a.c5g) * gy);
+    const F2 A0 = fma2(splat(-2.0f), n2, n0 - n1);
+    const F2 B = A0 + n7, C = A0 - n7;
+    const F2 X = fma2(splat(-2.0f), n4, n3), Y = fma2(splat(-2.0f), n6, n5);
     o[1] = B + X;
     o[3] = B - X;
     o[2] = C + Y;
     o[4] = C - Y;
-    const float D0 = fmaf(2.0f, n1, n0 + n2);
-    const float E = D0 + n8, G = D0 - n8;
-    const float U = n3 + n4, V = n5 + n6;
-    const float P = U + V, Mv = U - V;
+    const F2 D0 = fma2(splat(2.0f), n1, n0 + n2);
+    const F2 E = D0 + n8, G = D0 - n8;
+    const F2 U = n3 + n4, V = n5 + n6;
+    const F2 P = U + V, Mv = U - V;
     o[5] = E + P;
     o[7] = E - P;
     o[6] = G - Mv;
@@ -365,94 +377,82 @@ __device__ __forceinline__ void collide(const StepArgs& a, const float (&f)[9], 
   phi_out = phi;
 }
 
+__device__ __forceinline__ void unpair(const F2 (&v)[2], float (&s)[4]) {
+  s[0] = v[0].x;
+  s[1] = v[0].y;
+  s[2] = v[1].x;
+  s[3] = v[1].y;
+}
+
 // Stores one collided row. DEV storage keeps the rest population and this node's
 // anchor in FP32 and d_i = f*_i - w_i anchor(x + c_i) in 16 bits; the rest population
 // is closed on the values a reader will rebuild, so sum_i f*_i = phi holds (mass is
-// conserved to FP32 rounding, not 16-bit rounding). dmu[i-1][j] is the anchor of the
-// node population i of column j streams to.
-template <int ST, bool VEC>
-__device__ __forceinline__ void store_row(const Field& fd, long long ro, long long col,
-                                          const float (&o)[9][4], const float (&mua)[4],
-                                          const float (&dmu)[8][4], const float (&phi)[4]) {
+// conserved to FP32 rounding, not 16-bit rounding). dmu[i-1] is the anchor of the node
+// population i streams to, at this lane's columns.
+template <int ST>
+__device__ __forceinline__ void store_row_vec(const Field& fd, long long ro, long long col, const F2 (&o)[9][2],
+                                              const F2 (&mua)[2], const F2 (&dmu)[8][2], const F2 (&phi)[2]) {
   if constexpr (ST == ST_F32) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      float* p = fd.dst.f32 + (long long)i * fd.ps + ro + col;
-      if constexpr (VEC) {
-        *reinterpret_cast<float4*>(p) = make_float4(o[i][0], o[i][1], o[i][2], o[i][3]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) p[j] = o[i][j];
-      }
-    }
+    for (int i = 0; i < 9; ++i)
+      *reinterpret_cast<float4*>(fd.dst.f32 + (long long)i * fd.ps + ro + col) =
+          make_float4(o[i][0].x, o[i][0].y, o[i][1].x, o[i][1].y);
   } else {
     using D = Dev<ST>;
     // Columns (0, 1) and (2, 3) of each plane round in one conversion; f*_i as its reader
     // rebuilds it (anchor term plus the stored deviation) closes the rest population.
-    float rest[4], sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    F2 sum[2];
     uint32_t pk[8][2];
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
-      const float w = (float)wgt(i);
-      float dv[4], back[4];
+      const F2 w = splat((float)wgt(i)), nw = splat(-(float)wgt(i));
 #pragma unroll
-      for (int j = 0; j < 4; ++j) dv[j] = o[i][j] - w * dmu[i - 1][j];
-      pk[i - 1][0] = D::pack2(dv[0], dv[1]);
-      pk[i - 1][1] = D::pack2(dv[2], dv[3]);
-      D::raw2(pk[i - 1][0], back[0], back[1]);
-      D::raw2(pk[i - 1][1], back[2], back[3]);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) sum[j] += fmaf(w, dmu[i - 1][j], back[j] * D::UNSCALE);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) rest[j] = phi[j] - sum[j];
-    float* p0 = fd.dst.f32 + ro + col;
-    float* pm = fd.dst.f32 + fd.ps + ro + col;
-    if constexpr (VEC) {
-      *reinterpret_cast<float4*>(p0) = make_float4(rest[0], rest[1], rest[2], rest[3]);
-      *reinterpret_cast<float4*>(pm) = make_float4(mua[0], mua[1], mua[2], mua[3]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        p0[j] = rest[j];
-        pm[j] = mua[j];
+      for (int k = 0; k < 2; ++k) {
+        const F2 dv = fma2(nw, dmu[i - 1][k], o[i][k]);
+        pk[i - 1][k] = D::pack2(dv.x, dv.y);
+        F2 back;
+        D::raw2(pk[i - 1][k], back.x, back.y);
+        if constexpr (D::UNSCALE != 1.0f) back = splat(D::UNSCALE) * back;
+        const F2 rb = fma2(w, dmu[i - 1][k], back);
+        sum[k] = i == 1 ? rb : sum[k] + rb;
       }
     }
+    const F2 rest0 = phi[0] - sum[0], rest1 = phi[1] - sum[1];
+    *reinterpret_cast<float4*>(fd.dst.f32 + ro + col) = make_float4(rest0.x, rest0.y, rest1.x, rest1.y);
+    *reinterpret_cast<float4*>(fd.dst.f32 + fd.ps + ro + col) = make_float4(mua[0].x, mua[0].y, mua[1].x, mua[1].y);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      uint16_t* pd = fd.dst.dev + (long long)i * fd.ps + ro + col;
-      if constexpr (VEC) {
-        *reinterpret_cast<uint2*>(pd) = make_uint2(pk[i][0], pk[i][1]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) pd[j] = static_cast<uint16_t>(pk[i][j >> 1] >> (16 * (j & 1)));
-      }
-    }
+    for (int i = 0; i < 8; ++i)
+      *reinterpret_cast<uint2*>(fd.dst.dev + (long long)i * fd.ps + ro + col) = make_uint2(pk[i][0], pk[i][1]);
   }
 }
 
-// Scalar-path store for columns that may be partly out of range (not 4-aligned grids).
+// Scalar-path store for columns that may be partly out of range (grids whose width is not a
+// multiple of 4): the first nvalid of the 4 columns at col0.
 template <int ST>
 __device__ __forceinline__ void store_row_masked(const Field& fd, long long ro, int col0, int nvalid,
-                                                 const float (&o)[9][4], const float (&mua)[4],
-                                                 const float (&dmu)[8][4], const float (&phi)[4]) {
-  if (nvalid >= 4) {
-    store_row<ST, false>(fd, ro, col0, o, mua, dmu, phi);
-    return;
-  }
-  // Fewer than 4 valid columns: write them one at a time.
-  if constexpr (ST == ST_F32) {
-    for (int j = 0; j < nvalid; ++j)
+                                                 const F2 (&o2)[9][2], const F2 (&mua2)[2],
+                                                 const F2 (&dmu2)[8][2], const F2 (&phi2)[2]) {
+  float o[9][4], mua[4], dmu[8][4], phi[4];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) fd.dst.f32[(long long)i * fd.ps + ro + col0 + j] = o[i][j];
+  for (int i = 0; i < 9; ++i) unpair(o2[i], o[i]);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) unpair(dmu2[i], dmu[i]);
+  unpair(mua2, mua);
+  unpair(phi2, phi);
+  if constexpr (ST == ST_F32) {
+    for (int j = 0; j < 4; ++j)
+      if (j < nvalid)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fd.dst.f32[(long long)i * fd.ps + ro + col0 + j] = o[i][j];
   } else {
     using D = Dev<ST>;
-    for (int j = 0; j < nvalid; ++j) {
+    for (int j = 0; j < 4; ++j) {
+      if (j >= nvalid) break;
       float sum = 0.0f;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
         const float w = (float)wgt(i);
-        const uint16_t d = D::store(o[i][j] - w * dmu[i - 1][j]);
+        const uint16_t d = D::store(fmaf(-w, dmu[i - 1][j], o[i][j]));
         sum += fmaf(w, dmu[i - 1][j], D::load(d));
         fd.dst.dev[(long long)(i - 1) * fd.ps + ro + col0 + j] = d;
       }
@@ -462,31 +462,38 @@ __device__ __forceinline__ void store_row_masked(const Field& fd, long long ro, 
   }
 }
 
+// 16-bit storages with the default rates cache phi, j_x and j_y of a landed row in its slot
+// (over the deviations, which nothing reads after that) when the row's phi is formed; the
+// collision three rows later reads them back instead of summing the deviations again.
+template <int ST, bool VEC, bool FAST>
+struct DevCache {
+  static constexpr bool ON = VEC && FAST && ST != ST_F32;
+};
+__device__ __forceinline__ F2* cache_of(float4* slot) { return reinterpret_cast<F2*>(slot + 64); }
+__device__ __forceinline__ const F2* cache_of(const float4* slot) { return reinterpret_cast<const F2*>(slot + 64); }
+
 // Collides row `row` of this warp's strip from its landing slot and stores it.
 // mu_m, mu_c, mu_p: mu_alpha of rows row-1, row, row+1 at this lane's columns.
 template <int ST, bool VEC, bool FAST>
 __device__ __forceinline__ void collide_row(const StepArgs& a, const Field& fd, const float4* slot, int lane,
-                                            int row,
-                                            bool store, int ocol0, int nvalid, const float (&mu_m)[4],
-                                            const float (&mu_c)[4], const float (&mu_p)[4],
-                                            const float (&gx)[4], const float (&gy)[4]) {
-  float o[9][4], phic[4];
-  if constexpr (VEC && FAST && ST != ST_F32) {  // phi, j_x and j_y straight from the deviations
-    DevSums ds;
-    dev_sums<ST, true>(slot, lane, ds);
+                                            int row, bool store, int ocol0, int nvalid, const F2 (&mu_m)[2],
+                                            const F2 (&mu_c)[2], const F2 (&mu_p)[2], const F2 (&gx)[2],
+                                            const F2 (&gy)[2]) {
+  F2 o[9][2], phic[2];
+  if constexpr (DevCache<ST, VEC, FAST>::ON) {  // phi, j_x and j_y cached when the row landed
+    const F2* cache = cache_of(slot);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float oj[9];
-      phic[j] = dev_phi<ST>(slot, lane, ds, j);
-      const float m3 = Dev<ST>::UNSCALE * (ds.gp[j] - ds.gm[j]);
-      const float m5 = Dev<ST>::UNSCALE * ((ds.hp[j] + ds.hm[j]) + ds.h0[j]);
-      collide_fast(a, phic[j], m3, m5, mu_c[j], gx[j], gy[j], oj);
-      o[0][j] = 0.0f;  // the DEV store closes the rest population from phi
+    for (int k = 0; k < 2; ++k) {
+      F2 oj[9];
+      phic[k] = cache[k * 32 + lane];
+      collide_fast(a, phic[k], cache[(2 + k) * 32 + lane], cache[(4 + k) * 32 + lane], mu_c[k], gx[k], gy[k],
+                   oj);
+      o[0][k] = splat(0.0f);  // the DEV store closes the rest population from phi
 #pragma unroll
-      for (int i = 1; i < 9; ++i) o[i][j] = oj[i];
+      for (int i = 1; i < 9; ++i) o[i][k] = oj[i];
     }
   } else {
-    float fr[9][4];
+    F2 fr[9][2];
     read_row<ST, VEC, 0>(slot, lane, fr[0]);
     read_row<ST, VEC, 1>(slot, lane, fr[1]);
     read_row<ST, VEC, 2>(slot, lane, fr[2]);
@@ -497,37 +504,38 @@ __device__ __forceinline__ void collide_row(const StepArgs& a, const Field& fd, 
     read_row<ST, VEC, 7>(slot, lane, fr[7]);
     read_row<ST, VEC, 8>(slot, lane, fr[8]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float f[9], oj[9];
+    for (int k = 0; k < 2; ++k) {
+      F2 f[9], oj[9];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) f[i] = fr[i][j];
-      collide<FAST>(a, f, mu_c[j], gx[j], gy[j], oj, phic[j]);
+      for (int i = 0; i < 9; ++i) f[i] = fr[i][k];
+      collide<FAST>(a, f, mu_c[k], gx[k], gy[k], oj, phic[k]);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) o[i][j] = oj[i];
+      for (int i = 0; i < 9; ++i) o[i][k] = oj[i];
     }
   }
-  float dmu[8][4];
+  F2 dmu[8][2];
   if constexpr (ST != ST_F32) {  // anchors of the destination nodes x + c_i
     float ext[3][6];             // rows row-1, row, row+1; columns -1 .. 4 of this lane
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float(&m)[4] = k == 0 ? mu_m : (k == 1 ? mu_c : mu_p);
-      ext[k][0] = __shfl_up_sync(FULL, m[3], 1);
-      ext[k][1] = m[0];
-      ext[k][2] = m[1];
-      ext[k][3] = m[2];
-      ext[k][4] = m[3];
-      ext[k][5] = __shfl_down_sync(FULL, m[0], 1);
+    for (int r = 0; r < 3; ++r) {
+      const F2(&m)[2] = r == 0 ? mu_m : (r == 1 ? mu_c : mu_p);
+      ext[r][0] = __shfl_up_sync(FULL, m[1].y, 1);
+      ext[r][1] = m[0].x;
+      ext[r][2] = m[0].y;
+      ext[r][3] = m[1].x;
+      ext[r][4] = m[1].y;
+      ext[r][5] = __shfl_down_sync(FULL, m[0].x, 1);
     }
 #pragma unroll
     for (int i = 1; i < 9; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) dmu[i - 1][j] = ext[1 + cy(i)][j + cx(i) + 1];
+      for (int k = 0; k < 2; ++k)
+        dmu[i - 1][k] = f2(ext[1 + cy(i)][2 * k + cx(i) + 1], ext[1 + cy(i)][2 * k + cx(i) + 2]);
   }
   if (store) {
     const long long ro = (long long)row * fd.nx;
     if constexpr (VEC) {
-      store_row<ST, true>(fd, ro, ocol0, o, mu_c, dmu, phic);
+      store_row_vec<ST>(fd, ro, ocol0, o, mu_c, dmu, phic);
     } else {
       store_row_masked<ST>(fd, ro, ocol0, nvalid, o, mu_c, dmu, phic);
     }
@@ -554,16 +562,17 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
   const bool lane_out = lane >= 1 && lane <= 30 && ocol0 < fd.nx;
   const int nvalid = min(4, fd.nx - ocol0);
 
-  // Rolling accumulators (see the header comment): index 1 = row completing next, 0 = row after.
-  float Ax1[4], Ay1[4], Al1[4], Ax0[4], Ay0[4], Al0[4], php[4];
-  float T1[4], T0[4];
-  float Gx1[4], Gy1[4], Gx0[4], Gy0[4];
-  float mu1[4], mu2[4], mu3[4];  // mu_alpha of rows r-2, r-3, r-4
+  // Rolling accumulators (see the header comment): index 1 = row completing next, 0 = row
+  // after; U and V hold the y-difference terms of the last two rows (phi and mu_beta).
+  F2 Ax1[2], Al1[2], Ax0[2], Al0[2], U1[2], U0[2], php[2];
+  F2 T1[2], T0[2];
+  F2 Gx1[2], Gx0[2], V1[2], V0[2];
+  F2 mu1[2], mu2[2], mu3[2];  // mu_alpha of rows r-2, r-3, r-4
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    Ax1[j] = Ay1[j] = Al1[j] = Ax0[j] = Ay0[j] = Al0[j] = php[j] = 0.0f;
-    T1[j] = T0[j] = Gx1[j] = Gy1[j] = Gx0[j] = Gy0[j] = 0.0f;
-    mu1[j] = mu2[j] = mu3[j] = 0.0f;
+  for (int k = 0; k < 2; ++k) {
+    Ax1[k] = Al1[k] = Ax0[k] = Al0[k] = U1[k] = U0[k] = php[k] = splat(0.0f);
+    T1[k] = T0[k] = Gx1[k] = Gx0[k] = V1[k] = V0[k] = splat(0.0f);
+    mu1[k] = mu2[k] = mu3[k] = splat(0.0f);
   }
 
   // phi rows y0-3 .. ; row y collides at phi row y + COLLIDE_LAG.
@@ -581,6 +590,9 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
     if (d < n_it) fetch_next(slots + d * SLOT_F4);
     cp_async_commit();
   }
+  const F2 K12 = splat(1.0f / 12.0f), K6 = splat(1.0f / 6.0f), K3 = splat(1.0f / 3.0f);
+  const F2 K23 = splat(2.0f / 3.0f), KM103 = splat(-10.0f / 3.0f), K4 = splat(4.0f);
+  const F2 EPS = splat(a.eps);
   int s_cur = 0, s_pf = PF_DIST, s_col = SLOTS - COLLIDE_LAG;  // slots of rows r, r+PF_DIST, r-LAG
   for (int it = 0; it < n_it; ++it) {
     // 1. Fetch row r + PF_DIST.
@@ -588,83 +600,97 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
     cp_async_commit();
     // 2. Wait for row r; pull it and sum phi (Eq. 22).
     cp_async_wait<PF_DIST>();
-    float ph[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    F2 ph[2];
     if constexpr (VEC && ST != ST_F32) {  // grouped: one shuffle per c_x group
-      const float4* slot = slots + s_cur * SLOT_F4;
+      float4* slot = slots + s_cur * SLOT_F4;
       DevSums ds;
-      dev_sums<ST, false>(slot, lane, ds);
+      dev_sums<ST, DevCache<ST, VEC, FAST>::ON>(slot, lane, ds);
+      dev_phi<ST>(slot, lane, ds, ph);
+      if constexpr (DevCache<ST, VEC, FAST>::ON) {
+        F2* cache = cache_of(slot);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) ph[j] = dev_phi<ST>(slot, lane, ds, j);
+        for (int k = 0; k < 2; ++k) {
+          F2 jx = ds.gp[k] - ds.gm[k], jy = (ds.hp[k] + ds.hm[k]) + ds.h0[k];
+          if constexpr (Dev<ST>::UNSCALE != 1.0f) {
+            jx = splat(Dev<ST>::UNSCALE) * jx;
+            jy = splat(Dev<ST>::UNSCALE) * jy;
+          }
+          cache[k * 32 + lane] = ph[k];
+          cache[(2 + k) * 32 + lane] = jx;
+          cache[(4 + k) * 32 + lane] = jy;
+        }
+      }
     } else {
       const float4* slot = slots + s_cur * SLOT_F4;
-      float v[4];
+      F2 v[2];
+      read_row<ST, VEC, 0>(slot, lane, ph);
 #define LBCH_PULL(I)                    \
   read_row<ST, VEC, I>(slot, lane, v); \
-  ph[0] += v[0]; ph[1] += v[1]; ph[2] += v[2]; ph[3] += v[3];
-      LBCH_PULL(0) LBCH_PULL(1) LBCH_PULL(2) LBCH_PULL(3) LBCH_PULL(4)
+  ph[0] = ph[0] + v[0];                \
+  ph[1] = ph[1] + v[1];
+      LBCH_PULL(1) LBCH_PULL(2) LBCH_PULL(3) LBCH_PULL(4)
       LBCH_PULL(5) LBCH_PULL(6) LBCH_PULL(7) LBCH_PULL(8)
 #undef LBCH_PULL
     }
     // 3. grad phi and lap phi of row r-1 (Eq. 26a, 26b), rolling over rows.
-    float dx[4], dy[4], lp[4];
+    F2 dx[2], dy[2], lp[2];
     {
-      float s[4], d[4];
+      F2 s[2], d[2];
       neighbours(ph, s, d);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float e = d[j] * (1.0f / 12.0f);
-        const float u = fmaf(s[j], 1.0f / 12.0f, ph[j] * (1.0f / 3.0f));
-        const float t = fmaf(s[j], 1.0f / 6.0f, ph[j] * (2.0f / 3.0f));
-        dx[j] = Ax1[j] + e;
-        dy[j] = Ay1[j] + u;
-        lp[j] = Al1[j] + t;
-        Ax1[j] = fmaf(4.0f, e, Ax0[j]);
-        Ay1[j] = Ay0[j];
-        Al1[j] = Al0[j] + fmaf(s[j], 2.0f / 3.0f, ph[j] * (-10.0f / 3.0f));
-        Ax0[j] = e;
-        Ay0[j] = -u;
-        Al0[j] = t;
+      for (int k = 0; k < 2; ++k) {
+        const F2 e = d[k] * K12;
+        const F2 u = fma2(s[k], K12, ph[k] * K3);
+        const F2 t = fma2(s[k], K6, ph[k] * K23);
+        dx[k] = Ax1[k] + e;
+        dy[k] = u - U1[k];
+        lp[k] = Al1[k] + t;
+        Ax1[k] = fma2(K4, e, Ax0[k]);
+        U1[k] = U0[k];
+        Al1[k] = Al0[k] + fma2(s[k], K23, ph[k] * KM103);
+        Ax0[k] = e;
+        U0[k] = u;
+        Al0[k] = t;
       }
     }
     // 4. Pointwise at row r-1.
-    float Qx[4], Qy[4], w[4], Aq[4], mun[4];
+    F2 Qx[2], Qy[2], w[2], Aq[2], mun[2];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) pointwise(a, fd, php[j], dx[j], dy[j], lp[j], Qx[j], Qy[j], w[j], Aq[j], mun[j]);
+    for (int k = 0; k < 2; ++k) pointwise(a, fd, php[k], dx[k], dy[k], lp[k], Qx[k], Qy[k], w[k], Aq[k], mun[k]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) php[j] = ph[j];
+    for (int k = 0; k < 2; ++k) php[k] = ph[k];
     // 5. mu_beta of row r-2: A - div Q + eps lap w (Eq. 26 on Q and w).
-    float mub[4];
+    F2 mub[2];
     {
-      float sx[4], dqx[4], sqy[4], dqy[4], sw[4], dw[4];
+      F2 sx[2], dqx[2], sqy[2], dqy[2], sw[2], dw[2];
       neighbours(Qx, sx, dqx);
       neighbours(Qy, sqy, dqy);
       neighbours(w, sw, dw);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float aa = dqx[j] * (1.0f / 12.0f);
-        const float bb = fmaf(sqy[j], 1.0f / 12.0f, Qy[j] * (1.0f / 3.0f));
-        const float cc = a.eps * fmaf(sw[j], 1.0f / 6.0f, w[j] * (2.0f / 3.0f));
-        mub[j] = T1[j] + (cc - aa - bb);
-        T1[j] = T0[j] + (fmaf(-4.0f, aa, Aq[j]) +
-                         a.eps * fmaf(sw[j], 2.0f / 3.0f, w[j] * (-10.0f / 3.0f)));
-        T0[j] = (bb - aa) + cc;
+      for (int k = 0; k < 2; ++k) {
+        const F2 aa = dqx[k] * K12;
+        const F2 bb = fma2(sqy[k], K12, Qy[k] * K3);
+        const F2 cc = EPS * fma2(sw[k], K6, w[k] * K23);
+        mub[k] = T1[k] + ((cc - aa) - bb);
+        T1[k] = T0[k] + fma2(EPS, fma2(sw[k], K23, w[k] * KM103), fma2(splat(-4.0f), aa, Aq[k]));
+        T0[k] = (bb - aa) + cc;
       }
     }
     // 6. grad mu_beta of row r-3 (Eq. 26a).
-    float gx[4], gy[4];
+    F2 gx[2], gy[2];
     {
-      float s[4], d[4];
+      F2 s[2], d[2];
       neighbours(mub, s, d);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float e = d[j] * (1.0f / 12.0f);
-        const float u = fmaf(s[j], 1.0f / 12.0f, mub[j] * (1.0f / 3.0f));
-        gx[j] = Gx1[j] + e;
-        gy[j] = Gy1[j] + u;
-        Gx1[j] = fmaf(4.0f, e, Gx0[j]);
-        Gy1[j] = Gy0[j];
-        Gx0[j] = e;
-        Gy0[j] = -u;
+      for (int k = 0; k < 2; ++k) {
+        const F2 e = d[k] * K12;
+        const F2 u = fma2(s[k], K12, mub[k] * K3);
+        gx[k] = Gx1[k] + e;
+        gy[k] = u - V1[k];
+        Gx1[k] = fma2(K4, e, Gx0[k]);
+        V1[k] = V0[k];
+        Gx0[k] = e;
+        V0[k] = u;
       }
     }
     // 7. Collide row r-3.
@@ -673,10 +699,10 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
       collide_row<ST, VEC, FAST>(a, fd, slots + s_col * SLOT_F4, lane, y0 + it - 6, lane_out, ocol0, nvalid, mu3,
                                  mu2, mu1, gx, gy);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      mu3[j] = mu2[j];
-      mu2[j] = mu1[j];
-      mu1[j] = mun[j];
+    for (int k = 0; k < 2; ++k) {
+      mu3[k] = mu2[k];
+      mu2[k] = mu1[k];
+      mu1[k] = mun[k];
     }
     s_cur = s_cur + 1 == SLOTS ? 0 : s_cur + 1;
     s_pf = s_pf + 1 == SLOTS ? 0 : s_pf + 1;
@@ -684,7 +710,6 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
   }
   cp_async_wait<0>();
 }
-
 
 // Single field: warp w takes strip w % n_strips of segment w / n_strips.
 template <int ST, bool VEC, bool FAST>

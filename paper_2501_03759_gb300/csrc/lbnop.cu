@@ -828,9 +828,19 @@ void launch_smem(const ConvArgs& a, dim3 grid, cudaStream_t s) {
   conv_smem_kernel<CI, CO, BN><<<grid, CONV_THREADS, bytes, s>>>(a);
 }
 
+}  // namespace nop
+
+#include "lbnop_tc.cuh"
+
+namespace nop {
+
 template <int CI, int CO, bool TW>
 void conv_t(const ConvArgs& a, cudaStream_t s) {
   const int npix = a.B * a.H * a.W;
+  // rows of 128 pixels or more: the tcgen05 path (operands by TMA, accumulators in TMEM)
+  if constexpr (!TW) {
+    if (tc_applies(a, CI, CO) && launch_tc<CI, CO>(a, nullptr, device_sms(), s)) return;
+  }
   const int tiles = (npix + 63) / 64;
   const long long want_warps = (long long)device_sms() * 16;  // below this, slice the channels
   if constexpr (TW) {  // the operator entry point on forward-layout weights (register-fed)
@@ -1724,6 +1734,8 @@ lbch_status lbnop_conv3x3_bwd_weight(const uint16_t* d_x, const uint16_t* d_dy, 
   wgrad_launch(c_in, c_out, a, s);
   return cudaGetLastError() == cudaSuccess ? LBCH_OK : LBCH_ECUDA;
 }
+
+int64_t lbnop_tc_launches(void) { return tc_counter().load(std::memory_order_relaxed); }
 
 const char* lbnop_last_error(const lbnop_ctx* c) { return c ? c->err : "context is NULL"; }
 

@@ -91,6 +91,8 @@ def load():
             getattr(lib, name).restype = ctypes.c_int
         lib.lbnop_conv3x3.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
         lib.lbnop_conv3x3.restype = ctypes.c_int
+        lib.lbnop_tc_launches.argtypes = []
+        lib.lbnop_tc_launches.restype = ctypes.c_int64
         lib.lbnop_last_error.argtypes = [vp]
         lib.lbnop_last_error.restype = ctypes.c_char_p
         lib.lbnop_destroy.argtypes = [vp]
@@ -221,6 +223,11 @@ def lbnop_conv3x3_bwd_weight(d_x: int, d_dy: int, B: int, H: int, W: int, c_in: 
     st = load().lbnop_conv3x3_bwd_weight(ctypes.c_void_p(int(d_x)), ctypes.c_void_p(int(d_dy)), B, H, W, c_in,
                                          c_out, ctypes.c_void_p(int(d_dw)), ctypes.c_void_p(int(cuda_stream or 0)))
     _check(None, st, "lbnop_conv3x3_bwd_weight")
+
+
+def lbnop_tc_launches() -> int:
+    """Convolutions run on the tcgen05 tensor-core path so far in this process."""
+    return int(load().lbnop_tc_launches())
 
 
 def lbnop_last_error(ctx) -> str:

@@ -325,6 +325,67 @@ def test_network_backward_large_batch_matches_oracle():
     s.close()
 
 
+# ---------------------------------------------------------------- the tcgen05 tensor-core path
+
+# Rows of 128 pixels (or a multiple) with H a multiple of 4 take the tcgen05 path: operands
+# staged by TMA, FP32 accumulators in tensor memory. The shapes cover 1, 2 and 4 output rows
+# per CTA (few, some and many rows), both ends of a row (periodic wrap in x) and of the field
+# (wrap in y), and rows of 256 pixels (two tiles per row).
+TC_SHAPES = [(1, 4, 128), (2, 8, 256), (3, 12, 128), (10, 128, 128)]
+
+
+@pytest.mark.parametrize("ci,co", [(96, 96), (96, 64), (64, 96), (64, 64), (96, 16), (16, 96), (16, 16), (64, 16)])
+@pytest.mark.parametrize("shape", TC_SHAPES)
+def test_conv_tc_forward(ci, co, shape):
+    B, H, Wd = shape
+    x = W.bf16_exact((B, H, Wd, ci), 21, 1.0)
+    w = W.bf16_exact((9, co, ci), 22, 0.25)
+    b = W.bf16_exact((co,), 23, 1.0).astype(np.float32)
+    y = torch.empty((B, H, Wd, co), dtype=torch.float32, device="cuda")
+    xd, wd, bt = dev_bf16(x), dev_bf16(w), torch.from_numpy(b).cuda()
+    before = lbnop.lbnop_tc_launches()
+    lbnop.lbnop_conv3x3(xd.data_ptr(), wd.data_ptr(), bt.data_ptr(), B, H, Wd, ci, co, y.data_ptr(), stream())
+    torch.cuda.synchronize()
+    assert lbnop.lbnop_tc_launches() == before + 1  # the tensor-core path ran
+    ref = N.conv(x, w, b)
+    scale = N.conv(np.abs(x), np.abs(w)).max() + 1.0
+    assert np.abs(y.cpu().numpy() - ref).max() <= 2e-7 * 9 * ci * scale / 64 + 1e-6
+
+
+def test_network_on_tensor_core_path_matches_oracle():
+    """A 512^2 field: its finest level (128 x 128) runs e0b, d0a and the output layer, and in
+    the backward pass their data gradients, on the tcgen05 path; forward and gradients against
+    the oracle with the same BF16 storage points, with the bounds of the mma.sync path."""
+    B, H, Wd = 1, 512, 512
+    theta, phi, target, alpha = network_case(B, H, Wd, seed=3)
+    scale = 0.05
+    s = lbnop.Surrogate(H, Wd, max_batch=B, scale=scale)
+    s.set_params(theta)
+    pd, td = torch.from_numpy(phi.astype(np.float32)).cuda(), torch.from_numpy(target.astype(np.float32)).cuda()
+    before = lbnop.lbnop_tc_launches()
+    out = s.forward(pd, alpha).cpu().numpy().astype(np.float64)
+    mid = lbnop.lbnop_tc_launches()
+    assert mid - before == 3  # e0b, d0a, out
+    loss = s.backward(pd, alpha, td)
+    assert lbnop.lbnop_tc_launches() - mid == 3 + 3  # forward again, then the data gradients of out, d0a, e0b
+    g = s.grads_host().astype(np.float64)
+    ref_q, saved = N.forward(theta, phi, alpha, scale, quantize=N.bf16)
+    e_q = rel_l2(out - phi, ref_q - phi)
+    loss_ref, dout = N.loss(ref_q, target)
+    g_ref = N.backward(theta, saved, dout, scale)
+    k, worst = 0, 0.0
+    for name, ci, co, _, _ in N.LAYERS:
+        n = 9 * co * ci + co + (co if name == "e0a" else 0)
+        worst = max(worst, rel_l2(g[k:k + n], g_ref[k:k + n]))
+        k += n
+    print(f"tensor-core network 512^2: update rel L2 {e_q:.2e}, loss {loss:.6e} (oracle {loss_ref:.6e}), "
+          f"worst gradient rel L2 {worst:.2e}")
+    assert e_q <= 1e-2
+    assert abs(loss - loss_ref) <= 1e-4 * loss_ref
+    assert worst <= 2e-2
+    s.close()
+
+
 # ---------------------------------------------------------------- the plain scheme as judge and fallback
 
 def _judged_pair(n, alpha, theta, scale, warm=100):
