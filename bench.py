@@ -507,7 +507,9 @@ def run_surrogate(alphas=(0.1, 0.3, 0.45), seed: int = 777):
                      "leap and across its 50 correction steps",
             "network": "96/64/96/96 channels, 826,096 parameters: wider than the configured 32 base "
                        "channels (~0.5M), which left the rollout error 2-4x above the gate",
-            "gates": gates, "by_alpha": runs, "speedup": min(r["speedup"] for r in runs)}
+            "gates": gates, "by_alpha": runs, "speedup": min(r["speedup"] for r in runs),
+            "kernels": surrogate.time_kernels(theta),
+            "conv_level0_b16": surrogate.time_conv(16)}
 
 
 def cpu_oracle_rate(target_s: float = 8.0, n_sample: int = 2048):

@@ -4,6 +4,7 @@ and check the leap/LBM alternation against the plain LBM.
   python -m paper_2501_03759_gb300.surrogate train --out DIR   # data + training, writes DIR/leap_theta.npy
   python -m paper_2501_03759_gb300.surrogate eval --theta FILE  # gates against a held-out plain run
   python -m paper_2501_03759_gb300.surrogate time --theta FILE  # device time of a forward and a step
+  python -m paper_2501_03759_gb300.surrogate conv               # device time of one 3x3 convolution
 
 Data: periodic n x n spinodal runs of the scheme (phi0 = U[-0.05, 0.05], seeded; alpha of
 Eq. 6 spread over [0, 0.5]; the other parameters of Eq. 39), stepped together by the
@@ -263,6 +264,39 @@ def time_kernels(theta, n: int = 512, batch: int = 16, reps: int = 20):
     return {"n": n, "forward_batch1_us": fwd, "train_step_us": step, "train_batch": batch}
 
 
+def time_conv(batch: int = 16, n0: int = 128, ci: int = 96, co: int = 96, reps: int = 20):
+    """Device time (CUDA events) and FP32-accumulated BF16 tensor throughput of one periodic
+    3 x 3 convolution of batch x n0 x n0 pixels, c_in -> c_out (the finest level of a 512^2
+    field at n0 = 128; rows of 128 pixels take the tcgen05 path). FLOPs: 2 * 9 * c_in * c_out per
+    pixel."""
+    import torch
+
+    r = np.random.default_rng(1)
+    x = torch.from_numpy(r.integers(-64, 65, (batch, n0, n0, ci)).astype(np.float32) / 64).cuda()
+    w = torch.from_numpy(r.integers(-64, 65, (9, co, ci)).astype(np.float32) / 256).cuda()
+    xb, wb = x.to(torch.bfloat16), w.to(torch.bfloat16)
+    y = torch.empty((batch, n0, n0, co), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    tc0 = lbnop.lbnop_tc_launches()
+
+    def run():
+        lbnop.lbnop_conv3x3(xb.data_ptr(), wb.data_ptr(), None, batch, n0, n0, ci, co, y.data_ptr(),
+                            stream.cuda_stream)
+
+    run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) / reps * 1e3
+    flop = 2.0 * 9 * ci * co * batch * n0 * n0
+    return {"batch": batch, "pixels": batch * n0 * n0, "c_in": ci, "c_out": co, "us": us,
+            "tflops": flop / us / 1e6, "tensor_core_path": lbnop.lbnop_tc_launches() > tc0}
+
+
 def main(argv=None):
     import torch
 
@@ -285,6 +319,12 @@ def main(argv=None):
     k = sub.add_parser("time")
     k.add_argument("--theta", required=True)
     k.add_argument("--reps", type=int, default=20)
+    cb = sub.add_parser("conv", help="time one 3x3 convolution (the tcgen05 path for rows of 128 pixels)")
+    cb.add_argument("--batch", type=int, default=16)
+    cb.add_argument("--n0", type=int, default=128)
+    cb.add_argument("--ci", type=int, default=96)
+    cb.add_argument("--co", type=int, default=96)
+    cb.add_argument("--reps", type=int, default=20)
     args = ap.parse_args(argv)
     torch.cuda.set_device(0)
     if args.cmd == "train":
@@ -308,6 +348,8 @@ def main(argv=None):
         del data
     elif args.cmd == "time":
         print(json.dumps(time_kernels(np.load(args.theta), reps=args.reps)))
+    elif args.cmd == "conv":
+        print(json.dumps(time_conv(args.batch, args.n0, args.ci, args.co, args.reps)))
     else:
         theta = np.load(args.theta)
         for a in args.alpha:
