@@ -43,7 +43,8 @@ INNER = 100  # lattice steps per benchmark step
 WORKLOAD = "spinodal-8192x8192"
 METRIC = "MLUPS (lattice-node updates/s, 1e6)"
 STEP_KERNEL_SOURCES = ("paper_2501_03759_gb300/csrc/lbch_step.cuh",
-                       "paper_2501_03759_gb300/csrc/lbch_lattice.cuh")
+                       "paper_2501_03759_gb300/csrc/lbch_lattice.cuh",
+                       "paper_2501_03759_gb300/csrc/lbch_f2.cuh")
 
 
 def parse():

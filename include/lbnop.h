@@ -119,6 +119,16 @@ lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_a
  * lbm_steps; lbnop_leap_run_judged checks every leap and keeps the simulated time. */
 lbch_status lbnop_leap_run(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cycles, int64_t lbm_steps);
 
+/* The leaps of lbnop_leap_run and lbnop_leap_run_judged average the network over `turns`
+ * quarter turns of the field: 1 (the default) runs the network alone; 4 runs it on the field
+ * turned by 0, 90, 180 and 270 degrees (one forward of four fields), turns each prediction
+ * back and takes the mean. The scheme commutes with the square's quarter turns (its
+ * velocities, weights, relaxation rates and gamma of Eq. 6 are invariant under them) and the
+ * network only approximately, so the mean is an estimate of the same step that is exactly
+ * equivariant; it costs one batch-4 forward per leap. Mass stays conserved (each prediction
+ * conserves it). 4 needs H = W and max_batch >= 4; LBCH_EINVAL otherwise. */
+lbch_status lbnop_set_leap_turns(lbnop_ctx* c, int32_t turns);
+
 /* The plain scheme as the judge of each leap in lbnop_leap_run_judged. */
 typedef struct {
   int64_t leap_steps;      /* K > 0: the lattice steps one leap stands for. A rejected leap is

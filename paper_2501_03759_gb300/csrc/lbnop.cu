@@ -749,6 +749,32 @@ __global__ void diff_norm_final(const double* __restrict__ partial, int blocks, 
   }
 }
 
+// The four quarter turns of an n x n field into out[k] (k = 0..3, n^2 values each), row i and
+// column j: turn_k(phi)[i][j] = phi[src_k(i, j)] with src_1 = (j, n-1-i), src_2 = (n-1-i,
+// n-1-j), src_3 = (n-1-j, i) (k = 1 a counter-clockwise quarter turn about the centre).
+__global__ void turns_kernel(const float* __restrict__ phi, int n, float* __restrict__ out) {
+  const long long nn = (long long)n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nn; idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+    out[idx] = phi[idx];
+    out[nn + idx] = phi[(long long)j * n + (n - 1 - i)];
+    out[2 * nn + idx] = phi[(long long)(n - 1 - i) * n + (n - 1 - j)];
+    out[3 * nn + idx] = phi[(long long)(n - 1 - j) * n + i];
+  }
+}
+// The mean of four predictions y[k] of the turned fields, each turned back (turn_{4-k}).
+__global__ void turns_back_kernel(const float* __restrict__ y, int n, float* __restrict__ out) {
+  const long long nn = (long long)n * n;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nn; idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx - (long long)i * n);
+    const float y0 = y[idx];
+    const float y1 = y[nn + (long long)(n - 1 - j) * n + i];
+    const float y2 = y[2 * nn + (long long)(n - 1 - i) * n + (n - 1 - j)];
+    const float y3 = y[3 * nn + (long long)j * n + (n - 1 - i)];
+    out[idx] = (((y0 + y1) + y2) + y3) * 0.25f;
+  }
+}
+
 // Adam (Kingma and Ba 2015, Algorithm 1; c1 = 1 / (1 - beta1^t), c2 = 1 / (1 - beta2^t)) on
 // the gradient scaled by min(1, clip / |grad|) when clip > 0 (global-norm clipping), then the
 // BF16 copies of every weight: wf[t][co][ci] and wb[t][ci][co] = W[8 - t][co][ci].
@@ -960,6 +986,7 @@ struct lbnop_ctx {
   float *leap0, *leap1;
   float* phi_out;  // [max_batch][H][W], the training forward's output
   int* flags;
+  int leap_turns;           // quarter turns a leap averages the network over (1 or 4)
   char* judge_state;        // saved lbch state of an H x W FP32 field (judged leap runs)
   size_t judge_state_bytes;
   double* judge_vals;       // 16 doubles: mass / energy readings and audit sums
@@ -1414,6 +1441,7 @@ lbch_status lbnop_create(const lbnop_params* p, void* d_workspace, size_t bytes,
   }
   c->adam_t = 0;
   c->last_batch = 0;
+  c->leap_turns = 1;
   c->failed = false;
   c->err[0] = 0;
   *out = c;
@@ -1545,6 +1573,35 @@ lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_a
   return LBCH_OK;
 }
 
+// One leap of the field in leap0, in place: the network, or the mean over the field's four
+// quarter turns of the network's predictions turned back (lbnop_set_leap_turns).
+static void leap_forward(lbnop_ctx* c, double alpha) {
+  if (c->leap_turns == 4) {
+    const int n = c->p.H;
+    const double a4[4] = {alpha, alpha, alpha, alpha};
+    turns_kernel<<<grid_for((long long)n * n, 256), 256, 0, c->stream>>>(c->leap0, n, c->phi_out);
+    forward_impl(c, c->phi_out, a4, 4, c->phi_out, false);
+    turns_back_kernel<<<grid_for((long long)n * n, 256), 256, 0, c->stream>>>(c->phi_out, n, c->leap0);
+  } else {
+    forward_impl(c, c->leap0, &alpha, 1, c->leap0, false);
+  }
+}
+
+lbch_status lbnop_set_leap_turns(lbnop_ctx* c, int32_t turns) {
+  lbch_status st = pre(c);
+  if (st != LBCH_OK) return st;
+  if (turns != 1 && turns != 4) {
+    set_err(c, "set_leap_turns: turns must be 1 or 4");
+    return LBCH_EINVAL;
+  }
+  if (turns == 4 && (c->p.H != c->p.W || c->p.max_batch < 4)) {
+    set_err(c, "set_leap_turns: 4 turns need a square field and max_batch >= 4");
+    return LBCH_EINVAL;
+  }
+  c->leap_turns = turns;
+  return LBCH_OK;
+}
+
 lbch_status lbnop_leap_run(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cycles, int64_t lbm_steps) {
   lbch_status st = pre(c);
   if (st != LBCH_OK) return st;
@@ -1554,7 +1611,7 @@ lbch_status lbnop_leap_run(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int64_t cy
       set_err(c, "leap_run: lbch_get_phi_device: %s", lbch_last_error(lbm));
       return st;
     }
-    forward_impl(c, c->leap0, &alpha, 1, c->leap0, false);
+    leap_forward(c, alpha);
     if ((st = lbch_init_field_device(lbm, c->leap0)) != LBCH_OK ||
         (st = lbch_step(lbm, lbm_steps)) != LBCH_OK) {
       set_err(c, "leap_run: %s", lbch_last_error(lbm));
@@ -1604,7 +1661,7 @@ lbch_status lbnop_leap_run_judged(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int
     if (audit) {
       // leap prediction in leap0, plain K steps from the untouched state into leap1
       if ((st = lbch_get_phi_device(lbm, c->leap0)) != LBCH_OK) return lbm_fail(st);
-      forward_impl(c, c->leap0, &alpha, 1, c->leap0, false);
+      leap_forward(c, alpha);
       if ((st = lbch_step(lbm, J.leap_steps)) != LBCH_OK || (st = lbch_get_phi_device(lbm, c->leap1)) != LBCH_OK)
         return lbm_fail(st);
       diff_norm_kernel<<<n_head, 256, 0, c->stream>>>(c->leap0, c->leap1, (long long)c->p.H * c->p.W, c->partial);
@@ -1632,7 +1689,7 @@ lbch_status lbnop_leap_run_judged(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int
       if ((st = lbch_save_state_device(lbm, c->judge_state, c->judge_state_bytes)) != LBCH_OK ||
           (st = lbch_get_phi_device(lbm, c->leap0)) != LBCH_OK)
         return lbm_fail(st);
-      forward_impl(c, c->leap0, &alpha, 1, c->leap0, false);
+      leap_forward(c, alpha);
       if ((st = lbch_init_field_device(lbm, c->leap0)) != LBCH_OK || (st = lbch_mass_device(lbm, dv + 2)) != LBCH_OK ||
           (st = lbch_free_energy_device(lbm, dv + 3)) != LBCH_OK || (st = lbch_step(lbm, lbm_steps)) != LBCH_OK ||
           (st = lbch_mass_device(lbm, dv + 4)) != LBCH_OK || (st = lbch_free_energy_device(lbm, dv + 5)) != LBCH_OK)

@@ -75,6 +75,8 @@ def load():
         lib.lbnop_backward.restype = ctypes.c_int
         lib.lbnop_adam.argtypes = [vp, ctypes.c_double]
         lib.lbnop_adam.restype = ctypes.c_int
+        lib.lbnop_set_leap_turns.argtypes = [vp, i32]
+        lib.lbnop_set_leap_turns.restype = ctypes.c_int
         lib.lbnop_set_clip.argtypes = [vp, ctypes.c_double]
         lib.lbnop_set_clip.restype = ctypes.c_int
         lib.lbnop_grad_norm.argtypes = [vp, dp]
@@ -173,6 +175,10 @@ def lbnop_adam(ctx, lr: float) -> None:
 
 def lbnop_set_clip(ctx, max_norm: float) -> None:
     _check(ctx, load().lbnop_set_clip(ctx, float(max_norm)), "lbnop_set_clip")
+
+
+def lbnop_set_leap_turns(ctx, turns: int) -> None:
+    _check(ctx, load().lbnop_set_leap_turns(ctx, int(turns)), "lbnop_set_leap_turns")
 
 
 def lbnop_grad_norm(ctx) -> float:
@@ -303,6 +309,10 @@ class Surrogate:
     def set_clip(self, max_norm: float) -> None:
         """Global-norm gradient clipping for the following Adam steps (0: off)."""
         lbnop_set_clip(self.ctx, max_norm)
+
+    def set_leap_turns(self, turns: int) -> None:
+        """Leaps average the network over 1 or 4 quarter turns of the field (lbnop_set_leap_turns)."""
+        lbnop_set_leap_turns(self.ctx, turns)
 
     def grad_norm(self) -> float:
         """L2 norm of the last backward's gradient, before clipping (synchronises)."""
