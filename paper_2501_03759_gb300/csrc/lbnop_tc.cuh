@@ -38,7 +38,7 @@ constexpr int TC_SLOTS = 130;                  // pixel slots per chunk block: x
 constexpr int TC_CHUNK_A = (TC_SLOTS + 1) * 16;  // bytes between chunk blocks of an input row
 constexpr int TC_THREADS = 128;                // four warps: one TMEM lane quarter each
 constexpr int TC_LOADERS = 96;                 // warps 1-3 copy weight taps
-constexpr int TC_BSTAGES = 3;
+constexpr int TC_MAX_BSTAGES = 4;
 constexpr unsigned TC_SPIN_LIMIT = 1u << 20;   // bounded mbarrier waits (about a second at most)
 
 // Set by a CTA whose wait gave up; every later CTA of the path then returns at once.
@@ -52,13 +52,19 @@ template <int CI, int CO>
 __host__ __device__ constexpr int tc_tap_bytes() { return (CI / 8) * tc_chunk_b<CO>(); }
 template <int CO>
 __host__ __device__ constexpr int tc_stage_pitch() { return CO + 4; }
+// Weight-ring stages: four where they fit beside the input rows in one CTA's shared memory
+// (more taps in flight hide the copy latency behind the MMAs), else three.
+template <int CI, int CO, int R>
+__host__ __device__ constexpr int tc_bstages() {
+  return (R + 2) * tc_row_bytes<CI>() + 4 * tc_tap_bytes<CI, CO>() + 512 <= 227 * 1024 ? 4 : 3;
+}
 template <int CI, int CO, int R>
 __host__ __device__ constexpr int tc_operand_bytes() {
-  return (R + 2) * tc_row_bytes<CI>() + TC_BSTAGES * tc_tap_bytes<CI, CO>();
+  return (R + 2) * tc_row_bytes<CI>() + tc_bstages<CI, CO, R>() * tc_tap_bytes<CI, CO>();
 }
 template <int CO>
 __host__ __device__ constexpr int tc_staged_bytes() { return 128 * tc_stage_pitch<CO>() * 4 + 2 * CO * 4; }
-// The operand buffers, reused for the staged output rows, then 7 mbarriers and the TMEM address.
+// The operand buffers, reused for the staged output rows, then 9 mbarriers and the TMEM address.
 template <int CI, int CO, int R>
 __host__ __device__ constexpr int tc_main_bytes() {
   return tc_operand_bytes<CI, CO, R>() > tc_staged_bytes<CO>() ? tc_operand_bytes<CI, CO, R>() : tc_staged_bytes<CO>();
@@ -204,15 +210,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
   constexpr uint32_t LBO_A = TC_CHUNK_A, LBO_B = tc_chunk_b<CO>(), SBO = 128;
   constexpr int COLS = tc_tmem_cols<CO, R>();
   constexpr uint32_t IDESC = umma_idesc_bf16<128, CO>();
+  constexpr int TC_BSTAGES = tc_bstages<CI, CO, R>();
   extern __shared__ __align__(128) unsigned char tc_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 127) & ~(uintptr_t)127);
   unsigned char* sA = base;
   unsigned char* sB = base + (R + 2) * ROW;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + tc_main_bytes<CI, CO, R>());  // b_full[3], b_empty[3], done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
-  const uint32_t done_bar = smem_u32(&bars[6]);
+  // b_full[stages], b_empty[stages], done (9 at most), then the TMEM address
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + tc_main_bytes<CI, CO, R>());
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_MAX_BSTAGES + 1);
+  const uint32_t done_bar = smem_u32(&bars[2 * TC_BSTAGES]);
   auto b_full = [&](int s) { return smem_u32(&bars[s]); };
-  auto b_empty = [&](int s) { return smem_u32(&bars[3 + s]); };
+  auto b_empty = [&](int s) { return smem_u32(&bars[TC_BSTAGES + s]); };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (*(volatile int*)&tc_fault_flag) return;  // an earlier CTA's wait gave up: do nothing
@@ -235,6 +243,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  // Warps 1-3 issue the first weight taps (one per stage) before the input rows, so that
+  // both sets of copies are in flight together; they arrive on the taps' barriers below.
+  auto copy_tap = [&](int t) {
+    const int s = t % TC_BSTAGES;
+    for (int idx = tid - 32; idx < CO * KC; idx += TC_LOADERS) {
+      const int n = idx / KC, c = idx - n * KC;
+      tc_cp16(smem_u32(sB + s * TAP + c * LBO_B + n * 16), p.w + ((size_t)t * CO + n) * CI + 8 * c);
+    }
+  };
+  if (warp != 0)
+    for (int t = 0; t < TC_BSTAGES; ++t) copy_tap(t);
   // The R + 2 input rows, by every thread: periodic in h and in x.
   for (int idx = tid; idx < (R + 2) * TC_SLOTS * KC; idx += TC_THREADS) {
     const int i = idx / (TC_SLOTS * KC), rem = idx - i * (TC_SLOTS * KC);
@@ -242,11 +261,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
     const int h = wrap1(h0 - 1 + i, p.H), x = wrap1(x0 - 1 + s, p.W);
     tc_cp16(smem_u32(sA + i * ROW + c * TC_CHUNK_A + s * 16), p.x + ((size_t)(b * p.H + h) * p.W + x) * CI + 8 * c);
   }
-  tc_cp_done();
+  tc_cp_done();  // this thread's input rows (and first taps) have landed
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  __syncthreads();  // after it: the barriers are initialised and every input row is in place
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  if (warp != 0)
+    for (int t = 0; t < TC_BSTAGES; ++t) mbar_arrive(b_full(t));
 
   bool ok = true;
   if (warp == 0) {
@@ -274,18 +295,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
       }
       umma_commit(done_bar);  // arrives once every MMA issued above has completed
     }
-  } else {  // warps 1-3: the weight taps, through the ring
-    const int lt = tid - 32;
-    for (int t = 0; t < 9; ++t) {
+  } else {  // warps 1-3: the remaining weight taps, each into the stage its tap - stages left
+    for (int t = TC_BSTAGES; t < 9; ++t) {
       const int s = t % TC_BSTAGES;
-      if (t >= TC_BSTAGES && !mbar_wait(b_empty(s), ((t - TC_BSTAGES) / TC_BSTAGES) & 1)) {
+      if (!mbar_wait(b_empty(s), ((t - TC_BSTAGES) / TC_BSTAGES) & 1)) {
         ok = false;
         break;
       }
-      for (int idx = lt; idx < CO * KC; idx += TC_LOADERS) {
-        const int n = idx / KC, c = idx - n * KC;
-        tc_cp16(smem_u32(sB + s * TAP + c * LBO_B + n * 16), p.w + ((size_t)t * CO + n) * CI + 8 * c);
-      }
+      copy_tap(t);
       tc_cp_done();
       mbar_arrive(b_full(s));
     }

@@ -35,6 +35,7 @@ CORR = 50         # LBM correction steps after each leap
 SCALE = 0.01      # phi_out = phi + SCALE sig (D - mean D), sig the field's rms
 T_END = 50000
 WARMUP = 500      # plain LBM steps before the first leap (the noise of phi0 decays first)
+TURNS = 4         # leaps average the network over the field's four quarter turns
 CLIP = 3.0        # training clips each gradient to CLIP x the median norm of recent steps
 CLIP_WINDOW = 200
 CLIP_START = 20
@@ -173,18 +174,21 @@ JUDGE = dict(energy_rtol=1e-4, mass_atol=1e-6)
 
 
 def evaluate(theta, alpha: float, seed: int, n: int = 512, cycles: int = 90, leap: int = LEAP, corr: int = CORR,
-             warmup: int = WARMUP, judged: bool = True, audit_every: int = 0, phi_rtol: float = 1e-2):
+             warmup: int = WARMUP, judged: bool = True, audit_every: int = 0, phi_rtol: float = 1e-2,
+             turns: int = TURNS):
     """Plain LBM versus (warmup LBM steps, then cycles of one leap and corr LBM steps) from
     the same held-out field, to T = warmup + cycles (leap + corr) steps (50000 by default).
     With judged=True every leap is checked on the device by the plain scheme's mass and
     energy (and every audit_every-th against K plain steps) and replaced by plain steps if it
-    fails. Returns the gates, the judge's counts and timings."""
+    fails. turns = 4 averages each leap over the field's four quarter turns
+    (lbnop_set_leap_turns). Returns the gates, the judge's counts and timings."""
     import torch
 
     steps = warmup + cycles * (leap + corr)
     phi0 = spinodal(n, seed)
-    s = lbnop.Surrogate(n, n, max_batch=1, scale=SCALE)
+    s = lbnop.Surrogate(n, n, max_batch=max(1, turns), scale=SCALE)
     s.set_params(theta)
+    s.set_leap_turns(turns)
     plain = lbch.Solver(lbch.make_params(n, n, alpha=alpha), stream=s.stream)
     lept = lbch.Solver(lbch.make_params(n, n, alpha=alpha), stream=s.stream)
     # warm-up (kernels loaded, clocks up), then timed runs from fresh initial states
@@ -227,7 +231,7 @@ def evaluate(theta, alpha: float, seed: int, n: int = 512, cycles: int = 90, lea
         "mass_drift_abs": float(abs(m_leap - m0)),
         "seconds_plain": t_plain, "seconds_leap": t_leap, "speedup": t_plain / t_leap,
         "phi_rms_plain": float(np.sqrt(np.mean(a * a))),
-        "judge": stats, "steps_taken": lept.steps_taken,
+        "judge": stats, "steps_taken": lept.steps_taken, "turns": turns,
     }
     plain.close()
     lept.close()
@@ -316,6 +320,7 @@ def main(argv=None):
     e.add_argument("--theta", required=True)
     e.add_argument("--alpha", type=float, nargs="+", default=[0.3])
     e.add_argument("--seed", type=int, default=777)
+    e.add_argument("--turns", type=int, default=TURNS, choices=[1, 4])
     k = sub.add_parser("time")
     k.add_argument("--theta", required=True)
     k.add_argument("--reps", type=int, default=20)
@@ -353,7 +358,7 @@ def main(argv=None):
     else:
         theta = np.load(args.theta)
         for a in args.alpha:
-            print(json.dumps(evaluate(theta, a, args.seed)))
+            print(json.dumps(evaluate(theta, a, args.seed, turns=args.turns)))
 
 
 if __name__ == "__main__":

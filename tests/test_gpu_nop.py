@@ -325,6 +325,35 @@ def test_network_backward_large_batch_matches_oracle():
     s.close()
 
 
+def test_leap_turns_average_the_turned_predictions():
+    """With 4 turns a leap is the mean of the network's predictions on the field turned by 0,
+    90, 180 and 270 degrees, each turned back (torch.rot90 as the independent route); mass
+    is conserved, and the result is exactly equivariant under a quarter turn of the input."""
+    n, alpha = 64, 0.3
+    s = lbnop.Surrogate(n, n, max_batch=4, scale=0.05)
+    s.set_params(W.surrogate_theta(9, out_scale=0.5))
+    s.set_leap_turns(4)
+    a = lbch.Solver(lbch.make_params(n, n, alpha=alpha), stream=s.stream)
+    phi0 = W.noise(n, n, 0.05, 5)
+    a.init_field(phi0)
+    phi = a.phi_device()
+    s.leap_run(a, alpha, 1, 0)
+    got = a.phi_device().cpu().numpy()
+    xs = torch.stack([torch.rot90(phi, k, (0, 1)) for k in range(4)]).contiguous()
+    ys = s.forward(xs, [alpha] * 4)
+    want = sum(torch.rot90(ys[k], -k, (0, 1)) for k in range(4)).cpu().numpy() * 0.25
+    assert np.abs(got - want).max() <= 1e-6 * np.abs(want).max()
+    assert abs(got.astype(np.float64).sum() - phi0.sum()) <= 1e-6 * np.abs(phi0).sum()
+    # equivariance: leaping the turned field gives the turned leap (each prediction of the four
+    # turns is one of the four of the original, so only the order of the sum differs)
+    b = lbch.Solver(lbch.make_params(n, n, alpha=alpha), stream=s.stream)
+    b.init_field(np.rot90(phi0).copy())
+    s.leap_run(b, alpha, 1, 0)
+    assert np.abs(b.phi_device().cpu().numpy() - np.rot90(got)).max() <= 1e-6 * np.abs(want).max()
+    for o in (a, b, s):
+        o.close()
+
+
 # ---------------------------------------------------------------- the tcgen05 tensor-core path
 
 # Rows of 128 pixels (or a multiple) with H a multiple of 4 take the tcgen05 path: operands

@@ -43,3 +43,21 @@ def test_d4_turns_form_the_square_group():
     assert len(seen) == 8
     assert torch.equal(d4(d4(x, 1, False), 3, False), x)
     assert torch.equal(d4(d4(x, 0, True), 0, True), x)
+
+
+def test_leap_turns_validated_on_the_host():
+    # lbnop_create only lays out the caller's workspace (no CUDA call), so a context on a
+    # placeholder address can check the setter's arguments without a GPU.
+    import ctypes
+
+    from paper_2501_03759_gb300 import lbch
+
+    lib = lbnop.load()
+    for (H, W, B), allowed in (((64, 64, 4), {1, 4}), ((64, 64, 1), {1}), ((64, 128, 4), {1})):
+        p = lbnop.make_params(H, W, B)
+        ctx = lbnop.lbnop_create(p, 1 << 20, lbnop.lbnop_workspace_bytes(p), 0)
+        for turns in (0, 1, 2, 3, 4, 8):
+            st = lib.lbnop_set_leap_turns(ctx, turns)
+            assert st == (lbch.OK if turns in allowed else lbch.EINVAL), (H, W, B, turns)
+        lbnop.lbnop_destroy(ctx)
+    assert lib.lbnop_set_leap_turns(None, 1) == lbch.EINVAL
