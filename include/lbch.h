@@ -150,6 +150,13 @@ lbch_status lbch_set_state(lbch_ctx* ctx, const double* h_f9);
 lbch_status lbch_mass_device(lbch_ctx* ctx, double* d_out);
 lbch_status lbch_free_energy_device(lbch_ctx* ctx, double* d_out);
 
+/* Mass and free energy of a field phi given in device memory (nx*ny FP32 values, x fastest),
+ * with this context's parameters, asynchronously: d_out2[0] = sum_x phi (FP64 sum of the
+ * FP32 values, Eq. 22), d_out2[1] = the discrete free energy of lbch_free_energy (Eq. 7 with
+ * G of Eq. 9 or Eq. 8; for the field lbch_get_phi_device writes, the same value bit for bit).
+ * One pass over the field; the state is not read and need not be set. */
+lbch_status lbch_field_diagnostics_device(lbch_ctx* ctx, const float* d_phi, double* d_out2);
+
 /* Bytes of one state (the population buffer a step reads) for these parameters; 0 if
  * they are invalid. */
 size_t lbch_state_bytes(const lbch_params* p);

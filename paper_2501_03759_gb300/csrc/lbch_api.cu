@@ -643,6 +643,25 @@ lbch_status lbch_free_energy_device(lbch_ctx* c, double* d_out) {
   return finish(c, "free_energy_device: launch");
 }
 
+lbch_status lbch_field_diagnostics_device(lbch_ctx* c, const float* d_phi, double* d_out2) {
+  lbch_status st = precheck(c, false);
+  if (st != LBCH_OK) return st;
+  if (!d_phi || !d_out2) return LBCH_EINVAL;
+  EnergyConsts ec;
+  const double eps = c->p.regularization == LBCH_REG_NONE ? 0.0 : c->p.eps;
+  ec.k = (float)c->k;
+  ec.beta = (float)c->beta;
+  ec.beta4 = (float)(4.0 * c->beta);
+  ec.alpha = (float)c->p.alpha;
+  ec.half_eps = (float)(0.5 * eps);
+  ec.cw = c->p.regularization == LBCH_REG_LINEAR ? 0.0f : 1.0f;
+  // mass partial sums in the second staging plane (nx ny doubles >= the block count)
+  field_diag_kernel<<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(d_phi, grid_of(c), ec, c->partial, c->stage1);
+  final_sum_kernel<<<1, 1024, 0, c->stream>>>(c->stage1, c->aux_blocks, d_out2);
+  final_sum_kernel<<<1, 1024, 0, c->stream>>>(c->partial, c->aux_blocks, d_out2 + 1);
+  return finish(c, "field_diagnostics_device: launch");
+}
+
 size_t lbch_state_bytes(const lbch_params* p) { return check_params(p) ? 0 : state_bytes(p); }
 
 lbch_status lbch_save_state_device(lbch_ctx* c, void* d_dst, size_t bytes) {

@@ -316,6 +316,50 @@ __global__ void energy_kernel(const float* __restrict__ phi, Grid g, EnergyConst
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
+// The energy densities of energy_kernel and, beside them, the FP64 sum of phi itself (mass,
+// Eq. 22), for a field given in FP32: partial_e[block] and partial_m[block].
+__global__ void field_diag_kernel(const float* __restrict__ phi, Grid g, EnergyConsts c,
+                                  double* __restrict__ partial_e, double* __restrict__ partial_m) {
+  __shared__ double sh[AUX_THREADS / 32];
+  double acc = 0.0, mass = 0.0;
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
+    const long long rm = (long long)(y == 0 ? g.ny - 1 : y - 1) * g.nx;
+    const long long r0 = (long long)y * g.nx;
+    const long long rp = (long long)(y + 1 == g.ny ? 0 : y + 1) * g.nx;
+    for (int x = threadIdx.x; x < g.nx; x += blockDim.x) {
+      const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 1 == g.nx ? 0 : x + 1;
+      const float p0 = phi[r0 + x];
+      const float E = phi[r0 + xp], Wv = phi[r0 + xm], N = phi[rp + x], S = phi[rm + x];
+      const float NE = phi[rp + xp], NW = phi[rp + xm], SW = phi[rm + xm], SE = phi[rm + xp];
+      const float gx = (E - Wv) * (1.0f / 3.0f) + ((NE - NW) + (SE - SW)) * (1.0f / 12.0f);
+      const float gy = (N - S) * (1.0f / 3.0f) + ((NE - SE) + (NW - SW)) * (1.0f / 12.0f);
+      const float lap = ((E + Wv) + (N + S)) * (2.0f / 3.0f) + ((NE + NW) + (SE + SW)) * (1.0f / 6.0f) -
+                        p0 * (10.0f / 3.0f);
+      const float g2 = fmaf(gx, gx, gy * gy);
+      float gamma = 1.0f;
+      if (g2 >= 1e-12f) {
+        const float rs = rsqrtf(g2);
+        const float n1 = gx * rs, n2 = gy * rs;
+        const float n1s = n1 * n1, n2s = n2 * n2;
+        gamma = fmaf(c.alpha, fmaf(4.0f, fmaf(n1s, n1s, n2s * n2s), -3.0f), 1.0f);
+      }
+      const float q = p0 * p0 - 1.0f;
+      const float F = c.beta * q * q;
+      const float wv = fmaf(-c.cw, c.beta4 * p0 * q, lap);
+      const float e = fmaf(gamma, fmaf(0.5f * c.k, g2, F), c.half_eps * wv * wv);
+      acc += (double)e;
+      mass += (double)p0;
+    }
+  }
+  acc = block_sum(acc, sh);
+  __syncthreads();  // warp 0 has read sh before the second sum reuses it
+  mass = block_sum(mass, sh);
+  if (threadIdx.x == 0) {
+    partial_e[blockIdx.x] = acc;
+    partial_m[blockIdx.x] = mass;
+  }
+}
+
 // out[0] = sum of partial[0..n) in a fixed order (deterministic for a fixed n).
 __global__ void final_sum_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
   __shared__ double sh[1024 / 32];

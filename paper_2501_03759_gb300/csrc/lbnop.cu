@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -987,9 +988,12 @@ struct lbnop_ctx {
   float* phi_out;  // [max_batch][H][W], the training forward's output
   int* flags;
   int leap_turns;           // quarter turns a leap averages the network over (1 or 4)
-  char* judge_state;        // saved lbch state of an H x W FP32 field (judged leap runs)
-  size_t judge_state_bytes;
-  double* judge_vals;       // 16 doubles: mass / energy readings and audit sums
+  char* judge_state;        // two saved lbch states of an H x W FP32 field (judged leap runs)
+  size_t judge_state_bytes; // bytes of one of them
+  double* judge_vals;       // 16 doubles: two slots of mass / energy readings and audit sums
+  cudaStream_t side;        // judged runs read their readings back on this stream (made on first use)
+  cudaEvent_t ready[2];     // recorded after each cycle's first reading
+  bool side_made;
   long long adam_t;
   int last_batch;
   bool failed;
@@ -1091,7 +1095,7 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
   char* phi_out = take((size_t)p->max_batch * p->H * p->W * 4);
   char* flags = take(16);
   const size_t jsb = judge_state_size(p);
-  char* judge_state = take(jsb);
+  char* judge_state = take(2 * jsb);
   char* judge_vals = take(16 * 8);
   if (c) {
     c->n_params = n_params;
@@ -1632,47 +1636,83 @@ lbch_status lbnop_leap_run_judged(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int
     set_err(c, "leap_run_judged: invalid judge (leap_steps >= 1, tolerances finite and >= 0)");
     return LBCH_EINVAL;
   }
+  if (!c->side_made) {  // the read-back stream and its events, made once per context
+    cudaStream_t side = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+      if (e0) cudaEventDestroy(e0);
+      if (side) cudaStreamDestroy(side);
+      cuda_bad(c, cudaGetLastError(), "leap_run_judged: stream and events");
+      return LBCH_ECUDA;
+    }
+    c->side = side;
+    c->ready[0] = e0;
+    c->ready[1] = e1;
+    c->side_made = true;
+  }
   lbnop_judge_stats S{};
-  S.max_audit_err = 0.0;
   S.max_leap_rise = -INFINITY;
   S.max_corr_rise = -INFINITY;
   const double nodes = (double)c->p.H * c->p.W;
   const int64_t t0 = lbch_steps_taken(lbm);
+  // Readings of cycle k in slot k % 2 (8 doubles): mass and energy of phi when the cycle starts,
+  // then after its leap, then the audit sums. The reading at the start of cycle k + 1 is also
+  // the one after cycle k's correction steps.
   double* dv = c->judge_vals;
-  double hv[8];
-  // Reads n doubles from the device readings into hv (one synchronisation).
-  auto fetch = [&](int first, int n, const char* what) -> bool {
-    return !cuda_bad(c, cudaMemcpyAsync(hv, dv + first, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-                     what) &&
-           !cuda_bad(c, cudaStreamSynchronize(c->stream), what);
-  };
+  double hv[16];
+  auto backup = [&](int s) { return c->judge_state + (size_t)s * c->judge_state_bytes; };
+  auto audited = [&](int64_t k) { return J.audit_every > 0 && (k + 1) % J.audit_every == 0; };
   auto lbm_fail = [&](lbch_status s) {
     set_err(c, "leap_run_judged: %s", lbch_last_error(lbm));
     return s;
   };
-  // Mass and energy of the state the first leap starts from.
-  if ((st = lbch_mass_device(lbm, dv + 0)) != LBCH_OK || (st = lbch_free_energy_device(lbm, dv + 1)) != LBCH_OK)
-    return lbm_fail(st);
-  if (!fetch(0, 2, "leap_run_judged: read")) return LBCH_ECUDA;
-  double m_before = hv[0], e_before = hv[1];
-  const int n_head = HEAD_BLOCKS;
-  for (int64_t k = 0; k < cycles; ++k) {
-    const bool audit = J.audit_every > 0 && (k + 1) % J.audit_every == 0;
-    if (audit) {
-      // leap prediction in leap0, plain K steps from the untouched state into leap1
-      if ((st = lbch_get_phi_device(lbm, c->leap0)) != LBCH_OK) return lbm_fail(st);
+  // Enqueues cycle k (k == cycles: only the readings after the last cycle); asynchronous.
+  auto enqueue = [&](int64_t k) -> lbch_status {
+    const int s = (int)(k & 1);
+    double* v = dv + 8 * s;
+    lbch_status r;
+    if ((r = lbch_get_phi_device(lbm, c->leap0)) != LBCH_OK ||
+        (r = lbch_field_diagnostics_device(lbm, c->leap0, v)) != LBCH_OK)
+      return lbm_fail(r);
+    if (cuda_bad(c, cudaEventRecord(c->ready[s], c->stream), "leap_run_judged: event")) return LBCH_ECUDA;
+    if (k >= cycles) return LBCH_OK;
+    if (audited(k)) {  // the plain K steps from this state beside the network's prediction
       leap_forward(c, alpha);
-      if ((st = lbch_step(lbm, J.leap_steps)) != LBCH_OK || (st = lbch_get_phi_device(lbm, c->leap1)) != LBCH_OK)
-        return lbm_fail(st);
-      diff_norm_kernel<<<n_head, 256, 0, c->stream>>>(c->leap0, c->leap1, (long long)c->p.H * c->p.W, c->partial);
-      diff_norm_final<<<1, 32, 0, c->stream>>>(c->partial, n_head, dv + 6);
-      if ((st = lbch_step(lbm, lbm_steps)) != LBCH_OK || (st = lbch_mass_device(lbm, dv + 4)) != LBCH_OK ||
-          (st = lbch_free_energy_device(lbm, dv + 5)) != LBCH_OK)
-        return lbm_fail(st);
-      if (cuda_bad(c, cudaGetLastError(), "leap_run_judged: audit launch") ||
-          !fetch(4, 4, "leap_run_judged: read"))
-        return LBCH_ECUDA;
-      const double err = std::sqrt(hv[2] / hv[3]);
+      if ((r = lbch_step(lbm, J.leap_steps)) != LBCH_OK || (r = lbch_get_phi_device(lbm, c->leap1)) != LBCH_OK)
+        return lbm_fail(r);
+      diff_norm_kernel<<<HEAD_BLOCKS, 256, 0, c->stream>>>(c->leap0, c->leap1, (long long)c->p.H * c->p.W,
+                                                           c->partial);
+      diff_norm_final<<<1, 32, 0, c->stream>>>(c->partial, HEAD_BLOCKS, v + 4);
+    } else {
+      if ((r = lbch_save_state_device(lbm, backup(s), c->judge_state_bytes)) != LBCH_OK) return lbm_fail(r);
+      leap_forward(c, alpha);
+      if ((r = lbch_field_diagnostics_device(lbm, c->leap0, v + 2)) != LBCH_OK ||
+          (r = lbch_init_field_device(lbm, c->leap0)) != LBCH_OK)
+        return lbm_fail(r);
+    }
+    if ((r = lbch_step(lbm, lbm_steps)) != LBCH_OK) return lbm_fail(r);
+    return cuda_bad(c, cudaGetLastError(), "leap_run_judged: launch") ? LBCH_ECUDA : LBCH_OK;
+  };
+  // Both slots, once the reading at the start of cycle k + 1 (slot s) is done; the stream of
+  // the run keeps working meanwhile.
+  auto fetch = [&](int s) {
+    return !cuda_bad(c, cudaStreamWaitEvent(c->side, c->ready[s], 0), "leap_run_judged: wait") &&
+           !cuda_bad(c, cudaMemcpyAsync(hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, c->side), "leap_run_judged: read") &&
+           !cuda_bad(c, cudaStreamSynchronize(c->side), "leap_run_judged: read");
+  };
+  if (cycles > 0 && (st = enqueue(0)) != LBCH_OK) return st;
+  for (int64_t k = 0; k < cycles; ++k) {
+    // Cycle k + 1 goes on the stream before cycle k is judged; if cycle k is rejected it is
+    // discarded and enqueued again after the plain steps that replace cycle k.
+    if ((st = enqueue(k + 1)) != LBCH_OK) return st;
+    if (!fetch((int)((k + 1) & 1))) return LBCH_ECUDA;
+    const double* a = hv + 8 * (k & 1);
+    const double* b = hv + 8 * ((k + 1) & 1);
+    const double m_pre = a[0], e_pre = a[1], m_leap = a[2], e_leap = a[3], e_corr = b[1];
+    if (audited(k)) {
+      const double err = std::sqrt(a[4] / a[5]);
       ++S.audits;
       S.lbm_steps += J.leap_steps + lbm_steps;
       if (std::isfinite(err) && err <= J.phi_rtol) {
@@ -1681,61 +1721,43 @@ lbch_status lbnop_leap_run_judged(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int
         ++S.rejected;
         ++S.rejected_audit;
       }
-      if (std::isfinite(err) && err > S.max_audit_err) S.max_audit_err = err;
-      if (!std::isfinite(err)) S.max_audit_err = INFINITY;
-      m_before = hv[0];
-      e_before = hv[1];
+      S.max_audit_err = std::isfinite(err) ? std::max(S.max_audit_err, err) : INFINITY;
+      continue;
+    }
+    const bool finite = std::isfinite(m_pre) && std::isfinite(e_pre) && std::isfinite(m_leap) &&
+                        std::isfinite(e_leap) && std::isfinite(b[0]) && std::isfinite(e_corr);
+    bool ok = finite;
+    if (!finite) {
+      ++S.rejected_nonfinite;
     } else {
-      if ((st = lbch_save_state_device(lbm, c->judge_state, c->judge_state_bytes)) != LBCH_OK ||
-          (st = lbch_get_phi_device(lbm, c->leap0)) != LBCH_OK)
-        return lbm_fail(st);
-      leap_forward(c, alpha);
-      if ((st = lbch_init_field_device(lbm, c->leap0)) != LBCH_OK || (st = lbch_mass_device(lbm, dv + 2)) != LBCH_OK ||
-          (st = lbch_free_energy_device(lbm, dv + 3)) != LBCH_OK || (st = lbch_step(lbm, lbm_steps)) != LBCH_OK ||
-          (st = lbch_mass_device(lbm, dv + 4)) != LBCH_OK || (st = lbch_free_energy_device(lbm, dv + 5)) != LBCH_OK)
-        return lbm_fail(st);
-      if (cuda_bad(c, cudaGetLastError(), "leap_run_judged: launch") || !fetch(2, 4, "leap_run_judged: read"))
-        return LBCH_ECUDA;
-      const double m_leap = hv[0], e_leap = hv[1], m_corr = hv[2], e_corr = hv[3];
-      const bool finite = std::isfinite(m_leap) && std::isfinite(e_leap) && std::isfinite(m_corr) &&
-                          std::isfinite(e_corr);
-      const double rise_leap = (e_leap - e_before) / std::fabs(e_before);
+      const double rise_leap = (e_leap - e_pre) / std::fabs(e_pre);
       const double rise_corr = (e_corr - e_leap) / std::fabs(e_leap);
-      bool ok = finite;
-      if (!finite) {
-        ++S.rejected_nonfinite;
-      } else {
-        if (rise_leap > S.max_leap_rise) S.max_leap_rise = rise_leap;
-        if (rise_corr > S.max_corr_rise) S.max_corr_rise = rise_corr;
-        if (std::fabs(m_leap - m_before) > J.mass_atol * nodes) {
-          ok = false;
-          ++S.rejected_mass;
-        } else if (e_leap > e_before + J.energy_rtol * std::fabs(e_before) ||
-                   e_corr > e_leap + J.energy_rtol * std::fabs(e_leap)) {
-          ok = false;
-          ++S.rejected_energy;
-        }
-      }
-      if (ok) {
-        ++S.accepted;
-        S.lbm_steps += lbm_steps;
-        m_before = m_corr;
-        e_before = e_corr;
-      } else {
-        // the plain scheme over the same simulated time, from the saved state
-        ++S.rejected;
-        if ((st = lbch_restore_state_device(lbm, c->judge_state, c->judge_state_bytes)) != LBCH_OK ||
-            (st = lbch_step(lbm, J.leap_steps + lbm_steps)) != LBCH_OK ||
-            (st = lbch_mass_device(lbm, dv + 4)) != LBCH_OK || (st = lbch_free_energy_device(lbm, dv + 5)) != LBCH_OK)
-          return lbm_fail(st);
-        if (!fetch(4, 2, "leap_run_judged: read")) return LBCH_ECUDA;
-        S.lbm_steps += J.leap_steps + lbm_steps;
-        m_before = hv[0];
-        e_before = hv[1];
+      S.max_leap_rise = std::max(S.max_leap_rise, rise_leap);
+      S.max_corr_rise = std::max(S.max_corr_rise, rise_corr);
+      if (std::fabs(m_leap - m_pre) > J.mass_atol * nodes) {
+        ok = false;
+        ++S.rejected_mass;
+      } else if (e_leap > e_pre + J.energy_rtol * std::fabs(e_pre) ||
+                 e_corr > e_leap + J.energy_rtol * std::fabs(e_leap)) {
+        ok = false;
+        ++S.rejected_energy;
       }
     }
-    if ((st = lbch_set_steps_taken(lbm, t0 + (k + 1) * (J.leap_steps + lbm_steps))) != LBCH_OK) return lbm_fail(st);
+    if (ok) {
+      ++S.accepted;
+      S.lbm_steps += lbm_steps;
+      continue;
+    }
+    // Rejected: the plain scheme over the same simulated time from the state saved before the
+    // leap, then cycle k + 1 (or the last readings) again on top of it.
+    ++S.rejected;
+    S.lbm_steps += J.leap_steps + lbm_steps;
+    if ((st = lbch_restore_state_device(lbm, backup((int)(k & 1)), c->judge_state_bytes)) != LBCH_OK ||
+        (st = lbch_step(lbm, J.leap_steps + lbm_steps)) != LBCH_OK)
+      return lbm_fail(st);
+    if ((st = enqueue(k + 1)) != LBCH_OK) return st;
   }
+  if ((st = lbch_set_steps_taken(lbm, t0 + cycles * (J.leap_steps + lbm_steps))) != LBCH_OK) return lbm_fail(st);
   if (stats) *stats = S;
   return done(c, "leap_run_judged: launch");
 }
@@ -1796,6 +1818,13 @@ int64_t lbnop_tc_launches(void) { return tc_counter().load(std::memory_order_rel
 
 const char* lbnop_last_error(const lbnop_ctx* c) { return c ? c->err : "context is NULL"; }
 
-void lbnop_destroy(lbnop_ctx* c) { delete c; }
+void lbnop_destroy(lbnop_ctx* c) {
+  if (c && c->side_made) {
+    cudaEventDestroy(c->ready[0]);
+    cudaEventDestroy(c->ready[1]);
+    cudaStreamDestroy(c->side);
+  }
+  delete c;
+}
 
 }  // extern "C"

@@ -132,6 +132,8 @@ def load():
         for name in ("lbch_mass_device", "lbch_free_energy_device"):
             getattr(lib, name).argtypes = [vp, vp]
             getattr(lib, name).restype = ctypes.c_int
+        lib.lbch_field_diagnostics_device.argtypes = [vp, vp, vp]
+        lib.lbch_field_diagnostics_device.restype = ctypes.c_int
         lib.lbch_state_bytes.argtypes = [P]
         lib.lbch_state_bytes.restype = ctypes.c_size_t
         for name in ("lbch_save_state_device", "lbch_restore_state_device"):
@@ -292,6 +294,11 @@ def lbch_free_energy_device(ctx, d_out: int) -> None:
     _check(ctx, load().lbch_free_energy_device(ctx, ctypes.c_void_p(int(d_out))), "lbch_free_energy_device")
 
 
+def lbch_field_diagnostics_device(ctx, d_phi: int, d_out2: int) -> None:
+    _check(ctx, load().lbch_field_diagnostics_device(ctx, ctypes.c_void_p(int(d_phi)), ctypes.c_void_p(int(d_out2))),
+           "lbch_field_diagnostics_device")
+
+
 def lbch_state_bytes(p: lbch_params) -> int:
     return int(load().lbch_state_bytes(ctypes.byref(p)))
 
@@ -419,6 +426,13 @@ class Solver:
         _check_device_f64(out, "out")
         with self._on_device():
             lbch_free_energy_device(self.ctx, out.data_ptr())
+
+    def field_diagnostics_device(self, phi, out) -> None:
+        """Mass and free energy of a float32 CUDA field (ny, nx) into out[0:2] (float64 CUDA)."""
+        _check_device_f32(phi, self.nx * self.ny, "phi")
+        _check_device_f64(out, "out")
+        with self._on_device():
+            lbch_field_diagnostics_device(self.ctx, phi.data_ptr(), out.data_ptr())
 
     def save_state_device(self, out=None):
         """Device-side checkpoint into a uint8 CUDA tensor of lbch_state_bytes (allocated if None)."""

@@ -501,6 +501,12 @@ def test_device_checkpoint_and_device_diagnostics(storage):
     a.mass_device(m[0:1])
     a.free_energy_device(m[1:2])
     assert m[0].item() == a.mass() and m[1].item() == a.free_energy()
+    # the fused diagnostics of a given field: the energy bit for bit, the mass as the FP64 sum of
+    # the FP32 phi (the populations' sum differs by FP32 rounding of phi only)
+    d = torch.zeros(2, dtype=torch.float64, device="cuda")
+    a.field_diagnostics_device(a.phi_device(), d)
+    assert d[1].item() == a.free_energy()
+    assert abs(d[0].item() - a.mass()) <= 2.0 ** -23 * np.abs(a.field()).sum()
     a.restore_state_device(img)
     assert a.steps_taken == 34  # restore leaves the counter as it is
     a.step(21)
