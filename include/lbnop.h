@@ -185,16 +185,31 @@ lbch_status lbnop_leap_run_judged(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int
  *                        dy being BF16 [B][H][W][c_out]. */
 lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float* d_bias, int32_t B, int32_t H,
                           int32_t W, int32_t c_in, int32_t c_out, float* d_y, void* cuda_stream);
+/* The same convolution with weights packed once for the tensor-core path: lbnop_conv3x3_pack
+ * writes w ([9][c_out][c_in] BF16, 16-byte aligned) into d_packed (16-byte aligned, caller
+ * owned, lbnop_conv3x3_packed_bytes(c_in, c_out) bytes; 0 for unsupported widths) in the
+ * layout that path copies whole weight taps from, [9][c_in / 8][c_out][8] with 16 zero bytes
+ * after each [c_out][8] block. lbnop_conv3x3_packed then runs conv3x3 with it: d_packed is
+ * read where the tensor-core path takes the shape (W a multiple of 128, H a multiple of 4),
+ * d_w elsewhere; d_packed may be NULL, which keeps every shape on the mma.sync kernels.
+ * lbnop_conv3x3 packs into a stream-ordered temporary (cudaMallocAsync) on each call where
+ * the tensor-core path applies. */
+size_t lbnop_conv3x3_packed_bytes(int32_t c_in, int32_t c_out);
+lbch_status lbnop_conv3x3_pack(const uint16_t* d_w, int32_t c_in, int32_t c_out, void* d_packed, void* cuda_stream);
+lbch_status lbnop_conv3x3_packed(const uint16_t* d_x, const uint16_t* d_w, const void* d_packed, const float* d_bias,
+                                 int32_t B, int32_t H, int32_t W, int32_t c_in, int32_t c_out, float* d_y,
+                                 void* cuda_stream);
 lbch_status lbnop_conv3x3_bwd_data(const uint16_t* d_dy, const uint16_t* d_w, int32_t B, int32_t H, int32_t W,
                                    int32_t c_in, int32_t c_out, float* d_dx, void* cuda_stream);
 lbch_status lbnop_conv3x3_bwd_weight(const uint16_t* d_x, const uint16_t* d_dy, int32_t B, int32_t H, int32_t W,
                                      int32_t c_in, int32_t c_out, float* d_dw, void* cuda_stream);
 
-/* Number of convolutions this process has run on the tcgen05 tensor-core path (operands
- * staged by TMA, FP32 accumulators in tensor memory) since the library was loaded. That path
- * takes every convolution whose rows are a multiple of 128 pixels long (H a multiple of 4,
- * one input tensor); the others run on mma.sync kernels. A diagnostic for tests and
- * benchmarks. */
+/* Number of convolutions this process has run on the tcgen05 tensor-core path (input rows
+ * staged by cp.async, weight taps by bulk asynchronous copies, FP32 accumulators in tensor
+ * memory) since the library was loaded. That path takes every forward convolution whose rows
+ * are a multiple of 128 pixels long (H a multiple of 4) with packed weights: one input
+ * tensor, or on the network's first layer the input and its BF16 remainder (K = 32); the
+ * others run on mma.sync kernels. A diagnostic for tests and benchmarks. */
 int64_t lbnop_tc_launches(void);
 
 const char* lbnop_last_error(const lbnop_ctx* c);

@@ -657,8 +657,7 @@ lbch_status lbch_field_diagnostics_device(lbch_ctx* c, const float* d_phi, doubl
   ec.cw = c->p.regularization == LBCH_REG_LINEAR ? 0.0f : 1.0f;
   // mass partial sums in the second staging plane (nx ny doubles >= the block count)
   field_diag_kernel<<<c->aux_blocks, AUX_THREADS, 0, c->stream>>>(d_phi, grid_of(c), ec, c->partial, c->stage1);
-  final_sum_kernel<<<1, 1024, 0, c->stream>>>(c->stage1, c->aux_blocks, d_out2);
-  final_sum_kernel<<<1, 1024, 0, c->stream>>>(c->partial, c->aux_blocks, d_out2 + 1);
+  final_sum_pair_kernel<<<2, 1024, 0, c->stream>>>(c->stage1, c->partial, c->aux_blocks, d_out2);
   return finish(c, "field_diagnostics_device: launch");
 }
 

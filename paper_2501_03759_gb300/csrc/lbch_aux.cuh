@@ -369,4 +369,16 @@ __global__ void final_sum_kernel(const double* __restrict__ partial, int n, doub
   if (threadIdx.x == 0) out[0] = v;
 }
 
+// out[0] = sum of a[0..n), out[1] = sum of b[0..n): block 0 and block 1 of one launch, each in
+// the order of final_sum_kernel.
+__global__ void final_sum_pair_kernel(const double* __restrict__ a, const double* __restrict__ b, int n,
+                                      double* __restrict__ out) {
+  __shared__ double sh[1024 / 32];
+  const double* p = blockIdx.x == 0 ? a : b;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
 }  // namespace lbch

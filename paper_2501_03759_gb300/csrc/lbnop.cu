@@ -48,7 +48,9 @@ struct LayerTab {
 
 // ---------------------------------------------------------------- small helpers
 
-__device__ __forceinline__ float sigmoid_f(float z) { return 1.0f / (1.0f + expf(-z)); }
+// The logistic function with the fast exponential and division intrinsics: a few ulp of FP32,
+// far below the BF16 rounding every activation gets next; exp(-z) = inf gives 0 exactly.
+__device__ __forceinline__ float sigmoid_f(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
 __device__ __forceinline__ float silu_grad_f(float z) {
   const float s = sigmoid_f(z);
@@ -89,6 +91,7 @@ struct ConvArgs {
   const bf16* x2;  // or null: a second input of the same shape, multiplied by the same weights
   const bf16* w;  // TW = false: [9][CO][CI]; TW = true: [9][CI][CO], read at tap 8 - t
   const bf16* w2;  // or null: the BF16 remainder of the weights (w + w2 ~ 16 bits), applied to x
+  const unsigned char* wpk;  // or null: w packed for the tensor-core path (tc_pack_kernel)
   int B, H, W;
   const float* bias;  // [CO] or null
   const float* film;  // [CO] or null: adds alpha[b] film[n]
@@ -501,30 +504,50 @@ __global__ void s2d_kernel(const float* __restrict__ phi, const double* __restri
   }
 }
 
+// Eight BF16 channels of one pixel in one 16-byte word. The elementwise kernels below give
+// each thread 8 channels of one pixel (every channel count here is a multiple of 8) and index
+// in 32 bits (B H W C < 2^31 for every tensor of a context).
+union BF8 {
+  uint4 u;
+  bf16 h[8];
+};
+
+__device__ __forceinline__ BF8 ld8(const bf16* p) {
+  BF8 v;
+  v.u = *reinterpret_cast<const uint4*>(p);
+  return v;
+}
+
 // 2 x 2 average: x [B][2h][2w][C] -> y [B][h][w][C].
 __global__ void pool_kernel(const bf16* __restrict__ x, int B, int h, int w, int C, bf16* __restrict__ y) {
-  const long long n = (long long)B * h * w * C;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(k % C);
-    const long long pix = k / C;
-    const int j = (int)(pix % w), i = (int)((pix / w) % h), b = (int)(pix / ((long long)w * h));
-    const size_t r0 = ((size_t)(b * 2 * h + 2 * i) * 2 * w + 2 * j) * C + c, r1 = r0 + (size_t)2 * w * C;
-    const float s = (__bfloat162float(x[r0]) + __bfloat162float(x[r0 + C])) +
-                    (__bfloat162float(x[r1]) + __bfloat162float(x[r1 + C]));
-    y[k] = __float2bfloat16_rn(0.25f * s);
+  const int cv = C >> 3, n = B * h * w * cv;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int c8 = k % cv, pix = k / cv, j = pix % w, t = pix / w;  // t = b h + i: input row 2 t
+    const size_t r0 = ((size_t)(2 * t) * (2 * w) + 2 * j) * C + 8 * c8, r1 = r0 + (size_t)2 * w * C;
+    const BF8 a = ld8(x + r0), b = ld8(x + r0 + C), c = ld8(x + r1), d = ld8(x + r1 + C);
+    BF8 o;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const float s = (__bfloat162float(a.h[e]) + __bfloat162float(b.h[e])) +
+                      (__bfloat162float(c.h[e]) + __bfloat162float(d.h[e]));
+      o.h[e] = __float2bfloat16_rn(0.25f * s);
+    }
+    *reinterpret_cast<uint4*>(y + (size_t)k * 8) = o.u;
   }
 }
 
 // y [B][h][w][C] = nearest 2x upsampling of xc [B][h/2][w/2][C] plus skip [B][h][w][C].
 __global__ void up_add_kernel(const bf16* __restrict__ xc, const bf16* __restrict__ skip, int B, int h, int w, int C,
                               bf16* __restrict__ y) {
-  const long long n = (long long)B * h * w * C;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(k % C);
-    const long long pix = k / C;
-    const int j = (int)(pix % w), i = (int)((pix / w) % h), b = (int)(pix / ((long long)w * h));
-    const size_t src = ((size_t)(b * (h / 2) + i / 2) * (w / 2) + j / 2) * C + c;
-    y[k] = __float2bfloat16_rn(__bfloat162float(xc[src]) + __bfloat162float(skip[k]));
+  const int cv = C >> 3, n = B * h * w * cv;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int c8 = k % cv, pix = k / cv, j = pix % w, t = pix / w, i = t % h, b = t / h;
+    const size_t src = ((size_t)(b * (h / 2) + i / 2) * (w / 2) + j / 2) * C + 8 * c8;
+    const BF8 u = ld8(xc + src), v = ld8(skip + (size_t)k * 8);
+    BF8 o;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) o.h[e] = __float2bfloat16_rn(__bfloat162float(u.h[e]) + __bfloat162float(v.h[e]));
+    *reinterpret_cast<uint4*>(y + (size_t)k * 8) = o.u;
   }
 }
 
@@ -532,31 +555,59 @@ __global__ void up_add_kernel(const bf16* __restrict__ xc, const bf16* __restric
 // (the adjoint of nearest upsampling) when gf is given; times SiLU'(z) when z is given.
 __global__ void dz_kernel(const float* __restrict__ g, const float* __restrict__ gf, const bf16* __restrict__ z, int B,
                           int h, int w, int C, bf16* __restrict__ dz) {
-  const long long n = (long long)B * h * w * C;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    float v;
+  const int cv = C >> 3, n = B * h * w * cv;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    float v[8];
     if (gf) {
-      const int c = (int)(k % C);
-      const long long pix = k / C;
-      const int j = (int)(pix % w), i = (int)((pix / w) % h), b = (int)(pix / ((long long)w * h));
-      const size_t r0 = ((size_t)(b * 2 * h + 2 * i) * 2 * w + 2 * j) * C + c, r1 = r0 + (size_t)2 * w * C;
-      v = (gf[r0] + gf[r0 + C]) + (gf[r1] + gf[r1 + C]);
+      const int c8 = k % cv, pix = k / cv, j = pix % w, t = pix / w;
+      const size_t r0 = ((size_t)(2 * t) * (2 * w) + 2 * j) * C + 8 * c8, r1 = r0 + (size_t)2 * w * C;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float4 a = *reinterpret_cast<const float4*>(gf + r0 + 4 * q);
+        const float4 b = *reinterpret_cast<const float4*>(gf + r0 + C + 4 * q);
+        const float4 c = *reinterpret_cast<const float4*>(gf + r1 + 4 * q);
+        const float4 d = *reinterpret_cast<const float4*>(gf + r1 + C + 4 * q);
+        v[4 * q + 0] = (a.x + b.x) + (c.x + d.x);
+        v[4 * q + 1] = (a.y + b.y) + (c.y + d.y);
+        v[4 * q + 2] = (a.z + b.z) + (c.z + d.z);
+        v[4 * q + 3] = (a.w + b.w) + (c.w + d.w);
+      }
     } else {
-      v = g[k];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float4 a = *reinterpret_cast<const float4*>(g + (size_t)k * 8 + 4 * q);
+        v[4 * q + 0] = a.x;
+        v[4 * q + 1] = a.y;
+        v[4 * q + 2] = a.z;
+        v[4 * q + 3] = a.w;
+      }
     }
-    if (z) v *= silu_grad_f(__bfloat162float(z[k]));
-    dz[k] = __float2bfloat16_rn(v);
+    if (z) {
+      const BF8 zz = ld8(z + (size_t)k * 8);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] *= silu_grad_f(__bfloat162float(zz.h[e]));
+    }
+    BF8 o;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) o.h[e] = __float2bfloat16_rn(v[e]);
+    *reinterpret_cast<uint4*>(dz + (size_t)k * 8) = o.u;
   }
 }
 
-// gf [B][2h][2w][C] += 0.25 gc[parent] (the adjoint of 2 x 2 average pooling).
+// gf [B][2h][2w][C] += the adjoint of 2 x 2 averaging of gc [B][h][w][C] (FP32), four channels
+// per thread.
 __global__ void pool_bwd_kernel(const float* __restrict__ gc, int B, int h, int w, int C, float* __restrict__ gf) {
-  const long long n = (long long)B * 4 * h * w * C;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(k % C);
-    const long long pix = k / C;
-    const int j = (int)(pix % (2 * w)), i = (int)((pix / (2 * w)) % (2 * h)), b = (int)(pix / ((long long)4 * w * h));
-    gf[k] += 0.25f * gc[((size_t)(b * h + i / 2) * w + j / 2) * C + c];
+  const int cv = C >> 2, n = B * 4 * h * w * cv;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const int c4 = k % cv, pix = k / cv, j = pix % (2 * w), t = pix / (2 * w), i = t % (2 * h), b = t / (2 * h);
+    const float4 s = *reinterpret_cast<const float4*>(gc + ((size_t)(b * h + i / 2) * w + j / 2) * C + 4 * c4);
+    float4* d = reinterpret_cast<float4*>(gf + (size_t)k * 4);
+    float4 v = *d;
+    v.x += 0.25f * s.x;
+    v.y += 0.25f * s.y;
+    v.z += 0.25f * s.z;
+    v.w += 0.25f * s.w;
+    *d = v;
   }
 }
 
@@ -618,7 +669,26 @@ __global__ void sample_sums_kernel(const float* __restrict__ v, const float* __r
   const float* vb = v + (size_t)b * n;
   const float* tb = target ? target + (size_t)b * n : nullptr;
   double s = 0.0, s2 = 0.0;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+  // four values per load where every sample starts on a 16-byte boundary, then the tail
+  const long long n4 = (n & 3) == 0 ? n >> 2 : 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n4; k += stride) {
+    const float4 a = reinterpret_cast<const float4*>(vb)[k];
+    double d[4] = {a.x, a.y, a.z, a.w};
+    if (tb) {
+      const float4 t = reinterpret_cast<const float4*>(tb)[k];
+      d[0] -= (double)t.x;
+      d[1] -= (double)t.y;
+      d[2] -= (double)t.z;
+      d[3] -= (double)t.w;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      s += d[e];
+      s2 += d[e] * d[e];
+    }
+  }
+  for (long long k = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += stride) {
     const double d = tb ? (double)vb[k] - (double)tb[k] : (double)vb[k];
     s += d;
     s2 += d * d;
@@ -975,6 +1045,10 @@ struct lbnop_ctx {
   int h0, w0;  // level-0 size (H/4, W/4)
   float *theta, *m, *v, *grad;
   bf16 *wf, *wb, *wlo;
+  unsigned char* wpk;       // weights of the tensor-core layers in that path's layout
+  long long wpk_off[NL];    // byte offset of layer l's packed weights, or -1 (mma.sync path)
+  long long wpkb_off[NL];   // the same for its data-gradient convolution (weights wb), or -1
+  long long wver, wpk_ver;  // refreshes of the BF16 weights; the one the packed copy is of
   // activations (BF16), by level; z_* pre-activations, a_* SiLU outputs
   bf16 *x0, *x0l, *z[NL], *a[NL], *p1, *p2, *p3, *in_d2a, *in_d1a, *in_d0a;
   bf16* dz[4];
@@ -1054,6 +1128,19 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
   char* wf = take(n_w * 2);
   char* wb = take(n_w * 2);
   char* wlo = take(n_w * 2);
+  long long wpk_off[NL], wpkb_off[NL], wpk_bytes = 0;
+  for (int l = 0; l < NL; ++l) {
+    const int lv = kL[l].level, kc = (l == E0A ? 2 : 1) * kL[l].ci / 8;
+    // the layers whose level rows the tensor-core path takes (tc_applies, at the level's size):
+    // their forward weights and, but for the layers reading phi (no input gradient), the
+    // transposed weights of their data gradient (c_in and c_out swapped)
+    const bool tc = l != LIN && l != LINA && ((p->W / 4) >> lv) % 128 == 0 && ((p->H / 4) >> lv) % 4 == 0;
+    wpk_off[l] = tc ? wpk_bytes : -1;
+    if (tc) wpk_bytes += 9LL * kc * (kL[l].co * 16 + 16);
+    wpkb_off[l] = tc && l != E0A ? wpk_bytes : -1;
+    if (tc && l != E0A) wpk_bytes += 9LL * (kL[l].co / 8) * (kL[l].ci * 16 + 16);
+  }
+  char* wpk = take(wpk_bytes > 0 ? (size_t)wpk_bytes : 16);
   char* x0 = take(P[0] * 16 * 2);
   char* x0l = take(P[0] * 16 * 2);
   char *zz[NL], *aa[NL];
@@ -1107,6 +1194,11 @@ size_t layout(const lbnop_params* p, lbnop_ctx* c, char* base) {
     c->wf = (bf16*)wf;
     c->wb = (bf16*)wb;
     c->wlo = (bf16*)wlo;
+    c->wpk = (unsigned char*)wpk;
+    for (int l = 0; l < NL; ++l) {
+      c->wpk_off[l] = wpk_off[l];
+      c->wpkb_off[l] = wpkb_off[l];
+    }
     c->x0 = (bf16*)x0;
     c->x0l = (bf16*)x0l;
     for (int l = 0; l < NL; ++l) {
@@ -1194,6 +1286,7 @@ void layer_fwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x, bool training,
   a.x2 = (l == E0A || l == LIN || l == LINA) ? c->x0l : nullptr;
   a.w2 = (l == LIN || l == LINA) ? c->wlo + c->tab.woff[l] : nullptr;
   a.w = wf_of(c, l);
+  a.wpk = c->wpk_off[l] >= 0 ? c->wpk + c->wpk_off[l] : nullptr;
   a.B = d.B;
   a.H = d.h[kL[l].level];
   a.W = d.w[kL[l].level];
@@ -1211,9 +1304,25 @@ void layer_fwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x, bool training,
   conv_launch(kL[l].ci, kL[l].co, false, a, c->stream);
 }
 
+// The tensor-core layers' weights in that path's layout, once per refresh of the BF16 weights.
+void pack_weights(lbnop_ctx* c) {
+  if (c->wpk_ver == c->wver) return;
+  for (int l = 0; l < NL; ++l) {
+    if (c->wpk_off[l] < 0) continue;
+    const int kc = (l == E0A ? 2 : 1) * kL[l].ci / 8;
+    tc_pack_kernel<<<grid_for(9LL * kc * (kL[l].co + 1), 256), 256, 0, c->stream>>>(
+        wf_of(c, l), kL[l].ci, kL[l].co, kc, c->wpk + c->wpk_off[l]);
+    if (c->wpkb_off[l] >= 0)
+      tc_pack_kernel<<<grid_for(9LL * (kL[l].co / 8) * (kL[l].ci + 1), 256), 256, 0, c->stream>>>(
+          wb_of(c, l), kL[l].co, kL[l].ci, kL[l].co / 8, c->wpk + c->wpkb_off[l]);
+  }
+  c->wpk_ver = c->wver;
+}
+
 void forward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, int batch, float* d_out, bool training) {
   const Dims d = dims(c, batch);
   cudaStream_t s = c->stream;
+  pack_weights(c);
   const long long P0 = (long long)batch * d.h[0] * d.w[0];
   const long long hw = (long long)c->p.H * c->p.W;
   sample_sums_kernel<<<dim3(HEAD_BLOCKS, batch), 256, 0, s>>>(d_phi, nullptr, hw, c->partial, c->partial2);
@@ -1222,11 +1331,11 @@ void forward_impl(lbnop_ctx* c, const float* d_phi, const double* alpha, int bat
   layer_fwd(c, E0A, d, c->x0, training, alpha);
   layer_fwd(c, E0B, d, c->a[E0A], training, alpha);
   auto pool = [&](const bf16* x, int lvl, int C, bf16* y) {
-    const long long n = (long long)batch * d.h[lvl] * d.w[lvl] * C;
+    const long long n = (long long)batch * d.h[lvl] * d.w[lvl] * (C / 8);
     pool_kernel<<<grid_for(n, 256), 256, 0, s>>>(x, batch, d.h[lvl], d.w[lvl], C, y);
   };
   auto up_add = [&](const bf16* xc, const bf16* skip, int lvl, int C, bf16* y) {
-    const long long n = (long long)batch * d.h[lvl] * d.w[lvl] * C;
+    const long long n = (long long)batch * d.h[lvl] * d.w[lvl] * (C / 8);
     up_add_kernel<<<grid_for(n, 256), 256, 0, s>>>(xc, skip, batch, d.h[lvl], d.w[lvl], C, y);
   };
   pool(c->a[E0B], 1, CH[0], c->p1);
@@ -1297,6 +1406,7 @@ void layer_bwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x_in, float* gin,
     ConvArgs a{};
     a.x = dz;
     a.w = wb_of(c, l);
+    a.wpk = c->wpkb_off[l] >= 0 ? c->wpk + c->wpkb_off[l] : nullptr;
     a.B = d.B;
     a.H = d.h[lvl];
     a.W = d.w[lvl];
@@ -1307,12 +1417,12 @@ void layer_bwd(lbnop_ctx* c, int l, const Dims& d, const bf16* x_in, float* gin,
 
 // dz[level] = g (or up-adjoint of gf) times SiLU'(z) where z is given.
 void make_dz(lbnop_ctx* c, const Dims& d, int lvl, int C, const float* g, const float* gf, const bf16* z) {
-  const long long n = (long long)d.B * d.h[lvl] * d.w[lvl] * C;
+  const long long n = (long long)d.B * d.h[lvl] * d.w[lvl] * (C / 8);
   dz_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(g, gf, z, d.B, d.h[lvl], d.w[lvl], C, c->dz[lvl]);
 }
 
 void pool_bwd(lbnop_ctx* c, const Dims& d, int lvl_coarse, int C, const float* gc, float* gf) {
-  const long long n = (long long)d.B * 4 * d.h[lvl_coarse] * d.w[lvl_coarse] * C;
+  const long long n = (long long)d.B * 4 * d.h[lvl_coarse] * d.w[lvl_coarse] * (C / 4);
   pool_bwd_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(gc, d.B, d.h[lvl_coarse], d.w[lvl_coarse], C, gf);
 }
 
@@ -1388,6 +1498,7 @@ void refresh_or_update(lbnop_ctx* c, bool update, double lr) {
   adam_kernel<<<grid_for(c->n_params, 256), 256, 0, c->stream>>>(c->theta, c->m, c->v, c->grad, c->n_params,
                                                                  (float)lr, c1, c2, update ? 1 : 0, c->gnorm,
                                                                  c->clip, c->tab, c->wf, c->wb, c->wlo);
+  ++c->wver;  // the packed tensor-core weights are stale until the next forward repacks them
 }
 
 lbch_status check_batch(lbnop_ctx* c, int batch, const double* h_alpha) {
@@ -1444,6 +1555,8 @@ lbch_status lbnop_create(const lbnop_params* p, void* d_workspace, size_t bytes,
     }
   }
   c->adam_t = 0;
+  c->wver = 0;
+  c->wpk_ver = -1;  // the first forward packs
   c->last_batch = 0;
   c->leap_turns = 1;
   c->failed = false;
@@ -1768,12 +1881,29 @@ static lbch_status op_check(int32_t B, int32_t H, int32_t W, int32_t ci, int32_t
   return LBCH_OK;
 }
 
-lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float* d_bias, int32_t B, int32_t H,
-                          int32_t W, int32_t c_in, int32_t c_out, float* d_y, void* cuda_stream) {
+size_t lbnop_conv3x3_packed_bytes(int32_t c_in, int32_t c_out) {
+  if (!channels_ok(c_in) || !channels_ok(c_out)) return 0;
+  return tc_pack_bytes(c_in, c_out, false);
+}
+
+lbch_status lbnop_conv3x3_pack(const uint16_t* d_w, int32_t c_in, int32_t c_out, void* d_packed, void* cuda_stream) {
+  if (!d_w || !d_packed || !channels_ok(c_in) || !channels_ok(c_out) || ((uintptr_t)d_w % 16) != 0 ||
+      ((uintptr_t)d_packed % 16) != 0)
+    return LBCH_EINVAL;
+  const int kc = tc_kc(c_in, false);
+  tc_pack_kernel<<<grid_for(9LL * kc * (c_out + 1), 256), 256, 0, (cudaStream_t)cuda_stream>>>(
+      (const bf16*)d_w, c_in, c_out, kc, (unsigned char*)d_packed);
+  return cudaGetLastError() == cudaSuccess ? LBCH_OK : LBCH_ECUDA;
+}
+
+lbch_status lbnop_conv3x3_packed(const uint16_t* d_x, const uint16_t* d_w, const void* d_packed, const float* d_bias,
+                                 int32_t B, int32_t H, int32_t W, int32_t c_in, int32_t c_out, float* d_y,
+                                 void* cuda_stream) {
   if (!d_x || !d_w || !d_y || op_check(B, H, W, c_in, c_out) != LBCH_OK) return LBCH_EINVAL;
   ConvArgs a{};
   a.x = (const bf16*)d_x;
   a.w = (const bf16*)d_w;
+  a.wpk = (const unsigned char*)d_packed;
   a.B = B;
   a.H = H;
   a.W = W;
@@ -1781,6 +1911,32 @@ lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float*
   a.yf = d_y;
   conv_launch(c_in, c_out, false, a, (cudaStream_t)cuda_stream);
   return cudaGetLastError() == cudaSuccess ? LBCH_OK : LBCH_ECUDA;
+}
+
+lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float* d_bias, int32_t B, int32_t H,
+                          int32_t W, int32_t c_in, int32_t c_out, float* d_y, void* cuda_stream) {
+  if (!d_x || !d_w || !d_y || op_check(B, H, W, c_in, c_out) != LBCH_OK) return LBCH_EINVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  ConvArgs probe{};
+  probe.x = (const bf16*)d_x;
+  probe.wpk = reinterpret_cast<const unsigned char*>(d_w);  // stands for the packed copy's alignment
+  probe.W = W;
+  probe.H = H;
+  void* pk = nullptr;
+  if (tc_applies(probe, c_in, c_out)) {  // the tensor-core path: the weights packed for it, stream-ordered
+    if (cudaMallocAsync(&pk, tc_pack_bytes(c_in, c_out, false), s) != cudaSuccess) {
+      cudaGetLastError();
+      return LBCH_ECUDA;
+    }
+    lbch_status st = lbnop_conv3x3_pack(d_w, c_in, c_out, pk, cuda_stream);
+    if (st != LBCH_OK) {
+      cudaFreeAsync(pk, s);
+      return st;
+    }
+  }
+  const lbch_status st = lbnop_conv3x3_packed(d_x, d_w, pk, d_bias, B, H, W, c_in, c_out, d_y, cuda_stream);
+  if (pk && cudaFreeAsync(pk, s) != cudaSuccess) return LBCH_ECUDA;
+  return st;
 }
 
 lbch_status lbnop_conv3x3_bwd_data(const uint16_t* d_dy, const uint16_t* d_w, int32_t B, int32_t H, int32_t W,

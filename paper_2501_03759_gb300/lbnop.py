@@ -93,6 +93,12 @@ def load():
             getattr(lib, name).restype = ctypes.c_int
         lib.lbnop_conv3x3.argtypes = [vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
         lib.lbnop_conv3x3.restype = ctypes.c_int
+        lib.lbnop_conv3x3_packed_bytes.argtypes = [i32, i32]
+        lib.lbnop_conv3x3_packed_bytes.restype = ctypes.c_size_t
+        lib.lbnop_conv3x3_pack.argtypes = [vp, i32, i32, vp, vp]
+        lib.lbnop_conv3x3_pack.restype = ctypes.c_int
+        lib.lbnop_conv3x3_packed.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
+        lib.lbnop_conv3x3_packed.restype = ctypes.c_int
         lib.lbnop_tc_launches.argtypes = []
         lib.lbnop_tc_launches.restype = ctypes.c_int64
         lib.lbnop_last_error.argtypes = [vp]
@@ -215,6 +221,26 @@ def lbnop_conv3x3(d_x: int, d_w: int, d_bias: int | None, B: int, H: int, W: int
                               ctypes.c_void_p(int(d_bias)) if d_bias else None, B, H, W, c_in, c_out,
                               ctypes.c_void_p(int(d_y)), ctypes.c_void_p(int(cuda_stream or 0)))
     _check(None, st, "lbnop_conv3x3")
+
+
+def lbnop_conv3x3_packed_bytes(c_in: int, c_out: int) -> int:
+    """Bytes of a layer's weights packed for the tensor-core path (0: unsupported widths)."""
+    return int(load().lbnop_conv3x3_packed_bytes(c_in, c_out))
+
+
+def lbnop_conv3x3_pack(d_w: int, c_in: int, c_out: int, d_packed: int, cuda_stream) -> None:
+    st = load().lbnop_conv3x3_pack(ctypes.c_void_p(int(d_w)), c_in, c_out, ctypes.c_void_p(int(d_packed)),
+                                   ctypes.c_void_p(int(cuda_stream or 0)))
+    _check(None, st, "lbnop_conv3x3_pack")
+
+
+def lbnop_conv3x3_packed(d_x: int, d_w: int, d_packed: int | None, d_bias: int | None, B: int, H: int, W: int,
+                         c_in: int, c_out: int, d_y: int, cuda_stream) -> None:
+    st = load().lbnop_conv3x3_packed(ctypes.c_void_p(int(d_x)), ctypes.c_void_p(int(d_w)),
+                                     ctypes.c_void_p(int(d_packed)) if d_packed else None,
+                                     ctypes.c_void_p(int(d_bias)) if d_bias else None, B, H, W, c_in, c_out,
+                                     ctypes.c_void_p(int(d_y)), ctypes.c_void_p(int(cuda_stream or 0)))
+    _check(None, st, "lbnop_conv3x3_packed")
 
 
 def lbnop_conv3x3_bwd_data(d_dy: int, d_w: int, B: int, H: int, W: int, c_in: int, c_out: int, d_dx: int,

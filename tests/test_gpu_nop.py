@@ -356,8 +356,9 @@ def test_leap_turns_average_the_turned_predictions():
 
 # ---------------------------------------------------------------- the tcgen05 tensor-core path
 
-# Rows of 128 pixels (or a multiple) with H a multiple of 4 take the tcgen05 path: operands
-# staged by TMA, FP32 accumulators in tensor memory. The shapes cover 1, 2 and 4 output rows
+# Rows of 128 pixels (or a multiple) with H a multiple of 4 take the tcgen05 path: input rows
+# staged by cp.async, whole weight taps by bulk copies from a packed copy of the weights, FP32
+# accumulators in tensor memory. The shapes cover 1, 2 and 4 output rows
 # per CTA (few, some and many rows), both ends of a row (periodic wrap in x) and of the field
 # (wrap in y), and rows of 256 pixels (two tiles per row).
 TC_SHAPES = [(1, 4, 128), (2, 8, 256), (3, 12, 128), (10, 128, 128)]
@@ -381,10 +382,41 @@ def test_conv_tc_forward(ci, co, shape):
     assert np.abs(y.cpu().numpy() - ref).max() <= 2e-7 * 9 * ci * scale / 64 + 1e-6
 
 
+@pytest.mark.parametrize("ci,co", [(96, 96), (16, 64)])
+def test_conv_packed_weights(ci, co):
+    """Weights packed once (lbnop_conv3x3_pack) drive the tensor-core path; without a packed
+    copy the same shape runs on the mma.sync kernels. Both agree with the oracle's conv."""
+    B, H, Wd = 2, 8, 256
+    x = W.bf16_exact((B, H, Wd, ci), 31, 1.0)
+    w = W.bf16_exact((9, co, ci), 32, 0.25)
+    xd, wd = dev_bf16(x), dev_bf16(w)
+    nb = lbnop.lbnop_conv3x3_packed_bytes(ci, co)
+    assert nb == 9 * (ci // 8) * (co * 16 + 16)
+    assert lbnop.lbnop_conv3x3_packed_bytes(32, co) == 0
+    pk = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    lbnop.lbnop_conv3x3_pack(wd.data_ptr(), ci, co, pk.data_ptr(), stream())
+    ref = N.conv(x, w)
+    bound = 2e-7 * 9 * ci * (N.conv(np.abs(x), np.abs(w)).max() + 1.0) / 64 + 1e-6
+    for packed in (pk.data_ptr(), None):
+        y = torch.empty((B, H, Wd, co), dtype=torch.float32, device="cuda")
+        before = lbnop.lbnop_tc_launches()
+        lbnop.lbnop_conv3x3_packed(xd.data_ptr(), wd.data_ptr(), packed, None, B, H, Wd, ci, co, y.data_ptr(),
+                                   stream())
+        torch.cuda.synchronize()
+        assert lbnop.lbnop_tc_launches() - before == (1 if packed else 0)
+        assert np.abs(y.cpu().numpy() - ref).max() <= bound
+    # the packed layout itself: tap t, chunk c, output channel n holds w[t][n][8 c .. 8 c + 7]
+    raw = pk.cpu().numpy().view(np.uint16).reshape(9, ci // 8, co + 1, 8)
+    assert (raw[:, :, co, :] == 0).all()
+    wbits = wd.cpu().numpy().view(np.uint16).reshape(9, co, ci // 8, 8)
+    assert (raw[:, :, :co, :] == wbits.transpose(0, 2, 1, 3)).all()
+
+
 def test_network_on_tensor_core_path_matches_oracle():
-    """A 512^2 field: its finest level (128 x 128) runs e0b, d0a and the output layer, and in
-    the backward pass their data gradients, on the tcgen05 path; forward and gradients against
-    the oracle with the same BF16 storage points, with the bounds of the mma.sync path."""
+    """A 512^2 field: its finest level (128 x 128) runs e0a (the input and its BF16 remainder
+    as K = 32), e0b, d0a and the output layer, and in the backward pass the data gradients of
+    the last three, on the tcgen05 path; forward and gradients against the oracle with the
+    same BF16 storage points, with the bounds of the mma.sync path."""
     B, H, Wd = 1, 512, 512
     theta, phi, target, alpha = network_case(B, H, Wd, seed=3)
     scale = 0.05
@@ -394,9 +426,9 @@ def test_network_on_tensor_core_path_matches_oracle():
     before = lbnop.lbnop_tc_launches()
     out = s.forward(pd, alpha).cpu().numpy().astype(np.float64)
     mid = lbnop.lbnop_tc_launches()
-    assert mid - before == 3  # e0b, d0a, out
+    assert mid - before == 4  # e0a, e0b, d0a, out
     loss = s.backward(pd, alpha, td)
-    assert lbnop.lbnop_tc_launches() - mid == 3 + 3  # forward again, then the data gradients of out, d0a, e0b
+    assert lbnop.lbnop_tc_launches() - mid == 4 + 3  # forward again, then the data gradients of out, d0a, e0b
     g = s.grads_host().astype(np.float64)
     ref_q, saved = N.forward(theta, phi, alpha, scale, quantize=N.bf16)
     e_q = rel_l2(out - phi, ref_q - phi)
