@@ -1,7 +1,7 @@
 // The periodic 3 x 3 convolution of lbnop.cu on the 5th-generation tensor cores (tcgen05):
 // operands in shared memory in the MMA's canonical K-major layout, FP32 accumulators in
-// tensor memory (TMEM), one thread issuing the MMAs, one thread refilling a ring of weight
-// taps by bulk asynchronous copies under mbarriers.
+// tensor memory (TMEM), one thread issuing the MMAs, a producer warp streaming weight taps
+// into a ring by bulk asynchronous copies under mbarriers.
 //
 // Scope: rows of a multiple of 128 pixels (W % 128 == 0), H a multiple of 4, c_in and c_out
 // in {16, 64, 96}; with X2, c_in = 16 and a second input tensor x2 (the BF16 remainder of
@@ -10,27 +10,31 @@
 // 512 x 512 and larger fields, where most of its convolution work is; every other layer keeps
 // the mma.sync kernels.
 //
-// A CTA (8 warps) computes R (1, 2 or 4) consecutive rows (same sample) x 128 pixels x all
-// c_out channels:
-//   - the R + 2 input rows it needs (rows h - 1 .. h + R, periodic in h) are copied once, 16
-//     bytes (8 channels of one pixel) per cp.async, consecutive threads reading consecutive
-//     bytes, into [K / 8 chunks][130 pixel slots][8 channels]: pixel x0 - 1 + s (periodic in
-//     x) in slot s. That is the K-major, no-swizzle canonical layout of the MMA's A operand:
-//     16-byte rows (one pixel's 8 channels) 16 bytes apart within a chunk block, chunk blocks
-//     131 x 16 bytes apart (one spare row shifts consecutive chunks to different bank groups).
-//     The operand of tap (dy, dx) for output row r is input row r + 1 + dy from slot 1 + dx on:
-//     a shift of the descriptor's start address, no copy.
-//   - the weights of one tap (the K-major B operand) are kept in global memory already in
-//     that layout (tc_pack_kernel: [K / 8 chunks][c_out][8], chunk blocks c_out x 16 + 16
-//     bytes apart), so one thread moves a whole tap with one cp.async.bulk into a stage of a
-//     ring of up to four, as soon as the MMAs that read the stage's previous tap have
-//     completed; the copy completes the stage's mbarrier by its byte count.
-//   - accumulators: R x c_out FP32 columns of TMEM (lane = pixel), D += A_t B_t^T over the
-//     9 taps and K / 16 K-steps of 16.
+// The kernel is persistent: the grid holds as many CTAs per 128-pixel column block as fit on
+// the GPU at once, and CTA g takes the g-th of that many equal runs of consecutive output rows
+// (flattened over (b, h)), in tiles of up to 4 rows that stay within one sample. Per tile, the
+// 8 compute warps:
+//   - stage the input rows the tile needs (rows h - 1 .. h + rows, periodic in h) by 16-byte
+//     cp.async copies, consecutive threads reading consecutive bytes, into slots of
+//     [K / 8 chunks][130 pixel slots][8 channels]: pixel x0 - 1 + s (periodic in x) in slot s.
+//     That is the K-major, no-swizzle canonical layout of the MMA's A operand: 16-byte rows
+//     (one pixel's 8 channels) 16 bytes apart within a chunk block, chunk blocks 131 x 16 bytes
+//     apart (one spare row shifts consecutive chunks to different bank groups). The operand of
+//     tap (dy, dx) for output row r is input row r + 1 + dy from slot 1 + dx on: a shift of the
+//     descriptor's start address, no copy. After a full 4-row tile the next tile of the same
+//     sample reuses the last two input rows (moved to slots 0 and 1) and copies 4 new ones.
+//   - thread 0 issues the 9 taps x K / 16 K-steps of MMAs per row into R x c_out FP32 TMEM
+//     columns (lane = pixel), D += A_t B_t^T.
 //   - epilogue: warps w and w + 4 share TMEM lane quarter w (one pixel per thread) and read
 //     half of its c_out columns each with tcgen05.ld, add bias and conditioning, scale, and
-//     stage the row in shared memory (two buffers, alternating by row), from where all 256
-//     threads write it out coalesced (conv_epilogue's outputs).
+//     stage the row in shared memory (over the tile's dead input rows where they are large
+//     enough), from where all 256 threads write it out coalesced (conv_epilogue's outputs).
+// Warp 8 streams the weight taps of all its tiles in order: the weights are kept in global
+// memory already in the B operand's layout (tc_pack_kernel: [K / 8 chunks][c_out][8], chunk
+// blocks c_out x 16 + 16 bytes apart), so one bulk copy moves a whole tap into a stage of a
+// ring of up to four, as soon as the MMAs that read the stage's previous tap have completed
+// (also while the compute warps finish the previous tile); the copy completes the stage's
+// mbarrier by its byte count.
 // Staging the input rows through TMA was measured first: tensor-map boxes whose innermost
 // extent is one 8-channel chunk (16 bytes) move each pixel's chunk as a separate request, and
 // operand staging then took most of a CTA's time. Coalesced 16-byte copies land the same
@@ -43,8 +47,9 @@ namespace nop {
 
 constexpr int TC_SLOTS = 130;                  // pixel slots per chunk block: x0 - 1 .. x0 + 128
 constexpr int TC_CHUNK_A = (TC_SLOTS + 1) * 16;  // bytes between chunk blocks of an input row
-constexpr int TC_THREADS = 256;                // eight warps: warps w, w + 4 share TMEM lane quarter w
-constexpr int TC_PRODUCER = 128;               // thread that copies the weight taps (warp 4, lane 0)
+constexpr int TC_ROWS = 4;                     // output rows per tile at most
+constexpr int TC_COMPUTE = 256;                // warps 0-7: staging, MMA issue (thread 0), epilogue
+constexpr int TC_THREADS = TC_COMPUTE + 32;    // warp 8: the weight-tap producer (lane 0)
 constexpr int TC_MAX_BSTAGES = 4;
 constexpr unsigned TC_SPIN_LIMIT = 1u << 20;   // bounded mbarrier waits (about a second at most)
 
@@ -60,30 +65,35 @@ template <int KC, int CO>
 __host__ __device__ constexpr int tc_tap_bytes() { return KC * tc_chunk_b<CO>(); }
 template <int CO>
 __host__ __device__ constexpr int tc_stage_pitch() { return CO + 4; }
-// Weight-ring stages: four where they fit beside the input rows in one CTA's shared memory
-// (more taps in flight hide the copy latency behind the MMAs), else three.
-template <int KC, int CO, int R>
-__host__ __device__ constexpr int tc_bstages() {
-  return (R + 2) * tc_row_bytes<KC>() + 4 * tc_tap_bytes<KC, CO>() + 512 <= 227 * 1024 ? 4 : 3;
-}
-template <int KC, int CO, int R>
-__host__ __device__ constexpr int tc_operand_bytes() {
-  return (R + 2) * tc_row_bytes<KC>() + tc_bstages<KC, CO, R>() * tc_tap_bytes<KC, CO>();
-}
-// Two staged output rows (FP32, rows tc_stage_pitch apart), then bias and conditioning.
+// One staged output row (FP32, pixels tc_stage_pitch apart), then bias and conditioning.
 template <int CO>
-__host__ __device__ constexpr int tc_staged_bytes() { return 2 * 128 * tc_stage_pitch<CO>() * 4 + 2 * CO * 4; }
-// The operand buffers, reused for the staged output rows, then 9 mbarriers and the TMEM address.
-template <int KC, int CO, int R>
-__host__ __device__ constexpr int tc_main_bytes() {
-  return tc_operand_bytes<KC, CO, R>() > tc_staged_bytes<CO>() ? tc_operand_bytes<KC, CO, R>() : tc_staged_bytes<CO>();
+__host__ __device__ constexpr int tc_staged_bytes() { return 128 * tc_stage_pitch<CO>() * 4 + 2 * CO * 4; }
+// The staged row goes over input slots 0-3 (dead once a tile's MMAs are done; slots 4 and 5
+// may hold the next tile's first rows) where they hold it, else after the weight ring.
+template <int KC, int CO>
+__host__ __device__ constexpr bool tc_stage_in_a() { return 4 * tc_row_bytes<KC>() >= tc_staged_bytes<CO>(); }
+template <int KC, int CO, int S>
+__host__ __device__ constexpr int tc_main_bytes_s() {
+  return (TC_ROWS + 2) * tc_row_bytes<KC>() + S * tc_tap_bytes<KC, CO>() +
+         (tc_stage_in_a<KC, CO>() ? 0 : tc_staged_bytes<CO>());
 }
-template <int KC, int CO, int R>
-__host__ __device__ constexpr int tc_smem_bytes() { return tc_main_bytes<KC, CO, R>() + 128 + 128 /* alignment */; }
-// TMEM columns: a power of two >= 32 that holds R accumulators of CO columns.
-template <int CO, int R>
+// Weight-ring stages: four where they fit in one CTA's shared memory (more taps in flight
+// hide the copy latency behind the MMAs), else three, else two.
+template <int KC, int CO>
+__host__ __device__ constexpr int tc_bstages() {
+  return tc_main_bytes_s<KC, CO, 4>() + 512 <= 227 * 1024 ? 4 : (tc_main_bytes_s<KC, CO, 3>() + 512 <= 227 * 1024 ? 3 : 2);
+}
+// The input slots, the weight ring, the staged row if separate; then 9 mbarriers, the TMEM
+// address and an abort word.
+template <int KC, int CO>
+__host__ __device__ constexpr int tc_main_bytes() { return tc_main_bytes_s<KC, CO, tc_bstages<KC, CO>()>(); }
+template <int KC, int CO>
+__host__ __device__ constexpr int tc_smem_bytes() { return tc_main_bytes<KC, CO>() + 128 + 128 /* alignment */; }
+// TMEM columns: a power of two >= 32 that holds TC_ROWS accumulators of CO columns.
+template <int CO>
 __host__ __device__ constexpr int tc_tmem_cols() {
-  return R * CO <= 32 ? 32 : (R * CO <= 64 ? 64 : (R * CO <= 128 ? 128 : (R * CO <= 256 ? 256 : 512)));
+  constexpr int n = TC_ROWS * CO;
+  return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : (n <= 256 ? 256 : 512)));
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -182,11 +192,13 @@ __device__ __forceinline__ void tc_stage_cols(const uint32_t* r, int n0, const f
 #pragma unroll
   for (int j = 0; j < N; j += 4) {
     const int n = n0 + j;
+    const float4 bb = *reinterpret_cast<const float4*>(sbias + n);
+    const float4 ff = *reinterpret_cast<const float4*>(sfilm + n);
     float4 o;
-    o.x = (__uint_as_float(r[j]) + sbias[n] + sfilm[n]) * sc;
-    o.y = (__uint_as_float(r[j + 1]) + sbias[n + 1] + sfilm[n + 1]) * sc;
-    o.z = (__uint_as_float(r[j + 2]) + sbias[n + 2] + sfilm[n + 2]) * sc;
-    o.w = (__uint_as_float(r[j + 3]) + sbias[n + 3] + sfilm[n + 3]) * sc;
+    o.x = (__uint_as_float(r[j]) + bb.x + ff.x) * sc;
+    o.y = (__uint_as_float(r[j + 1]) + bb.y + ff.y) * sc;
+    o.z = (__uint_as_float(r[j + 2]) + bb.z + ff.z) * sc;
+    o.w = (__uint_as_float(r[j + 3]) + bb.w + ff.w) * sc;
     *reinterpret_cast<float4*>(stage_px + n) = o;
   }
 }
@@ -223,11 +235,13 @@ __device__ __forceinline__ void tc_epilogue_row(uint32_t taddr_row, int g, const
 // conv_epilogue does.
 template <int CO>
 __device__ __forceinline__ void tc_store_row(const ConvArgs& p, const float* stage, size_t pix0, int tid) {
-  constexpr int Q = CO / 4, PITCH = tc_stage_pitch<CO>();
-  for (int idx = tid; idx < 128 * Q; idx += TC_THREADS) {
-    const int px = idx / Q, c4 = idx - px * Q;
-    float4 v = *reinterpret_cast<const float4*>(stage + px * PITCH + 4 * c4);
-    const size_t o = (pix0 + px) * CO + 4 * c4;
+  constexpr int Q = CO / 4;
+  static_assert(tc_stage_pitch<CO>() == CO + 4, "staged pixel rows padded by one float4");
+  const size_t o0 = pix0 * CO;  // item idx = 4 channels: global offset 4 idx, staged at 4 (idx + px)
+  for (int idx = tid; idx < 128 * Q; idx += TC_COMPUTE) {
+    const int px = idx / Q;
+    float4 v = *reinterpret_cast<const float4*>(stage + 4 * (idx + px));
+    const size_t o = o0 + 4 * (size_t)idx;
     if (p.yf) {
       float4* y = reinterpret_cast<float4*>(p.yf + o);
       if (p.accumulate) {
@@ -247,28 +261,54 @@ __device__ __forceinline__ void tc_store_row(const ConvArgs& p, const float* sta
   }
 }
 
-// Grid: (W / 128) x (B H / R) CTAs of TC_THREADS; R output rows per CTA. p.wpk holds the
-// weights packed by tc_pack_kernel for (CI, CO, X2).
-template <int CI, int CO, int R, bool X2>
+// Named barrier 1 over the 256 compute threads (the producer warp takes no part), and the
+// same barrier reducing a flag: true if it holds on every compute thread.
+__device__ __forceinline__ void tc_compute_sync() { asm volatile("barrier.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool tc_compute_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbarrier.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+// Output rows of the tile starting at flattened row r: at most TC_ROWS, within the CTA's run
+// (which ends before `last`) and within the sample.
+__device__ __forceinline__ int tc_tile_rows(int r, int last, int H) {
+  const int h = r % H;
+  int n = last - r;
+  n = n < TC_ROWS ? n : TC_ROWS;
+  return n < H - h ? n : H - h;
+}
+
+// Grid: (W / 128) x G CTAs of TC_THREADS; CTA (x, g) takes flattened output rows
+// [g N / G, (g + 1) N / G), N = B H, of column block x. p.wpk holds the weights packed by
+// tc_pack_kernel for (CI, CO, X2).
+template <int CI, int CO, bool X2>
 __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs p, int* err) {
   constexpr int KC = (X2 ? 2 : 1) * CI / 8;    // 8-channel chunks of the contraction
   constexpr int K = 8 * KC;
   static_assert(K % 16 == 0 && CO % 16 == 0 && CO <= 256, "UMMA shape: K steps of 16, N a multiple of 16");
-  static_assert(R * CO <= 512, "accumulators fit in TMEM");
+  static_assert(TC_ROWS * CO <= 512, "accumulators fit in TMEM");
   static_assert(!X2 || CI == 16, "the second input only on 16-channel layers");
   constexpr int ROW = tc_row_bytes<KC>();       // bytes per staged input row
   constexpr int TAP = tc_tap_bytes<KC, CO>();   // bytes per staged weight tap
   constexpr uint32_t LBO_A = TC_CHUNK_A, LBO_B = tc_chunk_b<CO>(), SBO = 128;
-  constexpr int COLS = tc_tmem_cols<CO, R>();
+  constexpr int COLS = tc_tmem_cols<CO>();
   constexpr uint32_t IDESC = umma_idesc_bf16<128, CO>();
-  constexpr int S = tc_bstages<KC, CO, R>();
+  constexpr int S = tc_bstages<KC, CO>();
   constexpr int PITCH = tc_stage_pitch<CO>();
   extern __shared__ __align__(128) unsigned char tc_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 127) & ~(uintptr_t)127);
   unsigned char* sA = base;
-  unsigned char* sB = base + (R + 2) * ROW;
+  unsigned char* sB = base + (TC_ROWS + 2) * ROW;
+  float* stage = reinterpret_cast<float*>(tc_stage_in_a<KC, CO>() ? base : sB + S * TAP);
+  float* sbias = stage + 128 * PITCH;  // bias (0 if none), then the conditioning times alpha
+  float* sfilm = sbias + CO;
   // b_full[S], b_empty[S], done (9 at most), then the TMEM address and the abort word
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + tc_main_bytes<KC, CO, R>());
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + tc_main_bytes<KC, CO>());
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_MAX_BSTAGES + 1);
   volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const uint32_t done_bar = smem_u32(&bars[2 * S]);
@@ -277,8 +317,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * 128;
-  const int row0 = blockIdx.y * R;  // first output row in the flattened (b, h) order
-  const int b = row0 / p.H, h0 = row0 - b * p.H;
+  const int N = p.B * p.H;
+  const int first = (int)((long long)blockIdx.y * N / gridDim.y);
+  const int last = (int)((long long)(blockIdx.y + 1) * N / gridDim.y);
+  int ntiles = 0;
+  for (int r = first; r < last; r += tc_tile_rows(r, last, p.H)) ++ntiles;
 
   if (tid == 0) {
     *abort_word = *(volatile int*)&tc_fault_flag;  // an earlier CTA's wait gave up: do nothing
@@ -290,117 +333,143 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (*abort_word) return;  // uniform over the CTA: nothing allocated or in flight yet
+  if (*abort_word || ntiles == 0) return;  // uniform over the CTA: nothing allocated or in flight yet
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // The producer starts the first taps (one per stage), so that they are in flight together
-  // with the input rows; the stage of tap t is t % S.
-  int last_tap[TC_MAX_BSTAGES] = {-1, -1, -1, -1};  // the producer's last tap per stage
-  auto copy_tap = [&](int t) {
-    const int s = t % S;
-    mbar_arrive_expect_tx(b_full(s), (uint32_t)TAP);
-    tc_bulk_copy(smem_u32(sB + s * TAP), p.wpk + (size_t)t * TAP, (uint32_t)TAP, b_full(s));
-    last_tap[s] = t;
-  };
-  if (tid == TC_PRODUCER)
-    for (int t = 0; t < S; ++t) copy_tap(t);
-  // The R + 2 input rows, by every thread: periodic in h and in x; with X2, chunks KC / 2 ..
-  // KC - 1 from the second tensor.
-  for (int idx = tid; idx < (R + 2) * TC_SLOTS * KC; idx += TC_THREADS) {
-    const int i = idx / (TC_SLOTS * KC), rem = idx - i * (TC_SLOTS * KC);
-    const int s = rem / KC, c = rem - s * KC;
-    const int h = wrap1(h0 - 1 + i, p.H), x = wrap1(x0 - 1 + s, p.W);
-    const size_t px = (size_t)(b * p.H + h) * p.W + x;
-    const bf16* src = (X2 && c >= CI / 8) ? p.x2 + px * CI + 8 * (c - CI / 8) : p.x + px * CI + 8 * c;
-    tc_cp16(smem_u32(sA + i * ROW + c * TC_CHUNK_A + s * 16), src);
-  }
-  tc_cp_done();  // this thread's input rows have landed
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();  // after it: every input row is in place and the TMEM address is known
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
 
   bool ok = true;
-  if (tid == 0) {  // the MMA issuer
-    for (int t = 0; t < 9 && ok; ++t) {
-      const int s = t % S;
-      if (!mbar_wait(b_full(s), (t / S) & 1)) {
-        ok = false;
-        break;
+  if (warp == TC_COMPUTE / 32) {
+    if (lane == 0) {  // the producer: tap T of the run (tile T / 9, tap T % 9) into stage T % S
+      int last_tap[TC_MAX_BSTAGES] = {-1, -1, -1, -1};
+      for (int T = 0; T < 9 * ntiles; ++T) {
+        const int s = T % S;
+        if (T >= S && !mbar_wait(b_empty(s), ((T - S) / S) & 1)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(b_full(s), (uint32_t)TAP);
+        tc_bulk_copy(smem_u32(sB + s * TAP), p.wpk + (size_t)(T % 9) * TAP, (uint32_t)TAP, b_full(s));
+        last_tap[s] = T;
       }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int dy = t / 3 - 1, dx = t % 3 - 1;
-      const uint32_t bbase = smem_u32(sB + s * TAP);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const uint32_t abase = smem_u32(sA + (r + 1 + dy) * ROW) + (uint32_t)((1 + dx) * 16);
-#pragma unroll
-        for (int kk = 0; kk < K / 16; ++kk) {
-          const uint64_t ad = umma_desc(abase + kk * 2 * LBO_A, LBO_A, SBO);
-          const uint64_t bd = umma_desc(bbase + kk * 2 * LBO_B, LBO_B, SBO);
-          umma_bf16(tmem + (uint32_t)(r * CO), ad, bd, IDESC, (t > 0 || kk > 0) ? 1u : 0u);
+      if (!ok)  // the last copy into each stage has landed before the CTA ends
+        for (int s = 0; s < S; ++s)
+          if (last_tap[s] >= 0) mbar_wait(b_full(s), (last_tap[s] / S) & 1);
+    }
+    __syncwarp();
+  } else {
+    bool reuse = false;  // this tile's first two input rows are the last two of the previous tile
+    int tile = 0;
+    for (int r0 = first; r0 < last; ++tile) {
+      const int rk = tc_tile_rows(r0, last, p.H);
+      const int b = r0 / p.H, h0 = r0 - b * p.H;
+      // Input rows h0 - 1 .. h0 + rk in slots 0 .. rk + 1: periodic in h and in x; with X2,
+      // chunks KC / 2 .. KC - 1 from the second tensor.
+      const int i0 = reuse ? 2 : 0;
+      if (reuse) {  // slots 4, 5 -> 0, 1
+        const uint4* src = reinterpret_cast<const uint4*>(sA + 4 * ROW);
+        uint4* dst = reinterpret_cast<uint4*>(sA);
+        for (int k = tid; k < 2 * ROW / 16; k += TC_COMPUTE) dst[k] = src[k];
+      }
+      {
+        // item (i, slot, chunk), chunk fastest; each thread steps TC_COMPUTE items at a time
+        // (fewer than one row's items, so the row advances by one at most)
+        constexpr int PER_ROW = TC_SLOTS * KC;
+        static_assert(PER_ROW >= TC_COMPUTE, "a thread's items advance by one row at most");
+        const int n_items = (rk + 2 - i0) * PER_ROW;
+        const uint32_t sA32 = smem_u32(sA);
+        int i = i0, rem = tid;
+        size_t row_px = (size_t)(b * p.H + wrap1(h0 - 1 + i, p.H)) * p.W;  // first pixel of input row i
+        for (int idx = tid; idx < n_items; idx += TC_COMPUTE) {
+          const int sl = rem / KC, c = rem - sl * KC;
+          const size_t px = row_px + wrap1(x0 - 1 + sl, p.W);
+          const bf16* src = (X2 && c >= CI / 8) ? p.x2 + px * CI + 8 * (c - CI / 8) : p.x + px * CI + 8 * c;
+          tc_cp16(sA32 + (uint32_t)(i * ROW + c * TC_CHUNK_A + sl * 16), src);
+          rem += TC_COMPUTE;
+          if (rem >= PER_ROW) {
+            rem -= PER_ROW;
+            ++i;
+            row_px = (size_t)(b * p.H + wrap1(h0 - 1 + i, p.H)) * p.W;
+          }
         }
       }
-      umma_commit(b_empty(s));  // the stage is free once these MMAs have read it
-    }
-    umma_commit(done_bar);  // arrives once every MMA issued above has completed
-  } else if (tid == TC_PRODUCER) {  // the remaining taps, each into the stage its tap - S left
-    for (int t = S; t < 9; ++t) {
-      const int s = t % S;
-      if (!mbar_wait(b_empty(s), ((t - S) / S) & 1)) {
+      tc_cp_done();  // this thread's input rows (and moved rows) are visible to the tensor cores
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      tc_compute_sync();  // every input row in place; the last tile's accumulators all read
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tmem = *tmem_slot;
+      if (tid == 0) {  // the MMA issuer
+        // Descriptors of input slot 0 and weight stage 0 at their first chunk: every operand
+        // start is a 16-byte multiple from them, added to the start-address field (address / 16,
+        // 14 bits, which holds every shared-memory address).
+        const uint64_t a0 = umma_desc(smem_u32(sA), LBO_A, SBO);
+        const uint64_t b0 = umma_desc(smem_u32(sB), LBO_B, SBO);
+        for (int t = 0; t < 9 && ok; ++t) {
+          const int T = 9 * tile + t, s = T % S;
+          if (!mbar_wait(b_full(s), (T / S) & 1)) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int dy = t / 3 - 1, dx = t % 3 - 1;
+          const uint64_t bt = b0 + (uint64_t)((s * TAP) >> 4);
+          const uint64_t at = a0 + (uint64_t)(((1 + dy) * ROW + (1 + dx) * 16) >> 4);
+#pragma unroll
+          for (int r = 0; r < TC_ROWS; ++r) {
+            if (r < rk) {
+#pragma unroll
+              for (int kk = 0; kk < K / 16; ++kk)
+                umma_bf16(tmem + (uint32_t)(r * CO), at + (uint64_t)((r * ROW + kk * 2 * LBO_A) >> 4),
+                          bt + (uint64_t)((kk * 2 * LBO_B) >> 4), IDESC, (t > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          umma_commit(b_empty(s));  // the stage is free once these MMAs have read it
+        }
+        umma_commit(done_bar);  // arrives once every MMA issued above has completed
+      }
+      __syncwarp();
+      const bool fin = mbar_wait(done_bar, (uint32_t)(tile & 1));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!tc_compute_and(ok && fin)) {  // uniform over the compute warps
         ok = false;
         break;
       }
-      copy_tap(t);
-    }
-  }
-  __syncwarp();
-  const bool issued = __syncthreads_and(ok ? 1 : 0) != 0;
-  // Wait for the accumulators (on the failure path, for whatever was issued).
-  const bool fin = mbar_wait(done_bar, 0);
-  const bool good = __syncthreads_and((issued && fin) ? 1 : 0) != 0;  // uniform over the CTA
-  if (!good) {
-    if (tid == 0) {
-      atomicExch(&tc_fault_flag, 1);
-      if (err) atomicExch(err, 1);
-    }
-    if (tid == TC_PRODUCER)  // the last copy into each stage has landed before the CTA ends
-      for (int s = 0; s < S; ++s)
-        if (last_tap[s] >= 0) mbar_wait(b_full(s), (last_tap[s] / S) & 1);
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (good) {
-    // The MMAs have completed: the operand buffers are free and hold the staged rows now.
-    float* stage0 = reinterpret_cast<float*>(base);
-    float* sbias = stage0 + 2 * 128 * PITCH;  // bias (0 if none), then the conditioning times alpha
-    float* sfilm = sbias + CO;
-    const float al = p.film ? p.alpha[b] : 0.0f;
-    const float sc = p.scale_alpha ? p.alpha[b] : 1.0f;
-    for (int n = tid; n < CO; n += TC_THREADS) {
-      sbias[n] = p.bias ? p.bias[n] : 0.0f;
-      sfilm[n] = p.film ? al * p.film[n] : 0.0f;
-    }
-    __syncthreads();
-    const int quarter = warp & 3, half = warp >> 2;
-    const int px = 32 * quarter + lane;  // this thread's TMEM lane: pixel x0 + px
+      // Epilogue: the MMAs have completed, so slots 0-3 are free for the staged rows.
+      const float al = p.film ? p.alpha[b] : 0.0f;
+      const float sc = p.scale_alpha ? p.alpha[b] : 1.0f;
+      for (int n = tid; n < CO; n += TC_COMPUTE) {
+        sbias[n] = p.bias ? p.bias[n] : 0.0f;
+        sfilm[n] = p.film ? al * p.film[n] : 0.0f;
+      }
+      tc_compute_sync();
+      const int quarter = warp & 3, half = warp >> 2;
+      const int px = 32 * quarter + lane;  // this thread's TMEM lane: pixel x0 + px
 #pragma unroll 1
-    for (int r = 0; r < R; ++r) {
-      float* stage = stage0 + (r & 1) * 128 * PITCH;
-      const uint32_t row_addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(r * CO);
-      tc_epilogue_row<CO>(row_addr, half, sbias, sfilm, sc, stage + px * PITCH);
-      // every thread has staged row r and finished writing out row r - 1 (the other buffer)
-      __syncthreads();
-      tc_store_row<CO>(p, stage, (size_t)(row0 + r) * p.W + x0, tid);
+      for (int r = 0; r < rk; ++r) {
+        const uint32_t row_addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(r * CO);
+        tc_epilogue_row<CO>(row_addr, half, sbias, sfilm, sc, stage + px * PITCH);
+        tc_compute_sync();
+        tc_store_row<CO>(p, stage, (size_t)(r0 + r) * p.W + x0, tid);
+        tc_compute_sync();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      reuse = rk == TC_ROWS && r0 + rk < last && (r0 + rk) % p.H != 0;
+      r0 += rk;
     }
+  }
+  const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (!all_ok && tid == 0) {
+    atomicExch(&tc_fault_flag, 1);
+    if (err) atomicExch(err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot), "r"(COLS) : "memory");
 }
 
 // The weights of a (CI, CO, X2) layer in the layout of the kernel's weight ring:
@@ -440,33 +509,32 @@ inline std::atomic<long long>& tc_counter() {
   return n;
 }
 
-template <int CI, int CO, int R, bool X2>
-void launch_tc_rows(const ConvArgs& a, int* err, cudaStream_t s) {
-  constexpr int KC = (X2 ? 2 : 1) * CI / 8;
-  constexpr int bytes = tc_smem_bytes<KC, CO, R>();
-  static_assert(bytes <= 227 * 1024, "fits in one CTA's shared memory");
-  static std::atomic<unsigned long long> done{0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (!(done.load(std::memory_order_relaxed) & bit)) {
-    cudaFuncSetAttribute(conv_tc_kernel<CI, CO, R, X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    done.fetch_or(bit, std::memory_order_relaxed);
-  }
-  conv_tc_kernel<CI, CO, R, X2><<<dim3(a.W / 128, a.B * a.H / R), TC_THREADS, bytes, s>>>(a, err);
-}
-
-// Rows per CTA: 4 when that still gives two waves of CTAs over the SMs (operands reused by
-// four rows), else fewer (more CTAs).
+// One persistent launch: as many CTAs per column block as fit on the GPU at once (never
+// more than there are rows), each taking an equal run of rows.
 template <int CI, int CO, bool X2>
 void launch_tc_x(const ConvArgs& a, int* err, int sms, cudaStream_t s) {
-  const long long ctas4 = (long long)(a.W / 128) * ((long long)a.B * a.H) / 4;
-  if (ctas4 >= 2LL * sms)
-    launch_tc_rows<CI, CO, 4, X2>(a, err, s);
-  else if (ctas4 * 2 >= sms)
-    launch_tc_rows<CI, CO, 2, X2>(a, err, s);
-  else
-    launch_tc_rows<CI, CO, 1, X2>(a, err, s);
+  constexpr int KC = (X2 ? 2 : 1) * CI / 8;
+  constexpr int bytes = tc_smem_bytes<KC, CO>();
+  static_assert(bytes <= 227 * 1024, "fits in one CTA's shared memory");
+  static std::atomic<int> per_sm[64];  // resident CTAs per SM, by device (0: not queried yet)
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int occ = per_sm[dev & 63].load(std::memory_order_relaxed);
+  if (occ == 0) {
+    cudaFuncSetAttribute(conv_tc_kernel<CI, CO, X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv_tc_kernel<CI, CO, X2>, TC_THREADS, bytes) !=
+            cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    if (occ > 512 / tc_tmem_cols<CO>()) occ = 512 / tc_tmem_cols<CO>();  // co-resident CTAs share TMEM
+    per_sm[dev & 63].store(occ, std::memory_order_relaxed);
+  }
+  const int cols = a.W / 128, rows = a.B * a.H;
+  const long long want = ((long long)sms * occ + cols - 1) / cols;
+  const int G = (int)(want < rows ? want : rows);
+  conv_tc_kernel<CI, CO, X2><<<dim3(cols, G), TC_THREADS, bytes, s>>>(a, err);
 }
 
 // Launches conv_tc_kernel for this convolution (tc_applies holds).

@@ -316,6 +316,8 @@ def main(argv=None):
     t.add_argument("--iters", type=int, default=48000)
     t.add_argument("--batch", type=int, default=32)
     t.add_argument("--lr", type=float, default=1e-3)
+    t.add_argument("--lr-end", type=float, default=1e-5, help="learning rate at the end of the cosine schedule")
+    t.add_argument("--init", help="start from these weights (.npy) instead of a fresh initialisation")
     t.add_argument("--clip", type=float, default=CLIP, help="clip factor over the median recent norm; 0: off")
     t.add_argument("--no-augment", action="store_true", help="train without the symmetry-group turns")
     t.add_argument("--alpha-weight", type=float, default=0.0, help="draw run i with weight 1 + this * alpha_i")
@@ -341,11 +343,14 @@ def main(argv=None):
         t0 = time.perf_counter()
         data = generate(runs, args.n)
         t_gen = time.perf_counter() - t0
-        theta, log = train(data, [a for a, _ in runs], args.iters, args.batch, args.lr, clip=args.clip,
-                           augment=not args.no_augment, alpha_weight=args.alpha_weight)
+        theta0 = np.load(args.init) if args.init else None
+        theta, log = train(data, [a for a, _ in runs], args.iters, args.batch, args.lr, lr_end=args.lr_end,
+                           theta0=theta0, clip=args.clip, augment=not args.no_augment,
+                           alpha_weight=args.alpha_weight)
         t_train = time.perf_counter() - t0 - t_gen
         np.save(os.path.join(args.out, "leap_theta.npy"), theta.astype(np.float32))
         report = {"runs": runs, "n": args.n, "iters": args.iters, "batch": args.batch, "lr": args.lr,
+                  "lr_end": args.lr_end, "init": os.path.basename(args.init) if args.init else None,
                   "clip": args.clip, "augment": not args.no_augment, "alpha_weight": args.alpha_weight,
                   "leap": LEAP, "every": EVERY, "scale": SCALE, "t_end": T_END,
                   "seconds_generate": t_gen, "seconds_train": t_train, "log": log}
