@@ -1,7 +1,7 @@
 // The periodic 3 x 3 convolution of lbnop.cu on the 5th-generation tensor cores (tcgen05):
 // operands in shared memory in the MMA's canonical K-major layout, FP32 accumulators in
-// tensor memory (TMEM), one thread issuing the MMAs, a producer warp streaming weight taps
-// into a ring by bulk asynchronous copies under mbarriers.
+// tensor memory (TMEM), and warps specialised by role, so that loading, the MMAs and the
+// epilogue of consecutive tiles overlap.
 //
 // Scope: rows of a multiple of 128 pixels (W % 128 == 0), H a multiple of 4, c_in and c_out
 // in {16, 64, 96}; with X2, c_in = 16 and a second input tensor x2 (the BF16 remainder of
@@ -12,45 +12,55 @@
 //
 // The kernel is persistent: the grid holds as many CTAs per 128-pixel column block as fit on
 // the GPU at once, and CTA g takes the g-th of that many equal runs of consecutive output rows
-// (flattened over (b, h)), in tiles of up to 4 rows that stay within one sample. Per tile, the
-// 8 compute warps:
-//   - stage the input rows the tile needs (rows h - 1 .. h + rows, periodic in h) by 16-byte
-//     cp.async copies, consecutive threads reading consecutive bytes, into slots of
-//     [K / 8 chunks][130 pixel slots][8 channels]: pixel x0 - 1 + s (periodic in x) in slot s.
-//     That is the K-major, no-swizzle canonical layout of the MMA's A operand: 16-byte rows
-//     (one pixel's 8 channels) 16 bytes apart within a chunk block, chunk blocks 131 x 16 bytes
-//     apart (one spare row shifts consecutive chunks to different bank groups). The operand of
-//     tap (dy, dx) for output row r is input row r + 1 + dy from slot 1 + dx on: a shift of the
-//     descriptor's start address, no copy. After a full 4-row tile the next tile of the same
-//     sample reuses the last two input rows (moved to slots 0 and 1) and copies 4 new ones.
-//   - thread 0 issues the 9 taps x K / 16 K-steps of MMAs per row into R x c_out FP32 TMEM
-//     columns (lane = pixel), D += A_t B_t^T.
-//   - epilogue: warps w and w + 4 share TMEM lane quarter w (one pixel per thread) and read
-//     half of its c_out columns each with tcgen05.ld, add bias and conditioning, scale, and
-//     stage the row in shared memory (over the tile's dead input rows where they are large
-//     enough), from where all 256 threads write it out coalesced (conv_epilogue's outputs).
-// Warp 8 streams the weight taps of all its tiles in order: the weights are kept in global
-// memory already in the B operand's layout (tc_pack_kernel: [K / 8 chunks][c_out][8], chunk
-// blocks c_out x 16 + 16 bytes apart), so one bulk copy moves a whole tap into a stage of a
-// ring of up to four, as soon as the MMAs that read the stage's previous tap have completed
-// (also while the compute warps finish the previous tile); the copy completes the stage's
-// mbarrier by its byte count.
+// (flattened over (b, h)), in tiles of up to 2 rows within one sample. Tile k:
+//   - loader warps 8-11 copy its input rows (h - 1 .. h + rows, periodic in h) by 16-byte
+//     cp.async, consecutive threads reading consecutive bytes, into slots of a ring of six:
+//     input row i of tile k in slot (2 k + i) mod 6, as [K / 8 chunks][130 pixel slots]
+//     [8 channels], pixel x0 - 1 + s (periodic in x) in pixel slot s. That is the K-major,
+//     no-swizzle canonical layout of the MMA's A operand: 16-byte rows (one pixel's 8
+//     channels) 16 bytes apart within a chunk block, chunk blocks 131 x 16 bytes apart. The
+//     operand of tap (dy, dx) for output row r is input row r + 1 + dy from pixel slot 1 + dx
+//     on: a shift of the descriptor's start address, no copy. A 2-row tile that follows a
+//     2-row tile of the same sample finds its first two input rows in place (the previous
+//     tile's last two) and copies two.
+//   - warp 12 (lane 0) issues the 9 taps x K / 16 K-steps of MMAs per row into TMEM
+//     accumulator buffer k mod 2 (2 x c_out FP32 columns, lane = pixel), D += A_t B_t^T,
+//     while the epilogue still reads buffer (k + 1) mod 2.
+//   - warp 13 (lane 0) streams the weight taps of all tiles in order: the weights are kept in
+//     global memory already in the B operand's layout (tc_pack_kernel: [K / 8 chunks][c_out]
+//     [8], chunk blocks c_out x 16 + 16 bytes apart), so one bulk copy moves a whole tap into
+//     a stage of a ring of up to four, once the MMAs that read the stage's previous tap have
+//     completed; the copy completes the stage's mbarrier by its byte count.
+//   - epilogue warps 0-7: warps w and w + 4 share TMEM lane quarter w (one pixel per thread)
+//     and read half of its c_out columns each with tcgen05.ld, add bias and conditioning,
+//     scale, and stage the row in shared memory (in the tile's first two input slots, dead
+//     once its MMAs are done, where they hold it), from where all 256 threads write it out
+//     coalesced (conv_epilogue's outputs).
+// mbarriers order the roles: a_full (rows loaded), mma_done (accumulators complete; slot pair
+// free for a reloading tile), epi_done (accumulator buffer and staged slots free), and per
+// weight stage b_full / b_empty. Tile k's input slots were last written for tile k - 2 and
+// held its staged rows, so tile k's copies wait for tile k - 2's epilogue.
 // Staging the input rows through TMA was measured first: tensor-map boxes whose innermost
 // extent is one 8-channel chunk (16 bytes) move each pixel's chunk as a separate request, and
 // operand staging then took most of a CTA's time. Coalesced 16-byte copies land the same
 // layout at full rate; the weights, whose layout is chosen here, go as whole taps.
 // Every wait on an mbarrier is bounded; on timeout the kernel sets an error flag, waits
-// (bounded) for its copies in flight, frees its TMEM and stops.
+// (bounded) for its copies and MMAs in flight, frees its TMEM and stops.
 #pragma once
 
 namespace nop {
 
 constexpr int TC_SLOTS = 130;                  // pixel slots per chunk block: x0 - 1 .. x0 + 128
 constexpr int TC_CHUNK_A = (TC_SLOTS + 1) * 16;  // bytes between chunk blocks of an input row
-constexpr int TC_ROWS = 4;                     // output rows per tile at most
-constexpr int TC_COMPUTE = 256;                // warps 0-7: staging, MMA issue (thread 0), epilogue
-constexpr int TC_THREADS = TC_COMPUTE + 32;    // warp 8: the weight-tap producer (lane 0)
+constexpr int TC_ROWS = 2;                     // output rows per tile at most
+constexpr int TC_RING = 6;                     // input-row slots: two tiles in flight
+constexpr int TC_EPI = 256;                    // warps 0-7: epilogue
+constexpr int TC_LOAD = 128;                   // warps 8-11: input-row loaders
+constexpr int TC_MMA_WARP = 12;                // lane 0 issues the MMAs; the warp owns the TMEM
+constexpr int TC_PROD_WARP = 13;               // lane 0 streams the weight taps
+constexpr int TC_THREADS = 14 * 32;
 constexpr int TC_MAX_BSTAGES = 4;
+constexpr int TC_BARS = 2 * TC_MAX_BSTAGES + 7;  // b_full, b_empty, a_full[2], mma_done[2], epi_done[2], final
 constexpr unsigned TC_SPIN_LIMIT = 1u << 20;   // bounded mbarrier waits (about a second at most)
 
 // Set by a CTA whose wait gave up; every later CTA of the path then returns at once.
@@ -63,18 +73,17 @@ template <int CO>
 __host__ __device__ constexpr int tc_chunk_b() { return CO * 16 + 16; }  // bytes between chunk blocks of a tap
 template <int KC, int CO>
 __host__ __device__ constexpr int tc_tap_bytes() { return KC * tc_chunk_b<CO>(); }
+// One staged output row: 128 pixels x CO FP32, pixel rows CO floats apart with their float4s
+// permuted (tc_swz), then bias and conditioning.
 template <int CO>
-__host__ __device__ constexpr int tc_stage_pitch() { return CO + 4; }
-// One staged output row (FP32, pixels tc_stage_pitch apart), then bias and conditioning.
-template <int CO>
-__host__ __device__ constexpr int tc_staged_bytes() { return 128 * tc_stage_pitch<CO>() * 4 + 2 * CO * 4; }
-// The staged row goes over input slots 0-3 (dead once a tile's MMAs are done; slots 4 and 5
-// may hold the next tile's first rows) where they hold it, else after the weight ring.
+__host__ __device__ constexpr int tc_staged_bytes() { return 128 * CO * 4 + 2 * CO * 4; }
+// The staged row goes over a tile's first two input slots where they hold it, else after the
+// weight ring.
 template <int KC, int CO>
-__host__ __device__ constexpr bool tc_stage_in_a() { return 4 * tc_row_bytes<KC>() >= tc_staged_bytes<CO>(); }
+__host__ __device__ constexpr bool tc_stage_in_a() { return 2 * tc_row_bytes<KC>() >= tc_staged_bytes<CO>(); }
 template <int KC, int CO, int S>
 __host__ __device__ constexpr int tc_main_bytes_s() {
-  return (TC_ROWS + 2) * tc_row_bytes<KC>() + S * tc_tap_bytes<KC, CO>() +
+  return TC_RING * tc_row_bytes<KC>() + S * tc_tap_bytes<KC, CO>() +
          (tc_stage_in_a<KC, CO>() ? 0 : tc_staged_bytes<CO>());
 }
 // Weight-ring stages: four where they fit in one CTA's shared memory (more taps in flight
@@ -83,17 +92,24 @@ template <int KC, int CO>
 __host__ __device__ constexpr int tc_bstages() {
   return tc_main_bytes_s<KC, CO, 4>() + 512 <= 227 * 1024 ? 4 : (tc_main_bytes_s<KC, CO, 3>() + 512 <= 227 * 1024 ? 3 : 2);
 }
-// The input slots, the weight ring, the staged row if separate; then 9 mbarriers, the TMEM
-// address and an abort word.
+// The input slots, the weight ring, the staged row if separate; then the mbarriers, the TMEM
+// address and an abort word (256 bytes), and alignment slack.
 template <int KC, int CO>
 __host__ __device__ constexpr int tc_main_bytes() { return tc_main_bytes_s<KC, CO, tc_bstages<KC, CO>()>(); }
 template <int KC, int CO>
-__host__ __device__ constexpr int tc_smem_bytes() { return tc_main_bytes<KC, CO>() + 128 + 128 /* alignment */; }
-// TMEM columns: a power of two >= 32 that holds TC_ROWS accumulators of CO columns.
+__host__ __device__ constexpr int tc_smem_bytes() { return tc_main_bytes<KC, CO>() + 256 + 128; }
+// TMEM columns: a power of two >= 32 that holds two buffers of TC_ROWS accumulators of CO columns.
 template <int CO>
 __host__ __device__ constexpr int tc_tmem_cols() {
-  constexpr int n = TC_ROWS * CO;
+  constexpr int n = 2 * TC_ROWS * CO;
   return n <= 32 ? 32 : (n <= 64 ? 64 : (n <= 128 ? 128 : (n <= 256 ? 256 : 512)));
+}
+// Position of float4 j of pixel px in its staged row: consecutive pixels writing the same j
+// (the TMEM read: one pixel per thread) and consecutive threads reading one pixel's float4s
+// (the coalesced write-out) both fall in distinct bank groups.
+template <int CO>
+__device__ __forceinline__ int tc_swz(int px, int j) {
+  return CO >= 32 ? (j ^ (px & 7)) : (j ^ ((px >> 1) & 3));
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -184,11 +200,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-// Bias, conditioning and scale for n consecutive accumulator columns from column n0 (raw bits
-// in r), into this pixel's staged row.
-template <int N>
+// Bias, conditioning and scale for N consecutive accumulator columns from column n0 (raw bits
+// in r), into pixel px's staged row.
+template <int CO, int N>
 __device__ __forceinline__ void tc_stage_cols(const uint32_t* r, int n0, const float* sbias, const float* sfilm,
-                                              float sc, float* stage_px) {
+                                              float sc, float* stage, int px) {
 #pragma unroll
   for (int j = 0; j < N; j += 4) {
     const int n = n0 + j;
@@ -199,48 +215,44 @@ __device__ __forceinline__ void tc_stage_cols(const uint32_t* r, int n0, const f
     o.y = (__uint_as_float(r[j + 1]) + bb.y + ff.y) * sc;
     o.z = (__uint_as_float(r[j + 2]) + bb.z + ff.z) * sc;
     o.w = (__uint_as_float(r[j + 3]) + bb.w + ff.w) * sc;
-    *reinterpret_cast<float4*>(stage_px + n) = o;
+    *reinterpret_cast<float4*>(stage + px * CO + 4 * tc_swz<CO>(px, n / 4)) = o;
   }
 }
 
 // The accumulator columns of one output row that the warps of pair half g (0 or 1) read from
 // their TMEM lane quarter and stage: for c_out = 96, 32 columns at 32 g and 16 at 64 + 16 g;
 // for 64, 32 at 32 g; for 16, all 16 in half 0. Loads of 32 columns start at multiples of 32
-// and loads of 16 at multiples of 16 (row offsets r c_out are multiples of 16 too).
+// and loads of 16 at multiples of 16 (row and buffer offsets are multiples of 16 too).
 template <int CO>
 __device__ __forceinline__ void tc_epilogue_row(uint32_t taddr_row, int g, const float* sbias, const float* sfilm,
-                                                float sc, float* stage_px) {
+                                                float sc, float* stage, int px) {
   static_assert(CO == 16 || CO == 64 || CO == 96, "output widths of the network");
   if constexpr (CO == 16) {
     if (g != 0) return;  // warp-uniform
     uint32_t r[16];
     tmem_ld16(taddr_row, r);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    tc_stage_cols<16>(r, 0, sbias, sfilm, sc, stage_px);
+    tc_stage_cols<CO, 16>(r, 0, sbias, sfilm, sc, stage, px);
   } else {
     uint32_t r[CO == 96 ? 48 : 32];
     tmem_ld32(taddr_row + 32 * g, r);
     if constexpr (CO == 96) tmem_ld16(taddr_row + 64 + 16 * g, r + 32);
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    tc_stage_cols<32>(r, 32 * g, sbias, sfilm, sc, stage_px);
-    if constexpr (CO == 96) tc_stage_cols<16>(r + 32, 64 + 16 * g, sbias, sfilm, sc, stage_px);
+    tc_stage_cols<CO, 32>(r, 32 * g, sbias, sfilm, sc, stage, px);
+    if constexpr (CO == 96) tc_stage_cols<CO, 16>(r + 32, 64 + 16 * g, sbias, sfilm, sc, stage, px);
   }
 }
 
-// The epilogue stages one output row (128 pixels x CO channels, FP32) in shared memory with
-// rows tc_stage_pitch(CO) floats apart: 16-byte aligned, and 8 consecutive pixels (one phase
-// of a 16-byte store) fall in distinct bank groups. It is then written out in 16-byte pieces
-// that consecutive threads take from consecutive addresses (coalesced): the FP32 result
-// (added to what is there with accumulate), its BF16 rounding and its SiLU in BF16, as
-// conv_epilogue does.
+// Writes out one staged output row (128 pixels from pix0) in 16-byte pieces that consecutive
+// threads take from consecutive addresses (coalesced): the FP32 result (added to what is
+// there with accumulate), its BF16 rounding and its SiLU in BF16, as conv_epilogue does.
 template <int CO>
 __device__ __forceinline__ void tc_store_row(const ConvArgs& p, const float* stage, size_t pix0, int tid) {
   constexpr int Q = CO / 4;
-  static_assert(tc_stage_pitch<CO>() == CO + 4, "staged pixel rows padded by one float4");
-  const size_t o0 = pix0 * CO;  // item idx = 4 channels: global offset 4 idx, staged at 4 (idx + px)
-  for (int idx = tid; idx < 128 * Q; idx += TC_COMPUTE) {
-    const int px = idx / Q;
-    float4 v = *reinterpret_cast<const float4*>(stage + 4 * (idx + px));
+  const size_t o0 = pix0 * CO;  // item idx = 4 channels: global offset 4 idx
+  for (int idx = tid; idx < 128 * Q; idx += TC_EPI) {
+    const int px = idx / Q, c4 = idx - px * Q;
+    const float4 v = *reinterpret_cast<const float4*>(stage + px * CO + 4 * tc_swz<CO>(px, c4));
     const size_t o = o0 + 4 * (size_t)idx;
     if (p.yf) {
       float4* y = reinterpret_cast<float4*>(p.yf + o);
@@ -261,10 +273,10 @@ __device__ __forceinline__ void tc_store_row(const ConvArgs& p, const float* sta
   }
 }
 
-// Named barrier 1 over the 256 compute threads (the producer warp takes no part), and the
-// same barrier reducing a flag: true if it holds on every compute thread.
-__device__ __forceinline__ void tc_compute_sync() { asm volatile("barrier.sync 1, 256;" ::: "memory"); }
-__device__ __forceinline__ bool tc_compute_and(bool v) {
+// Named barrier 1 over the 256 epilogue threads, and the same barrier reducing a flag: true if
+// it holds on every epilogue thread.
+__device__ __forceinline__ void tc_epi_sync() { asm volatile("barrier.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool tc_epi_and(bool v) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbarrier.red.and.pred q, 1, 256, p;\n\tselp.u32 %0, 1, 0, q;\n}"
@@ -283,6 +295,34 @@ __device__ __forceinline__ int tc_tile_rows(int r, int last, int H) {
   return n < H - h ? n : H - h;
 }
 
+// The tiles of one CTA, in order: rows [r0, r0 + rk), input slot base sk = 2 k mod 6, and
+// whether the first two input rows are the previous tile's last two (a full tile of the same
+// sample before it). Every role walks the same sequence.
+struct TcTiles {
+  int first, last, H;
+  int k, r0, rk, sk;
+  bool reuse;
+  __device__ __forceinline__ void start(int f, int l, int h) {
+    first = f;
+    last = l;
+    H = h;
+    k = 0;
+    r0 = f;
+    sk = 0;
+    reuse = false;
+    rk = r0 < last ? tc_tile_rows(r0, last, H) : 0;
+  }
+  __device__ __forceinline__ bool more() const { return r0 < last; }
+  __device__ __forceinline__ void next() {
+    const bool full = rk == TC_ROWS;
+    r0 += rk;
+    ++k;
+    sk = sk + 2 == TC_RING ? 0 : sk + 2;
+    reuse = full && r0 < last && r0 % H != 0;
+    rk = r0 < last ? tc_tile_rows(r0, last, H) : 0;
+  }
+};
+
 // Grid: (W / 128) x G CTAs of TC_THREADS; CTA (x, g) takes flattened output rows
 // [g N / G, (g + 1) N / G), N = B H, of column block x. p.wpk holds the weights packed by
 // tc_pack_kernel for (CI, CO, X2).
@@ -291,7 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
   constexpr int KC = (X2 ? 2 : 1) * CI / 8;    // 8-channel chunks of the contraction
   constexpr int K = 8 * KC;
   static_assert(K % 16 == 0 && CO % 16 == 0 && CO <= 256, "UMMA shape: K steps of 16, N a multiple of 16");
-  static_assert(TC_ROWS * CO <= 512, "accumulators fit in TMEM");
+  static_assert(2 * TC_ROWS * CO <= 512, "two accumulator buffers fit in TMEM");
   static_assert(!X2 || CI == 16, "the second input only on 16-channel layers");
   constexpr int ROW = tc_row_bytes<KC>();       // bytes per staged input row
   constexpr int TAP = tc_tap_bytes<KC, CO>();   // bytes per staged weight tap
@@ -299,29 +339,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
   constexpr int COLS = tc_tmem_cols<CO>();
   constexpr uint32_t IDESC = umma_idesc_bf16<128, CO>();
   constexpr int S = tc_bstages<KC, CO>();
-  constexpr int PITCH = tc_stage_pitch<CO>();
+  constexpr bool SIA = tc_stage_in_a<KC, CO>();
+  constexpr int PER_ROW = TC_SLOTS * KC;        // 16-byte copies per input row
+  static_assert(PER_ROW >= TC_LOAD, "a loader's copies advance by one row at most");
   extern __shared__ __align__(128) unsigned char tc_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 127) & ~(uintptr_t)127);
   unsigned char* sA = base;
-  unsigned char* sB = base + (TC_ROWS + 2) * ROW;
-  float* stage = reinterpret_cast<float*>(tc_stage_in_a<KC, CO>() ? base : sB + S * TAP);
-  float* sbias = stage + 128 * PITCH;  // bias (0 if none), then the conditioning times alpha
-  float* sfilm = sbias + CO;
-  // b_full[S], b_empty[S], done (9 at most), then the TMEM address and the abort word
+  unsigned char* sB = base + TC_RING * ROW;
+  float* stage_sep = reinterpret_cast<float*>(sB + S * TAP);  // the staged row when not in the input slots
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + tc_main_bytes<KC, CO>());
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_MAX_BSTAGES + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + TC_BARS);
   volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  const uint32_t done_bar = smem_u32(&bars[2 * S]);
   auto b_full = [&](int s) { return smem_u32(&bars[s]); };
   auto b_empty = [&](int s) { return smem_u32(&bars[S + s]); };
+  auto a_full = [&](int j) { return smem_u32(&bars[2 * S + j]); };
+  auto mma_done = [&](int j) { return smem_u32(&bars[2 * S + 2 + j]); };
+  auto epi_done = [&](int j) { return smem_u32(&bars[2 * S + 4 + j]); };
+  const uint32_t final_bar = smem_u32(&bars[2 * S + 6]);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * 128;
   const int N = p.B * p.H;
   const int first = (int)((long long)blockIdx.y * N / gridDim.y);
   const int last = (int)((long long)(blockIdx.y + 1) * N / gridDim.y);
-  int ntiles = 0;
-  for (int r = first; r < last; r += tc_tile_rows(r, last, p.H)) ++ntiles;
 
   if (tid == 0) {
     *abort_word = *(volatile int*)&tc_fault_flag;  // an earlier CTA's wait gave up: do nothing
@@ -329,25 +369,160 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
       mbar_init(b_full(s), 1);   // the producer's arrival plus the tap's bytes
       mbar_init(b_empty(s), 1);  // the commit of the MMAs that read the stage
     }
-    mbar_init(done_bar, 1);
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(a_full(j), TC_LOAD);   // every loader thread, once its copies have landed
+      mbar_init(mma_done(j), 1);       // the commit after the tile's MMAs
+      mbar_init(epi_done(j), TC_EPI);  // every epilogue thread, once done with the buffer
+    }
+    mbar_init(final_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (*abort_word || ntiles == 0) return;  // uniform over the CTA: nothing allocated or in flight yet
-  if (warp == 0) {
+  if (*abort_word || first >= last) return;  // uniform over the CTA: nothing allocated or in flight yet
+  if (warp == TC_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
 
   bool ok = true;
-  if (warp == TC_COMPUTE / 32) {
-    if (lane == 0) {  // the producer: tap T of the run (tile T / 9, tap T % 9) into stage T % S
+  TcTiles tl;
+  tl.start(first, last, p.H);
+  if (warp < TC_EPI / 32) {
+    // ------------------------------------------------------------ epilogue warps 0-7
+    const int quarter = warp & 3, half = warp >> 2;
+    const int px = 32 * quarter + lane;  // this thread's TMEM lane: pixel x0 + px
+    for (; tl.more(); tl.next()) {
+      const int j = tl.k & 1;
+      const bool fin = mbar_wait(mma_done(j), (uint32_t)((tl.k >> 1) & 1));
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!tc_epi_and(fin)) {  // uniform over the epilogue warps
+        ok = false;
+        break;
+      }
+      float* stage = SIA ? reinterpret_cast<float*>(sA + tl.sk * ROW) : stage_sep;
+      float* sbias = stage + 128 * CO;  // bias (0 if none), then the conditioning times alpha
+      float* sfilm = sbias + CO;
+      const int b = tl.r0 / p.H;
+      const float al = p.film ? p.alpha[b] : 0.0f;
+      const float sc = p.scale_alpha ? p.alpha[b] : 1.0f;
+      for (int n = tid; n < CO; n += TC_EPI) {
+        sbias[n] = p.bias ? p.bias[n] : 0.0f;
+        sfilm[n] = p.film ? al * p.film[n] : 0.0f;
+      }
+      tc_epi_sync();
+#pragma unroll 1
+      for (int r = 0; r < tl.rk; ++r) {
+        const uint32_t row_addr =
+            tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)((j * TC_ROWS + r) * CO);
+        tc_epilogue_row<CO>(row_addr, half, sbias, sfilm, sc, stage, px);
+        tc_epi_sync();
+        tc_store_row<CO>(p, stage, (size_t)(tl.r0 + r) * p.W + x0, tid);
+        tc_epi_sync();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(epi_done(j));  // this thread's accumulator reads and staged-row reads are done
+    }
+  } else if (warp < (TC_EPI + TC_LOAD) / 32) {
+    // ------------------------------------------------------------ loader warps 8-11
+    const int ltid = tid - TC_EPI;
+    const uint32_t sA32 = smem_u32(sA);
+    for (; tl.more(); tl.next()) {
+      const int j = tl.k & 1;
+      // slots of input rows 2, 3: tile k - 2's first two, which held its staged rows
+      if (tl.k >= 2 && !mbar_wait(epi_done(j), (uint32_t)(((tl.k >> 1) + 1) & 1))) {
+        ok = false;
+        break;
+      }
+      // slots of input rows 0, 1 when not reused: tile k - 1's last two, read by its MMAs
+      if (!tl.reuse && tl.k >= 1 && !mbar_wait(mma_done(j ^ 1), (uint32_t)(((tl.k - 1) >> 1) & 1))) {
+        ok = false;
+        break;
+      }
+      const int b = tl.r0 / p.H, h0 = tl.r0 - b * p.H;
+      // item (i, pixel slot, chunk), chunk fastest; each loader steps TC_LOAD items at a time
+      const int i0 = tl.reuse ? 2 : 0;
+      const int n_items = (tl.rk + 2 - i0) * PER_ROW;
+      int i = i0, rem = ltid;
+      size_t row_px = (size_t)(b * p.H + wrap1(h0 - 1 + i, p.H)) * p.W;  // first pixel of input row i
+      int q = tl.sk + i >= TC_RING ? tl.sk + i - TC_RING : tl.sk + i;    // its slot
+      for (int idx = ltid; idx < n_items; idx += TC_LOAD) {
+        const int sl = rem / KC, c = rem - sl * KC;
+        const size_t px = row_px + wrap1(x0 - 1 + sl, p.W);
+        const bf16* src = (X2 && c >= CI / 8) ? p.x2 + px * CI + 8 * (c - CI / 8) : p.x + px * CI + 8 * c;
+        tc_cp16(sA32 + (uint32_t)(q * ROW + c * TC_CHUNK_A + sl * 16), src);
+        rem += TC_LOAD;
+        if (rem >= PER_ROW) {
+          rem -= PER_ROW;
+          ++i;
+          row_px = (size_t)(b * p.H + wrap1(h0 - 1 + i, p.H)) * p.W;
+          q = q + 1 == TC_RING ? 0 : q + 1;
+        }
+      }
+      tc_cp_done();  // this thread's copies have landed and are visible to the tensor cores
+      mbar_arrive(a_full(j));
+    }
+  } else if (warp == TC_MMA_WARP) {
+    // ------------------------------------------------------------ MMA issuer (lane 0)
+    if (lane == 0) {
+      // Descriptors of input slot 0 and weight stage 0 at their first chunk: every operand
+      // start is a 16-byte multiple from them, added to the start-address field (address / 16,
+      // 14 bits, which holds every shared-memory address).
+      const uint64_t a0 = umma_desc(smem_u32(sA), LBO_A, SBO);
+      const uint64_t b0 = umma_desc(smem_u32(sB), LBO_B, SBO);
+      for (; tl.more() && ok; tl.next()) {
+        const int j = tl.k & 1;
+        if (!mbar_wait(a_full(j), (uint32_t)((tl.k >> 1) & 1)) ||
+            (tl.k >= 2 && !mbar_wait(epi_done(j), (uint32_t)(((tl.k >> 1) + 1) & 1)))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dcol = tmem + (uint32_t)(j * TC_ROWS * CO);
+        for (int t = 0; t < 9; ++t) {
+          const int T = 9 * tl.k + t, s = T % S;
+          if (!mbar_wait(b_full(s), (uint32_t)((T / S) & 1))) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int dy = t / 3 - 1, dx = t % 3 - 1;
+          const uint64_t bt = b0 + (uint64_t)((s * TAP) >> 4);
+#pragma unroll
+          for (int r = 0; r < TC_ROWS; ++r) {
+            if (r < tl.rk) {
+              int q = tl.sk + r + 1 + dy;  // the slot of input row r + 1 + dy
+              q = q >= TC_RING ? q - TC_RING : q;
+              const uint64_t at = a0 + (uint64_t)((q * ROW + (1 + dx) * 16) >> 4);
+#pragma unroll
+              for (int kk = 0; kk < K / 16; ++kk)
+                umma_bf16(dcol + (uint32_t)(r * CO), at + (uint64_t)((kk * 2 * LBO_A) >> 4),
+                          bt + (uint64_t)((kk * 2 * LBO_B) >> 4), IDESC, (t > 0 || kk > 0) ? 1u : 0u);
+            }
+          }
+          umma_commit(b_empty(s));  // the stage is free once these MMAs have read it
+        }
+        if (!ok) break;
+        umma_commit(mma_done(j));  // the tile's accumulators are complete once this arrives
+      }
+      umma_commit(final_bar);  // every MMA issued above has completed once this arrives
+      if (!mbar_wait(final_bar, 0)) ok = false;
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ weight producer (lane 0)
+    if (lane == 0) {  // tap T of the run (tile T / 9, tap T % 9) into stage T % S
+      int ntiles = 0;
+      for (; tl.more(); tl.next()) ++ntiles;
       int last_tap[TC_MAX_BSTAGES] = {-1, -1, -1, -1};
       for (int T = 0; T < 9 * ntiles; ++T) {
         const int s = T % S;
-        if (T >= S && !mbar_wait(b_empty(s), ((T - S) / S) & 1)) {
+        if (T >= S && !mbar_wait(b_empty(s), (uint32_t)(((T - S) / S) & 1))) {
           ok = false;
           break;
         }
@@ -355,110 +530,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
         tc_bulk_copy(smem_u32(sB + s * TAP), p.wpk + (size_t)(T % 9) * TAP, (uint32_t)TAP, b_full(s));
         last_tap[s] = T;
       }
-      if (!ok)  // the last copy into each stage has landed before the CTA ends
-        for (int s = 0; s < S; ++s)
-          if (last_tap[s] >= 0) mbar_wait(b_full(s), (last_tap[s] / S) & 1);
+      // the last copy into each stage has landed before the CTA ends
+      for (int s = 0; s < S; ++s)
+        if (last_tap[s] >= 0 && !mbar_wait(b_full(s), (uint32_t)((last_tap[s] / S) & 1))) ok = false;
     }
     __syncwarp();
-  } else {
-    bool reuse = false;  // this tile's first two input rows are the last two of the previous tile
-    int tile = 0;
-    for (int r0 = first; r0 < last; ++tile) {
-      const int rk = tc_tile_rows(r0, last, p.H);
-      const int b = r0 / p.H, h0 = r0 - b * p.H;
-      // Input rows h0 - 1 .. h0 + rk in slots 0 .. rk + 1: periodic in h and in x; with X2,
-      // chunks KC / 2 .. KC - 1 from the second tensor.
-      const int i0 = reuse ? 2 : 0;
-      if (reuse) {  // slots 4, 5 -> 0, 1
-        const uint4* src = reinterpret_cast<const uint4*>(sA + 4 * ROW);
-        uint4* dst = reinterpret_cast<uint4*>(sA);
-        for (int k = tid; k < 2 * ROW / 16; k += TC_COMPUTE) dst[k] = src[k];
-      }
-      {
-        // item (i, slot, chunk), chunk fastest; each thread steps TC_COMPUTE items at a time
-        // (fewer than one row's items, so the row advances by one at most)
-        constexpr int PER_ROW = TC_SLOTS * KC;
-        static_assert(PER_ROW >= TC_COMPUTE, "a thread's items advance by one row at most");
-        const int n_items = (rk + 2 - i0) * PER_ROW;
-        const uint32_t sA32 = smem_u32(sA);
-        int i = i0, rem = tid;
-        size_t row_px = (size_t)(b * p.H + wrap1(h0 - 1 + i, p.H)) * p.W;  // first pixel of input row i
-        for (int idx = tid; idx < n_items; idx += TC_COMPUTE) {
-          const int sl = rem / KC, c = rem - sl * KC;
-          const size_t px = row_px + wrap1(x0 - 1 + sl, p.W);
-          const bf16* src = (X2 && c >= CI / 8) ? p.x2 + px * CI + 8 * (c - CI / 8) : p.x + px * CI + 8 * c;
-          tc_cp16(sA32 + (uint32_t)(i * ROW + c * TC_CHUNK_A + sl * 16), src);
-          rem += TC_COMPUTE;
-          if (rem >= PER_ROW) {
-            rem -= PER_ROW;
-            ++i;
-            row_px = (size_t)(b * p.H + wrap1(h0 - 1 + i, p.H)) * p.W;
-          }
-        }
-      }
-      tc_cp_done();  // this thread's input rows (and moved rows) are visible to the tensor cores
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      tc_compute_sync();  // every input row in place; the last tile's accumulators all read
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t tmem = *tmem_slot;
-      if (tid == 0) {  // the MMA issuer
-        // Descriptors of input slot 0 and weight stage 0 at their first chunk: every operand
-        // start is a 16-byte multiple from them, added to the start-address field (address / 16,
-        // 14 bits, which holds every shared-memory address).
-        const uint64_t a0 = umma_desc(smem_u32(sA), LBO_A, SBO);
-        const uint64_t b0 = umma_desc(smem_u32(sB), LBO_B, SBO);
-        for (int t = 0; t < 9 && ok; ++t) {
-          const int T = 9 * tile + t, s = T % S;
-          if (!mbar_wait(b_full(s), (T / S) & 1)) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int dy = t / 3 - 1, dx = t % 3 - 1;
-          const uint64_t bt = b0 + (uint64_t)((s * TAP) >> 4);
-          const uint64_t at = a0 + (uint64_t)(((1 + dy) * ROW + (1 + dx) * 16) >> 4);
-#pragma unroll
-          for (int r = 0; r < TC_ROWS; ++r) {
-            if (r < rk) {
-#pragma unroll
-              for (int kk = 0; kk < K / 16; ++kk)
-                umma_bf16(tmem + (uint32_t)(r * CO), at + (uint64_t)((r * ROW + kk * 2 * LBO_A) >> 4),
-                          bt + (uint64_t)((kk * 2 * LBO_B) >> 4), IDESC, (t > 0 || kk > 0) ? 1u : 0u);
-            }
-          }
-          umma_commit(b_empty(s));  // the stage is free once these MMAs have read it
-        }
-        umma_commit(done_bar);  // arrives once every MMA issued above has completed
-      }
-      __syncwarp();
-      const bool fin = mbar_wait(done_bar, (uint32_t)(tile & 1));
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (!tc_compute_and(ok && fin)) {  // uniform over the compute warps
-        ok = false;
-        break;
-      }
-      // Epilogue: the MMAs have completed, so slots 0-3 are free for the staged rows.
-      const float al = p.film ? p.alpha[b] : 0.0f;
-      const float sc = p.scale_alpha ? p.alpha[b] : 1.0f;
-      for (int n = tid; n < CO; n += TC_COMPUTE) {
-        sbias[n] = p.bias ? p.bias[n] : 0.0f;
-        sfilm[n] = p.film ? al * p.film[n] : 0.0f;
-      }
-      tc_compute_sync();
-      const int quarter = warp & 3, half = warp >> 2;
-      const int px = 32 * quarter + lane;  // this thread's TMEM lane: pixel x0 + px
-#pragma unroll 1
-      for (int r = 0; r < rk; ++r) {
-        const uint32_t row_addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(r * CO);
-        tc_epilogue_row<CO>(row_addr, half, sbias, sfilm, sc, stage + px * PITCH);
-        tc_compute_sync();
-        tc_store_row<CO>(p, stage, (size_t)(r0 + r) * p.W + x0, tid);
-        tc_compute_sync();
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      reuse = rk == TC_ROWS && r0 + rk < last && (r0 + rk) % p.H != 0;
-      r0 += rk;
-    }
   }
   const bool all_ok = __syncthreads_and(ok ? 1 : 0) != 0;
   if (!all_ok && tid == 0) {
@@ -468,8 +544,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) conv_tc_kernel(const __grid_con
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot), "r"(COLS) : "memory");
+  if (warp == TC_MMA_WARP)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
 }
 
 // The weights of a (CI, CO, X2) layer in the layout of the kernel's weight ring:
