@@ -513,7 +513,24 @@ def run_surrogate(alphas=(0.1, 0.3, 0.45), seed: int = 777):
                        "channels (~0.5M), which left the rollout error 2-4x above the gate",
             "gates": gates, "by_alpha": runs, "speedup": min(r["speedup"] for r in runs),
             "kernels": surrogate.time_kernels(theta),
-            "conv_level0_b16": surrogate.time_conv(16)}
+            "conv_level0_b16": conv_with_roofline(surrogate.time_conv(16))}
+
+
+def conv_with_roofline(c):
+    """The tcgen05 convolution's throughput against the measured bf16 peaks: the sustained one
+    (a kernel inside a long step) and the burst one."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        sus, burst, kind = float(d["bf16_tflops_sustained"]), float(d["bf16_tflops"]), "measured"
+    else:
+        sus, burst, kind = 1700.0, 1900.0, "fallback"
+    c = dict(c)
+    c["frac_of_sustained"] = c["tflops"] / sus
+    c["frac_of_burst"] = c["tflops"] / burst
+    c["peak_kind"] = kind
+    return c
 
 
 def cpu_oracle_rate(target_s: float = 8.0, n_sample: int = 2048):

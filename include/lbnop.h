@@ -192,8 +192,7 @@ lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float*
  * after each [c_out][8] block. lbnop_conv3x3_packed then runs conv3x3 with it: d_packed is
  * read where the tensor-core path takes the shape (W a multiple of 128, H a multiple of 4),
  * d_w elsewhere; d_packed may be NULL, which keeps every shape on the mma.sync kernels.
- * lbnop_conv3x3 packs into a stream-ordered temporary (cudaMallocAsync) on each call where
- * the tensor-core path applies. */
+ * lbnop_conv3x3 is lbnop_conv3x3_packed with d_packed = NULL (the library allocates nothing). */
 size_t lbnop_conv3x3_packed_bytes(int32_t c_in, int32_t c_out);
 lbch_status lbnop_conv3x3_pack(const uint16_t* d_w, int32_t c_in, int32_t c_out, void* d_packed, void* cuda_stream);
 lbch_status lbnop_conv3x3_packed(const uint16_t* d_x, const uint16_t* d_w, const void* d_packed, const float* d_bias,

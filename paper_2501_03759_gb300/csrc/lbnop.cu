@@ -1915,28 +1915,8 @@ lbch_status lbnop_conv3x3_packed(const uint16_t* d_x, const uint16_t* d_w, const
 
 lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float* d_bias, int32_t B, int32_t H,
                           int32_t W, int32_t c_in, int32_t c_out, float* d_y, void* cuda_stream) {
-  if (!d_x || !d_w || !d_y || op_check(B, H, W, c_in, c_out) != LBCH_OK) return LBCH_EINVAL;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  ConvArgs probe{};
-  probe.x = (const bf16*)d_x;
-  probe.wpk = reinterpret_cast<const unsigned char*>(d_w);  // stands for the packed copy's alignment
-  probe.W = W;
-  probe.H = H;
-  void* pk = nullptr;
-  if (tc_applies(probe, c_in, c_out)) {  // the tensor-core path: the weights packed for it, stream-ordered
-    if (cudaMallocAsync(&pk, tc_pack_bytes(c_in, c_out, false), s) != cudaSuccess) {
-      cudaGetLastError();
-      return LBCH_ECUDA;
-    }
-    lbch_status st = lbnop_conv3x3_pack(d_w, c_in, c_out, pk, cuda_stream);
-    if (st != LBCH_OK) {
-      cudaFreeAsync(pk, s);
-      return st;
-    }
-  }
-  const lbch_status st = lbnop_conv3x3_packed(d_x, d_w, pk, d_bias, B, H, W, c_in, c_out, d_y, cuda_stream);
-  if (pk && cudaFreeAsync(pk, s) != cudaSuccess) return LBCH_ECUDA;
-  return st;
+  // no packed weights: the mma.sync kernels for every shape (the library allocates nothing)
+  return lbnop_conv3x3_packed(d_x, d_w, nullptr, d_bias, B, H, W, c_in, c_out, d_y, cuda_stream);
 }
 
 lbch_status lbnop_conv3x3_bwd_data(const uint16_t* d_dy, const uint16_t* d_w, int32_t B, int32_t H, int32_t W,

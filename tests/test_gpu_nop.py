@@ -373,8 +373,11 @@ def test_conv_tc_forward(ci, co, shape):
     b = W.bf16_exact((co,), 23, 1.0).astype(np.float32)
     y = torch.empty((B, H, Wd, co), dtype=torch.float32, device="cuda")
     xd, wd, bt = dev_bf16(x), dev_bf16(w), torch.from_numpy(b).cuda()
+    pk = torch.empty(lbnop.lbnop_conv3x3_packed_bytes(ci, co), dtype=torch.uint8, device="cuda")
+    lbnop.lbnop_conv3x3_pack(wd.data_ptr(), ci, co, pk.data_ptr(), stream())
     before = lbnop.lbnop_tc_launches()
-    lbnop.lbnop_conv3x3(xd.data_ptr(), wd.data_ptr(), bt.data_ptr(), B, H, Wd, ci, co, y.data_ptr(), stream())
+    lbnop.lbnop_conv3x3_packed(xd.data_ptr(), wd.data_ptr(), pk.data_ptr(), bt.data_ptr(), B, H, Wd, ci, co,
+                               y.data_ptr(), stream())
     torch.cuda.synchronize()
     assert lbnop.lbnop_tc_launches() == before + 1  # the tensor-core path ran
     ref = N.conv(x, w, b)
@@ -385,7 +388,8 @@ def test_conv_tc_forward(ci, co, shape):
 @pytest.mark.parametrize("ci,co", [(96, 96), (16, 64)])
 def test_conv_packed_weights(ci, co):
     """Weights packed once (lbnop_conv3x3_pack) drive the tensor-core path; without a packed
-    copy the same shape runs on the mma.sync kernels. Both agree with the oracle's conv."""
+    copy (and through lbnop_conv3x3) the same shape runs on the mma.sync kernels. All agree
+    with the oracle's conv."""
     B, H, Wd = 2, 8, 256
     x = W.bf16_exact((B, H, Wd, ci), 31, 1.0)
     w = W.bf16_exact((9, co, ci), 32, 0.25)
@@ -405,6 +409,12 @@ def test_conv_packed_weights(ci, co):
         torch.cuda.synchronize()
         assert lbnop.lbnop_tc_launches() - before == (1 if packed else 0)
         assert np.abs(y.cpu().numpy() - ref).max() <= bound
+    y = torch.empty((B, H, Wd, co), dtype=torch.float32, device="cuda")
+    before = lbnop.lbnop_tc_launches()
+    lbnop.lbnop_conv3x3(xd.data_ptr(), wd.data_ptr(), None, B, H, Wd, ci, co, y.data_ptr(), stream())
+    torch.cuda.synchronize()
+    assert lbnop.lbnop_tc_launches() == before
+    assert np.abs(y.cpu().numpy() - ref).max() <= bound
     # the packed layout itself: tap t, chunk c, output channel n holds w[t][n][8 c .. 8 c + 7]
     raw = pk.cpu().numpy().view(np.uint16).reshape(9, ci // 8, co + 1, 8)
     assert (raw[:, :, co, :] == 0).all()
