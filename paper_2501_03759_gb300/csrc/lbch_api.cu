@@ -388,7 +388,7 @@ lbch_status ctx_setup(const lbch_params* p, char* state, char* scratch, cudaStre
   f.ps = c->ps;
   f.nx = p->nx;
   f.ny = p->ny;
-  f.n_strips = (p->nx + OUT_W - 1) / OUT_W;
+  f.n_strips = n_strips_for(p->nx);
   const long long resident = (long long)sms * per_sm * STEP_WARPS;
   long long segs = resident / f.n_strips;
   if (segs < 1) segs = 1;

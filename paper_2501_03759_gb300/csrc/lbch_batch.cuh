@@ -90,7 +90,7 @@ lbch_params field_params(const lbch_params* common, int32_t nx, int32_t ny, doub
   return p;
 }
 
-int n_strips_of(int nx) { return (nx + OUT_W - 1) / OUT_W; }
+int n_strips_of(int nx) { return n_strips_for(nx); }
 
 // Task list for a rows-per-warp target: largest fields first (longest work first),
 // and within a field the strips of a segment next to each other (they share halos).

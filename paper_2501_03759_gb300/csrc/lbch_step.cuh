@@ -33,6 +33,12 @@ namespace lbch {
 constexpr int STRIP_W = 128;                 // columns per warp strip
 constexpr int HALO_W = 4;                    // halo columns on each side
 constexpr int OUT_W = STRIP_W - 2 * HALO_W;  // output columns per strip
+// A field exactly STRIP_W wide is one strip that covers the whole periodic row: the lane
+// neighbour exchanges below rotate (lane 0's left neighbour is lane 31), so every column is
+// computed from its true periodic neighbours and all STRIP_W columns are output. In a strip
+// of a wider (or narrower) field the rotated-in values reach only halo columns: an output
+// column depends on columns at most HALO_W (the stencil depth) away, inside the strip.
+__host__ __device__ constexpr int n_strips_for(int nx) { return nx == STRIP_W ? 1 : (nx + OUT_W - 1) / OUT_W; }
 constexpr int STEP_WARPS = 4;                // warps per CTA
 // Pipeline depth per storage (measured on GB300 at 8192^2): fetch one row ahead and collide
 // row r-3 right after its grad mu_beta. The 16-bit storages keep 12 warps per SM (their
@@ -82,12 +88,20 @@ __device__ __forceinline__ int imod(int v, int n) {
   return r < 0 ? r + n : r;
 }
 
+// The value of the lane to the left (lane 31 for lane 0) and to the right (lane 0 for 31).
+__device__ __forceinline__ float from_lane_left(float v) {
+  return __shfl_sync(FULL, v, (threadIdx.x + 31) & 31);
+}
+__device__ __forceinline__ float from_lane_right(float v) {
+  return __shfl_sync(FULL, v, (threadIdx.x + 1) & 31);
+}
+
 // Left/right neighbour sums and differences of a per-column quantity over the strip:
 // s_j = q_{j-1} + q_{j+1}, d_j = q_{j+1} - q_{j-1} for this lane's columns j = 0..3 (pairs
 // (0, 1) and (2, 3)), with the outer neighbours from the adjacent lanes.
 __device__ __forceinline__ void neighbours(const F2 (&q)[2], F2 (&s)[2], F2 (&d)[2]) {
-  const float left = __shfl_up_sync(FULL, q[1].y, 1);
-  const float right = __shfl_down_sync(FULL, q[0].x, 1);
+  const float left = from_lane_left(q[1].y);
+  const float right = from_lane_right(q[0].x);
   const F2 A = f2(left, q[0].x), B = f2(q[0].y, q[1].x), C = f2(q[1].y, right);
   s[0] = A + B;
   s[1] = B + C;
@@ -165,12 +179,12 @@ __device__ __forceinline__ void issue_row(const Field& fd, float4* slot, int lan
 // Pull shift along x of a per-column quantity of the strip: column j takes column j - 1
 // (c_x = 1) or column j + 1 (c_x = -1).
 __device__ __forceinline__ void from_left(F2 (&v)[2]) {
-  const float prev = __shfl_up_sync(FULL, v[1].y, 1);
+  const float prev = from_lane_left(v[1].y);
   v[1] = f2(v[0].y, v[1].x);
   v[0] = f2(prev, v[0].x);
 }
 __device__ __forceinline__ void from_right(F2 (&v)[2]) {
-  const float next = __shfl_down_sync(FULL, v[0].x, 1);
+  const float next = from_lane_right(v[0].x);
   v[0] = f2(v[0].y, v[1].x);
   v[1] = f2(v[1].y, next);
 }
@@ -519,12 +533,12 @@ __device__ __forceinline__ void collide_row(const StepArgs& a, const Field& fd, 
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const F2(&m)[2] = r == 0 ? mu_m : (r == 1 ? mu_c : mu_p);
-      ext[r][0] = __shfl_up_sync(FULL, m[1].y, 1);
+      ext[r][0] = from_lane_left(m[1].y);
       ext[r][1] = m[0].x;
       ext[r][2] = m[0].y;
       ext[r][3] = m[1].x;
       ext[r][4] = m[1].y;
-      ext[r][5] = __shfl_down_sync(FULL, m[0].x, 1);
+      ext[r][5] = from_lane_right(m[0].x);
     }
 #pragma unroll
     for (int i = 1; i < 9; ++i)
@@ -550,16 +564,18 @@ __device__ __forceinline__ void step_warp(const StepArgs& a, const Field& fd, in
   constexpr int PF_DIST = PP::PF_DIST, COLLIDE_LAG = PP::LAG, SLOTS = PP::SLOTS, SLOT_F4 = PP::SLOT_F4;
   const int y0 = seg * fd.seg_len;
   const int y1 = min(y0 + fd.seg_len, fd.ny);
-  const int xs = strip * OUT_W - HALO_W;  // strip start column (before wrap)
+  const bool full_row = fd.nx == STRIP_W;  // one strip over the whole periodic row
+  const int xs = full_row ? 0 : strip * OUT_W - HALO_W;  // strip start column (before wrap)
 
   Cols cl;
   cl.c0 = imod(xs + 4 * lane, fd.nx);
 #pragma unroll
   for (int k = 0; k < 6; ++k) cl.cs[k] = imod(xs + 4 * lane + k - 1, fd.nx);
 
-  // Output columns of this lane: strip columns 4 lane + j in [HALO_W, STRIP_W - HALO_W).
-  const int ocol0 = strip * OUT_W + 4 * lane - HALO_W;  // global column of element 0
-  const bool lane_out = lane >= 1 && lane <= 30 && ocol0 < fd.nx;
+  // Output columns of this lane: strip columns 4 lane + j in [HALO_W, STRIP_W - HALO_W), or
+  // all of them for a full row.
+  const int ocol0 = xs + 4 * lane;  // global column of element 0
+  const bool lane_out = full_row || (lane >= 1 && lane <= 30 && ocol0 < fd.nx);
   const int nvalid = min(4, fd.nx - ocol0);
 
   // Rolling accumulators (see the header comment): index 1 = row completing next, 0 = row
