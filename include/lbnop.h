@@ -211,6 +211,14 @@ lbch_status lbnop_conv3x3_bwd_weight(const uint16_t* d_x, const uint16_t* d_dy, 
  * others run on mma.sync kernels. A diagnostic for tests and benchmarks. */
 int64_t lbnop_tc_launches(void);
 
+/* 1 if a tcgen05 convolution of this process (on the current device) gave up one of its
+ * bounded waits (about a second each): its outputs are invalid, and every later launch of that
+ * path returns without work. 0 if none did, -1 if the flag cannot be read. Read it after
+ * synchronising the stream the convolutions ran on. The calls of an lbnop context that
+ * synchronise (set_params, backward, train_step, grad_norm, get_grads, and
+ * leap_run_judged at its end) check it themselves and fail with LBCH_ECUDA. */
+int32_t lbnop_tc_fault(void);
+
 const char* lbnop_last_error(const lbnop_ctx* c);
 void lbnop_destroy(lbnop_ctx* c);
 

@@ -1261,6 +1261,18 @@ lbch_status done(lbnop_ctx* c, const char* what) {
   return cuda_bad(c, cudaGetLastError(), what) ? LBCH_ECUDA : LBCH_OK;
 }
 
+// After a synchronisation that covers this context's convolutions: true (and the context
+// failed) if a tensor-core convolution of this process gave up a bounded wait (its outputs are
+// invalid; tc_fault_flag), or if the flag cannot be read.
+bool tc_faulted(lbnop_ctx* c, const char* what) {
+  int v = 0;
+  if (cuda_bad(c, cudaMemcpyFromSymbol(&v, tc_fault_flag, sizeof(int)), what)) return true;
+  if (!v) return false;
+  c->failed = true;
+  set_err(c, "%s: a tensor-core convolution gave up a bounded wait; its results are invalid", what);
+  return true;
+}
+
 // Level dimensions for `batch` fields.
 struct Dims {
   int B, h[4], w[4];
@@ -1580,7 +1592,7 @@ lbch_status lbnop_set_params(lbnop_ctx* c, const float* h_theta) {
   c->adam_t = 0;
   int bad = 0;
   if (cuda_bad(c, cudaMemcpyAsync(&bad, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "set_params") ||
-      cuda_bad(c, cudaStreamSynchronize(c->stream), "set_params: sync"))
+      cuda_bad(c, cudaStreamSynchronize(c->stream), "set_params: sync") || tc_faulted(c, "set_params"))
     return LBCH_ECUDA;
   if (bad) {
     set_err(c, "set_params: NaN or Inf in the parameters");
@@ -1624,7 +1636,7 @@ lbch_status lbnop_backward(lbnop_ctx* c, const float* d_phi, const double* h_alp
   if ((st = done(c, "backward: launch")) != LBCH_OK) return st;
   if (h_loss) {
     if (cuda_bad(c, cudaMemcpyAsync(h_loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss") ||
-        cuda_bad(c, cudaStreamSynchronize(c->stream), "backward: sync"))
+        cuda_bad(c, cudaStreamSynchronize(c->stream), "backward: sync") || tc_faulted(c, "backward"))
       return LBCH_ECUDA;
   }
   return LBCH_OK;
@@ -1635,7 +1647,7 @@ lbch_status lbnop_get_grads(lbnop_ctx* c, float* h_grad) {
   if (st != LBCH_OK) return st;
   if (!h_grad) return LBCH_EINVAL;
   if (cuda_bad(c, cudaMemcpyAsync(h_grad, c->grad, c->n_params * 4, cudaMemcpyDeviceToHost, c->stream), "grads") ||
-      cuda_bad(c, cudaStreamSynchronize(c->stream), "get_grads: sync"))
+      cuda_bad(c, cudaStreamSynchronize(c->stream), "get_grads: sync") || tc_faulted(c, "get_grads"))
     return LBCH_ECUDA;
   return LBCH_OK;
 }
@@ -1672,7 +1684,7 @@ lbch_status lbnop_grad_norm(lbnop_ctx* c, double* h_norm) {
     return LBCH_EINVAL;
   }
   if (cuda_bad(c, cudaMemcpyAsync(h_norm, c->gnorm, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "gnorm") ||
-      cuda_bad(c, cudaStreamSynchronize(c->stream), "grad_norm: sync"))
+      cuda_bad(c, cudaStreamSynchronize(c->stream), "grad_norm: sync") || tc_faulted(c, "grad_norm"))
     return LBCH_ECUDA;
   return LBCH_OK;
 }
@@ -1684,7 +1696,7 @@ lbch_status lbnop_train_step(lbnop_ctx* c, const float* d_phi, const double* h_a
   if ((st = lbnop_adam(c, lr)) != LBCH_OK) return st;
   if (h_loss) {
     if (cuda_bad(c, cudaMemcpyAsync(h_loss, c->loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "loss") ||
-        cuda_bad(c, cudaStreamSynchronize(c->stream), "train_step: sync"))
+        cuda_bad(c, cudaStreamSynchronize(c->stream), "train_step: sync") || tc_faulted(c, "train_step"))
       return LBCH_ECUDA;
   }
   return LBCH_OK;
@@ -1871,6 +1883,8 @@ lbch_status lbnop_leap_run_judged(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int
     if ((st = enqueue(k + 1)) != LBCH_OK) return st;
   }
   if ((st = lbch_set_steps_taken(lbm, t0 + cycles * (J.leap_steps + lbm_steps))) != LBCH_OK) return lbm_fail(st);
+  // every leap's forward pass completed before the last readings were copied back
+  if (cycles > 0 && tc_faulted(c, "leap_run_judged")) return LBCH_ECUDA;
   if (stats) *stats = S;
   return done(c, "leap_run_judged: launch");
 }
@@ -1951,6 +1965,15 @@ lbch_status lbnop_conv3x3_bwd_weight(const uint16_t* d_x, const uint16_t* d_dy, 
 }
 
 int64_t lbnop_tc_launches(void) { return tc_counter().load(std::memory_order_relaxed); }
+
+int32_t lbnop_tc_fault(void) {
+  int v = 0;
+  if (cudaMemcpyFromSymbol(&v, tc_fault_flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return v ? 1 : 0;
+}
 
 const char* lbnop_last_error(const lbnop_ctx* c) { return c ? c->err : "context is NULL"; }
 

@@ -101,6 +101,8 @@ def load():
         lib.lbnop_conv3x3_packed.restype = ctypes.c_int
         lib.lbnop_tc_launches.argtypes = []
         lib.lbnop_tc_launches.restype = ctypes.c_int64
+        lib.lbnop_tc_fault.argtypes = []
+        lib.lbnop_tc_fault.restype = ctypes.c_int32
         lib.lbnop_last_error.argtypes = [vp]
         lib.lbnop_last_error.restype = ctypes.c_char_p
         lib.lbnop_destroy.argtypes = [vp]
@@ -255,6 +257,12 @@ def lbnop_conv3x3_bwd_weight(d_x: int, d_dy: int, B: int, H: int, W: int, c_in: 
     st = load().lbnop_conv3x3_bwd_weight(ctypes.c_void_p(int(d_x)), ctypes.c_void_p(int(d_dy)), B, H, W, c_in,
                                          c_out, ctypes.c_void_p(int(d_dw)), ctypes.c_void_p(int(cuda_stream or 0)))
     _check(None, st, "lbnop_conv3x3_bwd_weight")
+
+
+def lbnop_tc_fault() -> int:
+    """1 if a tcgen05 convolution of this process gave up a bounded wait (its outputs are
+    invalid), 0 if none did, -1 if unreadable. Read after synchronising."""
+    return int(load().lbnop_tc_fault())
 
 
 def lbnop_tc_launches() -> int:

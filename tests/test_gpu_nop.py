@@ -380,6 +380,7 @@ def test_conv_tc_forward(ci, co, shape):
                                y.data_ptr(), stream())
     torch.cuda.synchronize()
     assert lbnop.lbnop_tc_launches() == before + 1  # the tensor-core path ran
+    assert lbnop.lbnop_tc_fault() == 0  # and no bounded wait gave up
     ref = N.conv(x, w, b)
     scale = N.conv(np.abs(x), np.abs(w)).max() + 1.0
     assert np.abs(y.cpu().numpy() - ref).max() <= 2e-7 * 9 * ci * scale / 64 + 1e-6
