@@ -661,7 +661,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e = run_e2e(lbch, torch, phi0, n, args.steps, 1)
+        e = run_e2e(lbch, torch, phi0, n, args.steps, args.warmup)
         barrier()
         e2e = {"value": job_rate(world, e["lu"], max_over_ranks(dist, e["wall_s"])) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": e["h2d_bytes_per_step"], "d2h_bytes_per_step": e["d2h_bytes_per_step"],
