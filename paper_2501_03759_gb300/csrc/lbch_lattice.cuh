@@ -64,8 +64,11 @@ struct Dev<ST_F16> {
   __device__ __forceinline__ static uint16_t store(float v) {
     return __half_as_ushort(__float2half_rn(v * F16_SCALE));
   }
-  __device__ __forceinline__ static uint32_t pack2(float lo, float hi) {
-    const __half2 h = __floats2half2_rn(lo * F16_SCALE, hi * F16_SCALE);
+  __device__ __forceinline__ static uint32_t pack2(float lo, float hi) { return pack2_scaled(lo * F16_SCALE, hi * F16_SCALE); }
+  // pack2 of values already multiplied by F16_SCALE (exact: a power of two), so that callers
+  // can scale a pair in one packed multiply.
+  __device__ __forceinline__ static uint32_t pack2_scaled(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<const uint32_t*>(&h);
   }
   __device__ __forceinline__ static void raw2(uint32_t u, float& lo, float& hi) {

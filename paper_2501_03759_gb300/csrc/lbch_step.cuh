@@ -424,7 +424,12 @@ __device__ __forceinline__ void store_row_vec(const Field& fd, long long ro, lon
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const F2 dv = fma2(nw, dmu[i - 1][k], o[i][k]);
-        pk[i - 1][k] = D::pack2(dv.x, dv.y);
+        if constexpr (ST == ST_F16) {  // the storage scale for both columns in one packed multiply
+          const F2 sv = splat(F16_SCALE) * dv;
+          pk[i - 1][k] = D::pack2_scaled(sv.x, sv.y);
+        } else {
+          pk[i - 1][k] = D::pack2(dv.x, dv.y);
+        }
         F2 back;
         D::raw2(pk[i - 1][k], back.x, back.y);
         if constexpr (D::UNSCALE != 1.0f) back = splat(D::UNSCALE) * back;
