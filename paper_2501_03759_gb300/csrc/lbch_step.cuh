@@ -45,8 +45,7 @@ constexpr int STEP_WARPS = 4;                // warps per CTA
 // landing slots are smaller); colliding row r-4 first in the iteration with no prefetch
 // instead ran 10% slower once their per-row instruction count had come down, and one row
 // of prefetch with r-4 needs a sixth slot, which costs a CTA per SM; so does two rows of
-// prefetch with r-3 (0.547 -> 0.710 ms per 8192^2 BF16 launch). For FP32 two rows of
-// prefetch keep two CTAs per SM but ran 0.844 -> 0.890 ms per 8192^2 launch.
+// prefetch with r-3 (0.547 -> 0.710 ms per 8192^2 BF16 launch).
 template <int ST, bool VEC>
 struct Pipe {
   static constexpr bool DEV16 = ST != ST_F32;
