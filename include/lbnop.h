@@ -161,12 +161,15 @@ typedef struct {
 
 /* lbnop_leap_run with the plain scheme as judge and fallback. Each of the `cycles` cycles
  * saves the state of `lbm` in this context's workspace, leaps, re-initialises f =
- * f^eq(phi_out), runs lbm_steps steps, and then reads back (one synchronisation per
- * cycle) the mass and free energy before the leap, after it and after the correction.
+ * f^eq(phi_out), runs lbm_steps steps, and reads back the mass and free energy (FP64 sums on
+ * the device) before the leap, after it and after the correction. The readings of cycle k
+ * are copied to the host on a side stream while cycle k + 1 already runs (two saved states
+ * in the workspace); the host judges cycle k from them.
  * If any is NaN/Inf, the mass moved by more than mass_atol H W, or the energy rose by
  * more than energy_rtol |E| across the leap or the correction, the saved state is
- * restored and K + lbm_steps plain steps are run instead, so that a run in which every
- * leap is rejected equals the plain scheme bit for bit. Audited cycles (audit_every)
+ * restored and K + lbm_steps plain steps are run instead (cycle k + 1, started on the
+ * rejected state, is discarded and run again), so that a run in which every leap is
+ * rejected equals the plain scheme bit for bit. Audited cycles (audit_every)
  * run the plain K steps next to the leap instead of re-initialising, and continue from
  * the plain state. After each cycle the step counter of `lbm` (lbch_steps_taken) has
  * advanced by K + lbm_steps: simulated time, whether the cycle leapt or not.
