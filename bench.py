@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-small-configs", action="store_true",
                     help="skip the 64^2 droplet and 256^2 spinodal legs and the oracle comparisons")
     ap.add_argument("--config2-steps", type=int, default=20000, help="steps of the 256^2 spinodal run")
+    ap.add_argument("--log-dir", default=os.environ.get("LBCH_LOG_DIR"),
+                    help="write the 256^2 run's mass and energy every 100 steps as CSV into this folder "
+                         "(default: $LBCH_LOG_DIR; none if unset)")
     ap.add_argument("--storage", choices=["f32", "bf16_dev", "f16_dev"], default="f32",
                     help="population storage of the main timed line")
     return ap.parse_args()
@@ -701,14 +704,15 @@ def main():
             cfg2[name] = {"mlups": r["mlups"], "us_per_step": r["us_per_step"],
                           "energy_law": energy_law(r["log"][:, 1]),
                           "mass_drift_per_node": float(abs(r["log"][-1, 0] - r["log"][0, 0]) / (256 * 256))}
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        csv = os.path.join(ROOT, "gpurun_out", "config2_spinodal256_mass_energy.csv")
-        with open(csv, "w") as fh:
-            fh.write("step," + ",".join(f"mass_{k},energy_{k}" for k in c2) + "\n")
-            for j in range(c2["f32"]["log"].shape[0]):
-                fh.write(f"{j * 100}," + ",".join(f"{c2[k]['log'][j, 0]:.12e},{c2[k]['log'][j, 1]:.12e}"
-                                                    for k in c2) + "\n")
-        cfg2["csv"] = os.path.relpath(csv, ROOT)
+        if args.log_dir:  # mass and energy every 100 steps, both storages
+            os.makedirs(args.log_dir, exist_ok=True)
+            csv = os.path.join(args.log_dir, "config2_spinodal256_mass_energy.csv")
+            with open(csv, "w") as fh:
+                fh.write("step," + ",".join(f"mass_{k},energy_{k}" for k in c2) + "\n")
+                for j in range(c2["f32"]["log"].shape[0]):
+                    fh.write(f"{j * 100}," + ",".join(f"{c2[k]['log'][j, 0]:.12e},{c2[k]['log'][j, 1]:.12e}"
+                                                        for k in c2) + "\n")
+            cfg2["csv"] = csv
         if not args.no_cpu_baseline:
             o = oracle_legs(c1_fields, c2, windows, c2_steps=args.config2_steps)
             errors = o["errors"]
