@@ -980,6 +980,11 @@ void conv_t(const ConvArgs& a, cudaStream_t s) {
 
 template <int CI, int CO>
 void wgrad_t(const WgradArgs& a, cudaStream_t s) {
+  // rows of 128 pixels or more: the tcgen05 path (pixels as the contraction, accumulators in TMEM)
+  if (wgrad_tc_applies(a)) {
+    launch_wgrad_tc<CI, CO>(a, nullptr, device_sms(), s);
+    return;
+  }
   const int npix = a.B * a.H * a.W;
   wgrad_kernel<CI, CO><<<dim3((npix + a.chunk - 1) / a.chunk, 9), 128, 0, s>>>(a);
 }

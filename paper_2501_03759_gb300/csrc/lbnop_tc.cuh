@@ -563,6 +563,181 @@ __global__ void tc_pack_kernel(const bf16* __restrict__ w, int CI, int CO, int K
   }
 }
 
+// ---------------------------------------------------------------- weight gradient
+
+// The weight gradient dw[t][o][i] += sum_p dz(p)[o] x(p + d_t)[i] (t = 3 (dy + 1) + dx + 1, the
+// data-parallel half of the backward pass of a convolution) on the tensor cores: the pixels are
+// the contraction. The staging layout of the convolution above, [chunk][pixel slot][8
+// channels], is then the canonical MN-major layout (8 pixels x 8 channels per 128-byte core
+// matrix, channel chunks TC_CHUNK_A apart along M or N, 8-pixel groups 128 bytes apart along
+// K), so both operands are staged exactly as the convolution stages its input rows and the
+// descriptors keep their strides; the instruction descriptor marks A and B MN-major.
+// A = dz of one row (M = c_out padded to 128 with zero chunks), B = x of the row dy away (N =
+// c_in), shifted by dx through the start address; K = 16 pixels per MMA, 8 per row of 128.
+//
+// Grid: (W / 128) x 3 (dy) x G CTAs of WG_THREADS. CTA (x, dy, g) takes the g-th of G equal
+// runs of the B H rows of column block x, accumulates its three dx taps in TMEM (3 c_in
+// columns, lane = output channel) and adds them into dw with FP32 atomics at the end. Warps
+// 0-3 stage (dz row, x row) pairs into a ring of WG_STAGES and, at the end, read TMEM; warp 4
+// allocates TMEM and lane 0 issues the MMAs.
+constexpr int WG_THREADS = 5 * 32;
+constexpr int WG_LOAD = 128;
+constexpr int WG_MCH = 16;  // chunks of the A operand: M = 128 channels
+
+template <int CI>
+__host__ __device__ constexpr int wg_stage_bytes() { return (WG_MCH + CI / 8) * TC_CHUNK_A; }
+template <int CI>
+__host__ __device__ constexpr int wg_stages() {
+  return 4 * wg_stage_bytes<CI>() + 256 <= 227 * 1024 ? 4 : (3 * wg_stage_bytes<CI>() + 256 <= 227 * 1024 ? 3 : 2);
+}
+template <int CI>
+__host__ __device__ constexpr int wg_smem_bytes() { return wg_stages<CI>() * wg_stage_bytes<CI>() + 256 + 128; }
+template <int CI>
+__host__ __device__ constexpr int wg_tmem_cols() {
+  return 3 * CI <= 32 ? 32 : (3 * CI <= 64 ? 64 : (3 * CI <= 128 ? 128 : (3 * CI <= 256 ? 256 : 512)));
+}
+// kind::f16, FP32 accumulator, BF16 A and B, both MN-major (bits 15, 16), N >> 3, M >> 4.
+template <int M, int N>
+__host__ __device__ constexpr uint32_t umma_idesc_bf16_mn() {
+  return umma_idesc_bf16<M, N>() | (1u << 15) | (1u << 16);
+}
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(WG_THREADS, 1) wgrad_tc_kernel(const __grid_constant__ WgradArgs p, int* err) {
+  static_assert(CO <= 128 && CO % 16 == 0 && CI % 16 == 0 && 3 * CI <= 512, "M = 128 channels, 3 taps in TMEM");
+  constexpr int ST = wg_stages<CI>(), STG = wg_stage_bytes<CI>();
+  constexpr int COLS = wg_tmem_cols<CI>();
+  constexpr uint32_t IDESC = umma_idesc_bf16_mn<128, CI>();
+  // MN-major: the leading offset steps along K (8-pixel groups), the stride offset along M / N
+  // (channel chunks)
+  constexpr uint32_t LBO = 128, SBO = TC_CHUNK_A;
+  constexpr int ZC = CO / 8, XC = CI / 8;  // chunks of dz and of x per pixel
+  extern __shared__ __align__(128) unsigned char wg_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(wg_smem_raw) + 127) & ~(uintptr_t)127);
+  // stage s: dz chunk blocks 0..15 (ZC.. zero), then the x chunk blocks
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + ST * STG);  // full[ST], empty[ST], done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * 4 + 1);
+  volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  auto full = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[ST + s]); };
+  const uint32_t done_bar = smem_u32(&bars[2 * ST]);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * 128, dy = (int)blockIdx.y - 1;
+  const int N = p.B * p.H;
+  const int first = (int)((long long)blockIdx.z * N / gridDim.z);
+  const int last = (int)((long long)(blockIdx.z + 1) * N / gridDim.z);
+  const int nrows = last - first;
+
+  if (tid == 0) {
+    *abort_word = *(volatile int*)&tc_fault_flag;
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(full(s), WG_LOAD);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // the zero chunks of every stage's A operand (M rows CO .. 127), written once
+  for (int s = 0; s < ST; ++s)
+    for (int k = tid; k < (WG_MCH - ZC) * TC_CHUNK_A / 16; k += WG_THREADS)
+      reinterpret_cast<uint4*>(base + s * STG + ZC * TC_CHUNK_A)[k] = make_uint4(0u, 0u, 0u, 0u);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (*abort_word || nrows <= 0) return;  // uniform: nothing allocated or in flight
+  if (warp == 4) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  bool ok = true;
+  if (warp < 4) {
+    // ------------------------------------------------ loaders: row j of the run into stage j % ST
+    const uint32_t base32 = smem_u32(base);
+    for (int j = 0; j < nrows && ok; ++j) {
+      const int s = j % ST;
+      if (j >= ST && !mbar_wait(empty(s), (uint32_t)(((j - ST) / ST) & 1))) {
+        ok = false;
+        break;
+      }
+      const int row = first + j, b = row / p.H, h = row - b * p.H;
+      const size_t zrow = ((size_t)row * p.W + x0) * CO;                                   // dz pixels x0 ..
+      const size_t xrow = (size_t)(b * p.H + wrap1(h + dy, p.H)) * p.W;                    // x row h + dy
+      // dz: pixel x0 + q - 1 in slot q (q = 1 .. 128), chunks 0 .. ZC - 1
+      for (int idx = tid; idx < 128 * ZC; idx += WG_LOAD) {
+        const int q = idx / ZC, c = idx - q * ZC;
+        tc_cp16(base32 + (uint32_t)(s * STG + c * TC_CHUNK_A + (q + 1) * 16), p.dz + zrow + (size_t)q * CO + 8 * c);
+      }
+      // x: pixel x0 - 1 + q (periodic) in slot q (q = 0 .. 129)
+      for (int idx = tid; idx < TC_SLOTS * XC; idx += WG_LOAD) {
+        const int q = idx / XC, c = idx - q * XC;
+        const size_t px = xrow + wrap1(x0 - 1 + q, p.W);
+        tc_cp16(base32 + (uint32_t)(s * STG + (WG_MCH + c) * TC_CHUNK_A + q * 16), p.x + px * CI + 8 * c);
+      }
+      tc_cp_done();
+      mbar_arrive(full(s));
+    }
+  } else if (lane == 0) {
+    // ------------------------------------------------ MMA issuer: 3 dx taps x 8 K-steps per row
+    const uint64_t d0 = umma_desc(smem_u32(base), LBO, SBO);
+    for (int j = 0; j < nrows; ++j) {
+      const int s = j % ST;
+      if (!mbar_wait(full(s), (uint32_t)((j / ST) & 1))) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t as = d0 + (uint64_t)((s * STG + 16) >> 4);                          // dz slot 1
+      const uint64_t bs = d0 + (uint64_t)((s * STG + WG_MCH * TC_CHUNK_A) >> 4);         // x slot 0
+#pragma unroll
+      for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk)
+          umma_bf16(tmem + (uint32_t)(dxi * CI), as + (uint64_t)(kk * 16), bs + (uint64_t)(dxi + kk * 16), IDESC,
+                    (j > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(empty(s));
+    }
+    umma_commit(done_bar);
+  }
+  __syncwarp();
+  // every thread: the accumulators are complete (or the run gave up)
+  const bool fin = mbar_wait(done_bar, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool good = __syncthreads_and((ok && fin) ? 1 : 0) != 0;
+  if (!good && tid == 0) {
+    atomicExch(&tc_fault_flag, 1);
+    if (err) atomicExch(err, 1);
+  }
+  if (good && warp < 4) {
+    // ------------------------------------------------ epilogue: TMEM lane 32 warp + lane = channel o
+    const int o = 32 * warp + lane;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < 3 * CI; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(lane_addr + (uint32_t)c0, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (o < CO) {
+        const int dxi = c0 / CI, i0 = c0 - dxi * CI, t = 3 * (dy + 1) + dxi;
+        float* d = p.dw + ((size_t)t * CO + o) * CI + i0;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) atomicAdd(d + e, __uint_as_float(r[e]));
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 4)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
+}
+
 // ---------------------------------------------------------------- host side
 
 // Whether the tensor-core path takes this convolution: rows of a multiple of 128 pixels, H a
@@ -611,6 +786,40 @@ void launch_tc_x(const ConvArgs& a, int* err, int sms, cudaStream_t s) {
   const long long want = ((long long)sms * occ + cols - 1) / cols;
   const int G = (int)(want < rows ? want : rows);
   conv_tc_kernel<CI, CO, X2><<<dim3(cols, G), TC_THREADS, bytes, s>>>(a, err);
+}
+
+// The tensor-core weight gradient applies to rows of a multiple of 128 pixels (16-byte aligned
+// tensors); every dz row pairs with its own sample's rows, so H is free.
+inline bool wgrad_tc_applies(const WgradArgs& a) {
+  return a.W % 128 == 0 && a.B * a.H >= 1 && ((uintptr_t)a.x % 16) == 0 && ((uintptr_t)a.dz % 16) == 0;
+}
+
+// One launch: (W / 128) x 3 (dy) x G CTAs, G equal runs of rows per column block and dy, as
+// many CTAs as fit on the GPU at once (never more runs than rows).
+template <int CI, int CO>
+void launch_wgrad_tc(const WgradArgs& a, int* err, int sms, cudaStream_t s) {
+  constexpr int bytes = wg_smem_bytes<CI>();
+  static_assert(bytes <= 227 * 1024, "fits in one CTA's shared memory");
+  static std::atomic<int> per_sm[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int occ = per_sm[dev & 63].load(std::memory_order_relaxed);
+  if (occ == 0) {
+    cudaFuncSetAttribute(wgrad_tc_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wgrad_tc_kernel<CI, CO>, WG_THREADS, bytes) !=
+            cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    if (occ > 512 / wg_tmem_cols<CI>()) occ = 512 / wg_tmem_cols<CI>();  // co-resident CTAs share TMEM
+    per_sm[dev & 63].store(occ, std::memory_order_relaxed);
+  }
+  const int cols = a.W / 128, rows = a.B * a.H;
+  const long long want = ((long long)sms * occ) / (3LL * cols);
+  const int G = (int)(want < 1 ? 1 : (want < rows ? want : rows));
+  wgrad_tc_kernel<CI, CO><<<dim3(cols, 3, G), WG_THREADS, bytes, s>>>(a, err);
+  tc_counter().fetch_add(1, std::memory_order_relaxed);
 }
 
 // Launches conv_tc_kernel for this convolution (tc_applies holds).

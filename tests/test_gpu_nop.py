@@ -423,11 +423,36 @@ def test_conv_packed_weights(ci, co):
     assert (raw[:, :, :co, :] == wbits.transpose(0, 2, 1, 3)).all()
 
 
+# The weight gradient takes the tcgen05 path on rows of 128 pixels (or a multiple); H is free
+# (every dz row meets its own sample's rows). Shapes: one row, a few rows across samples, an
+# odd H, rows of 256 pixels, and many rows per CTA.
+WG_TC_SHAPES = [(1, 1, 128), (3, 5, 128), (2, 8, 256), (10, 128, 128)]
+
+
+@pytest.mark.parametrize("ci,co", CHANNELS)
+@pytest.mark.parametrize("shape", WG_TC_SHAPES)
+def test_conv_bwd_weight_tc(ci, co, shape):
+    B, H, Wd = shape
+    x = W.bf16_exact((B, H, Wd, ci), 26, 1.0)
+    dy = W.bf16_exact((B, H, Wd, co), 27, 1.0)
+    dw = torch.empty((9, co, ci), dtype=torch.float32, device="cuda")
+    xd, dyd = dev_bf16(x), dev_bf16(dy)
+    before = lbnop.lbnop_tc_launches()
+    lbnop.lbnop_conv3x3_bwd_weight(xd.data_ptr(), dyd.data_ptr(), B, H, Wd, ci, co, dw.data_ptr(), stream())
+    torch.cuda.synchronize()
+    assert lbnop.lbnop_tc_launches() == before + 1  # the tensor-core path ran
+    assert lbnop.lbnop_tc_fault() == 0
+    ref = N.conv_bwd_weight(x, dy)
+    scale = N.conv_bwd_weight(np.abs(x), np.abs(dy)).max() + 1.0
+    assert np.abs(dw.cpu().numpy() - ref).max() <= 1e-6 * scale
+
+
 def test_network_on_tensor_core_path_matches_oracle():
     """A 512^2 field: its finest level (128 x 128) runs e0a (the input and its BF16 remainder
     as K = 32), e0b, d0a and the output layer, and in the backward pass the data gradients of
-    the last three, on the tcgen05 path; forward and gradients against the oracle with the
-    same BF16 storage points, with the bounds of the mma.sync path."""
+    the last three and the weight gradients of all six level-0 layers, on the tcgen05 path;
+    forward and gradients against the oracle with the same BF16 storage points, with the bounds
+    of the mma.sync path."""
     B, H, Wd = 1, 512, 512
     theta, phi, target, alpha = network_case(B, H, Wd, seed=3)
     scale = 0.05
@@ -439,7 +464,9 @@ def test_network_on_tensor_core_path_matches_oracle():
     mid = lbnop.lbnop_tc_launches()
     assert mid - before == 4  # e0a, e0b, d0a, out
     loss = s.backward(pd, alpha, td)
-    assert lbnop.lbnop_tc_launches() - mid == 4 + 3  # forward again, then the data gradients of out, d0a, e0b
+    # forward again, the data gradients of out, d0a, e0b, and the weight gradients of the level-0
+    # layers (e0a, lin, lina twice: phi's two BF16 halves share their weights)
+    assert lbnop.lbnop_tc_launches() - mid == 4 + 3 + 9
     g = s.grads_host().astype(np.float64)
     ref_q, saved = N.forward(theta, phi, alpha, scale, quantize=N.bf16)
     e_q = rel_l2(out - phi, ref_q - phi)
