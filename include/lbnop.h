@@ -206,12 +206,13 @@ lbch_status lbnop_conv3x3_bwd_data(const uint16_t* d_dy, const uint16_t* d_w, in
 lbch_status lbnop_conv3x3_bwd_weight(const uint16_t* d_x, const uint16_t* d_dy, int32_t B, int32_t H, int32_t W,
                                      int32_t c_in, int32_t c_out, float* d_dw, void* cuda_stream);
 
-/* Number of convolutions this process has run on the tcgen05 tensor-core path (input rows
- * staged by cp.async, weight taps by bulk asynchronous copies, FP32 accumulators in tensor
- * memory) since the library was loaded. That path takes every forward convolution whose rows
- * are a multiple of 128 pixels long (H a multiple of 4) with packed weights: one input
- * tensor, or on the network's first layer the input and its BF16 remainder (K = 32); the
- * others run on mma.sync kernels. A diagnostic for tests and benchmarks. */
+/* Number of launches this process has run on the tcgen05 tensor-core path (operands staged
+ * in shared memory, FP32 accumulators in tensor memory) since the library was loaded. That
+ * path takes every forward convolution whose rows are a multiple of 128 pixels long (H a
+ * multiple of 4) with packed weights: one input tensor, or on the network's first layer the
+ * input and its BF16 remainder (K = 32); and every weight gradient (conv3x3_bwd_weight, and
+ * the network's backward pass) whose rows are a multiple of 128 pixels. The others run on
+ * mma.sync kernels. A diagnostic for tests and benchmarks. */
 int64_t lbnop_tc_launches(void);
 
 /* 1 if a tcgen05 convolution of this process (on the current device) gave up one of its
