@@ -578,10 +578,12 @@ __global__ void tc_pack_kernel(const bf16* __restrict__ w, int CI, int CO, int K
 // Grid: (W / 128) x 3 (dy) x G CTAs of WG_THREADS. CTA (x, dy, g) takes the g-th of G equal
 // runs of the B H rows of column block x, accumulates its three dx taps in TMEM (3 c_in
 // columns, lane = output channel) and adds them into dw with FP32 atomics at the end. Warps
-// 0-3 stage (dz row, x row) pairs into a ring of WG_STAGES and, at the end, read TMEM; warp 4
-// allocates TMEM and lane 0 issues the MMAs.
-constexpr int WG_THREADS = 5 * 32;
-constexpr int WG_LOAD = 128;
+// 0-7 stage (dz row, x row) pairs into a ring of stages (16-byte copies: eight warps keep
+// enough of them in flight), and warps 0-3 read TMEM at the end; warp 8 allocates TMEM and
+// its lane 0 issues the MMAs.
+constexpr int WG_LOAD = 256;
+constexpr int WG_MMA_WARP = WG_LOAD / 32;
+constexpr int WG_THREADS = WG_LOAD + 32;
 constexpr int WG_MCH = 16;  // chunks of the A operand: M = 128 channels
 
 template <int CI>
@@ -645,7 +647,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_tc_kernel(const __grid_co
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if (*abort_word || nrows <= 0) return;  // uniform: nothing allocated or in flight
-  if (warp == 4) {
+  if (warp == WG_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(COLS)
                  : "memory");
@@ -657,7 +659,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_tc_kernel(const __grid_co
   const uint32_t tmem = *tmem_slot;
 
   bool ok = true;
-  if (warp < 4) {
+  if (warp < WG_MMA_WARP) {
     // ------------------------------------------------ loaders: row j of the run into stage j % ST
     const uint32_t base32 = smem_u32(base);
     for (int j = 0; j < nrows && ok; ++j) {
@@ -734,7 +736,7 @@ __global__ void __launch_bounds__(WG_THREADS, 1) wgrad_tc_kernel(const __grid_co
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 4)
+  if (warp == WG_MMA_WARP)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS) : "memory");
 }
 
