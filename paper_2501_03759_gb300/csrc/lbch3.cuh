@@ -153,12 +153,20 @@ __device__ __forceinline__ void stencil(const float* __restrict__ v, const Site&
   grad_lap(v[s.id], t, gx, gy, gz, lap);
 }
 
+// Population load with a 256-byte L2 fetch (.L2::256B): a block's 128 threads read 512
+// contiguous bytes of each plane row (0.7636 -> 0.7602 ms per 256^3 step on GB300).
+__device__ __forceinline__ float ld_pop(const float* p) {
+  float v;
+  asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
 __global__ void __launch_bounds__(NX3) phi3_kernel(const float* __restrict__ f, Grid3 g, float* __restrict__ phi) {
   Site s;
   if (!site_of(g, blockIdx.x, s)) return;
   float p = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 15; ++i) p += f[(long long)i * g.ps + s.at(-cx(i), -cy(i), -cz(i))];
+  for (int i = 0; i < 15; ++i) p += ld_pop(f + (long long)i * g.ps + s.at(-cx(i), -cy(i), -cz(i)));
   phi[s.id] = p;
 }
 
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(NX3) collide3_kernel(const float* __restrict__
   if (!site_of(g, blockIdx.x, s)) return;
   float f[15];
 #pragma unroll
-  for (int i = 0; i < 15; ++i) f[i] = src[(long long)i * g.ps + s.at(-cx(i), -cy(i), -cz(i))];
+  for (int i = 0; i < 15; ++i) f[i] = ld_pop(src + (long long)i * g.ps + s.at(-cx(i), -cy(i), -cz(i)));
   float gx, gy, gz, unused;
   stencil(mub, s, gx, gy, gz, unused);
   float phi = 0.0f;
