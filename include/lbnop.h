@@ -185,7 +185,10 @@ lbch_status lbnop_leap_run_judged(lbnop_ctx* c, lbch_ctx* lbm, double alpha, int
  *   conv3x3:             y = conv(x, w) + bias (bias may be NULL), FP32 out.
  *   conv3x3_bwd_data:    dx = sum_d w_d^T dy(p - d), FP32 out ([B][H][W][c_in]).
  *   conv3x3_bwd_weight:  dw[d] = sum_p dy(p) x(p + d)^T, FP32 out ([9][c_out][c_in]),
- *                        dy being BF16 [B][H][W][c_out]. */
+ *                        dy being BF16 [B][H][W][c_out].
+ * Errors: LBCH_EINVAL for NULL pointers or unsupported shapes; LBCH_ECUDA if a launch fails.
+ * A CUDA error left pending by earlier work of the calling thread is reported as LBCH_ECUDA
+ * before anything is launched, and stays pending for the caller to read. */
 lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float* d_bias, int32_t B, int32_t H,
                           int32_t W, int32_t c_in, int32_t c_out, float* d_y, void* cuda_stream);
 /* The same convolution with weights packed once for the tensor-core path: lbnop_conv3x3_pack

@@ -1909,6 +1909,7 @@ lbch_status lbnop_conv3x3_pack(const uint16_t* d_w, int32_t c_in, int32_t c_out,
   if (!d_w || !d_packed || !channels_ok(c_in) || !channels_ok(c_out) || ((uintptr_t)d_w % 16) != 0 ||
       ((uintptr_t)d_packed % 16) != 0)
     return LBCH_EINVAL;
+  if (cudaPeekAtLastError() != cudaSuccess) return LBCH_ECUDA;  // an earlier error stays the caller's
   const int kc = tc_kc(c_in, false);
   tc_pack_kernel<<<grid_for(9LL * kc * (c_out + 1), 256), 256, 0, (cudaStream_t)cuda_stream>>>(
       (const bf16*)d_w, c_in, c_out, kc, (unsigned char*)d_packed);
@@ -1919,6 +1920,7 @@ lbch_status lbnop_conv3x3_packed(const uint16_t* d_x, const uint16_t* d_w, const
                                  int32_t B, int32_t H, int32_t W, int32_t c_in, int32_t c_out, float* d_y,
                                  void* cuda_stream) {
   if (!d_x || !d_w || !d_y || op_check(B, H, W, c_in, c_out) != LBCH_OK) return LBCH_EINVAL;
+  if (cudaPeekAtLastError() != cudaSuccess) return LBCH_ECUDA;
   ConvArgs a{};
   a.x = (const bf16*)d_x;
   a.w = (const bf16*)d_w;
@@ -1941,6 +1943,7 @@ lbch_status lbnop_conv3x3(const uint16_t* d_x, const uint16_t* d_w, const float*
 lbch_status lbnop_conv3x3_bwd_data(const uint16_t* d_dy, const uint16_t* d_w, int32_t B, int32_t H, int32_t W,
                                    int32_t c_in, int32_t c_out, float* d_dx, void* cuda_stream) {
   if (!d_dy || !d_w || !d_dx || op_check(B, H, W, c_in, c_out) != LBCH_OK) return LBCH_EINVAL;
+  if (cudaPeekAtLastError() != cudaSuccess) return LBCH_ECUDA;
   ConvArgs a{};
   a.x = (const bf16*)d_dy;
   a.w = (const bf16*)d_w;
@@ -1955,6 +1958,7 @@ lbch_status lbnop_conv3x3_bwd_data(const uint16_t* d_dy, const uint16_t* d_w, in
 lbch_status lbnop_conv3x3_bwd_weight(const uint16_t* d_x, const uint16_t* d_dy, int32_t B, int32_t H, int32_t W,
                                      int32_t c_in, int32_t c_out, float* d_dw, void* cuda_stream) {
   if (!d_x || !d_dy || !d_dw || op_check(B, H, W, c_in, c_out) != LBCH_OK) return LBCH_EINVAL;
+  if (cudaPeekAtLastError() != cudaSuccess) return LBCH_ECUDA;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   if (cudaMemsetAsync(d_dw, 0, (size_t)9 * c_in * c_out * sizeof(float), s) != cudaSuccess) return LBCH_ECUDA;
   WgradArgs a{};
