@@ -3,10 +3,10 @@
 A pin that passes whatever the oracle computes pins nothing. Each case below copies
 oracle/lbch_oracle.cpp with one plausible mistake in one branch (a wrong factor, a
 flipped sign, a dropped term, a wrong reading), builds that copy with g++, and runs
-the named pins of tests/test_oracle_pins.py against it in a separate process
-(LBCH_ORACLE_LIB points the oracle package at the copy). The case passes only if
-those pins FAIL on the planted mistake; the unmodified oracle passes them in
-test_oracle_pins.py itself.
+the named pins against it in a separate process (LBCH_ORACLE_LIB points the oracle
+package at the copy): tests/test_oracle_pins.py for the 2D scheme, and
+tests/test_oracle3_pins.py for the D3Q15 scheme. The case passes only if those pins FAIL
+on the planted mistake; the unmodified oracle passes them in the pin files themselves.
 
 Everything here runs on the CPU; no mistake is ever planted in the CUDA library.
 """
@@ -20,6 +20,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lbch_oracle.cpp")
 PINS = "tests/test_oracle_pins.py"
+PINS3 = "tests/test_oracle3_pins.py"
 
 # (name, original text, planted text, pins expected to fail). Each original text must occur
 # exactly once in the 2D part of the oracle source.
@@ -74,20 +75,51 @@ MUTANTS = [
 ]
 
 
-def _planted_source(old, new):
+# The same for the D3Q15 scheme (Eqs. 3, 6, 17-19, 21, 24, 26 with d = 3): each original text
+# occurs exactly once in the 3D part. Most are caught by the separately written NumPy step
+# (test_numpy_second_route_3d, alpha = 0.35), the rest by the dispersion and mass pins.
+MUTANTS3 = [
+    ("grad_n_gamma_12_alpha_3d", "gn[d] = 16.0 * alpha * n[d] * n[d] * n[d];",
+     "gn[d] = 12.0 * alpha * n[d] * n[d] * n[d];", ["test_numpy_second_route_3d"]),
+    ("projector_sign_3d", "v += ((d == e ? 1.0 : 0.0) - n[d] * n[e]) * gn[e];  // P = I - n n^T",
+     "v += ((d == e ? 1.0 : 0.0) + n[d] * n[e]) * gn[e];", ["test_numpy_second_route_3d"]),
+    ("gamma_alpha_sign_3d", "a.gamma = 1.0 + alpha * (4.0 * s4 - 3.0);  // Eq. 6, d = 3",
+     "a.gamma = 1.0 - alpha * (4.0 * s4 - 3.0);", ["test_linear_dispersion_3d_axis"]),
+    ("jz_rate_default_3d", "sc->s[3] = sc->s[5] = sc->s[7] = sj;",
+     "sc->s[3] = sc->s[5] = sj;", ["test_numpy_second_route_3d"]),
+    ("laplacian_half_3d",
+     "for (int i = 0; i < 15; ++i) s += 2.0 * W3[i] * (chi[idx3(sc, x + CX3[i], y + CY3[i], z + CZ3[i])] - c);",
+     "for (int i = 0; i < 15; ++i) s += W3[i] * (chi[idx3(sc, x + CX3[i], y + CY3[i], z + CZ3[i])] - c);",
+     ["test_numpy_second_route_3d", "test_linear_dispersion_3d_axis"]),
+    ("tangential_drops_k_3d", "const double kq = literal_q ? 1.0 : sc.k;",
+     "const double kq = 1.0;", ["test_numpy_second_route_3d"]),
+    ("willmore_drops_fprime_w_3d",
+     "reg = sc.eps * (lap3(sc, F.w.data(), x, y, z) - fp * F.w[id]);  // Eq. 13",
+     "reg = sc.eps * lap3(sc, F.w.data(), x, y, z);", ["test_numpy_second_route_3d"]),
+    ("source_sign_3d", "F[i] = -W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);  // Eq. 19",
+     "F[i] = W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);", ["test_numpy_second_route_3d"]),
+    ("rest_equilibrium_3d", "feq[0] = phi + (W3[0] - 1.0) * mua;",
+     "feq[0] = phi - W3[0] * mua;", ["test_mass_and_energy_droplet_3d"]),
+]
+
+
+def _planted_source(old, new, part="2d"):
     src = open(SRC).read()
-    cut = src.index("// 3D: D3Q15")  # plant in the 2D scheme only
+    cut = src.index("// 3D: D3Q15")  # the 2D scheme before, the 3D scheme after
     head, tail = src[:cut], src[cut:]
-    assert head.count(old) == 1, old
-    return head.replace(old, new) + tail
+    if part == "2d":
+        assert head.count(old) == 1, old
+        return head.replace(old, new) + tail
+    assert tail.count(old) == 1, old
+    return head + tail.replace(old, new)
 
 
-def _build_and_run(tmp, name, old, new, pins):
+def _build_and_run(tmp, name, old, new, pins, part="2d", pin_file=PINS):
     d = os.path.join(tmp, name)
     os.makedirs(d, exist_ok=True)
     cpp = os.path.join(d, "lbch_oracle.cpp")
     with open(cpp, "w") as fh:
-        fh.write(_planted_source(old, new))
+        fh.write(_planted_source(old, new, part))
     lib = os.path.join(d, "liboracle.so")
     subprocess.run(["g++", "-O2", "-std=c++17", "-fno-fast-math", "-ffp-contract=off", "-fopenmp",
                     "-fPIC", "-shared", "-I", os.path.join(ROOT, "oracle"), cpp, "-o", lib], check=True)
@@ -95,7 +127,7 @@ def _build_and_run(tmp, name, old, new, pins):
     rc = {}
     for pin in pins:
         r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider",
-                            f"{PINS}::{pin}"], cwd=ROOT, env=env, capture_output=True, text=True)
+                            f"{pin_file}::{pin}"], cwd=ROOT, env=env, capture_output=True, text=True)
         rc[pin] = (r.returncode, r.stdout[-2000:])
     return rc
 
@@ -103,12 +135,13 @@ def _build_and_run(tmp, name, old, new, pins):
 @pytest.fixture(scope="module")
 def outcomes(tmp_path_factory):
     tmp = str(tmp_path_factory.mktemp("oracle_mutants"))
-    with ThreadPoolExecutor(max(1, min(len(MUTANTS), (os.cpu_count() or 2) // 2))) as ex:
+    with ThreadPoolExecutor(max(1, min(len(MUTANTS) + len(MUTANTS3), (os.cpu_count() or 2) // 2))) as ex:
         futs = {m[0]: ex.submit(_build_and_run, tmp, *m) for m in MUTANTS}
+        futs.update({m[0]: ex.submit(_build_and_run, tmp, *m, "3d", PINS3) for m in MUTANTS3})
         return {k: f.result() for k, f in futs.items()}
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS + MUTANTS3])
 def test_planted_mistake_is_caught(outcomes, name):
     for pin, (code, out) in outcomes[name].items():
         # pytest exit code 1: tests ran and at least one failed (not a build or collection error).
