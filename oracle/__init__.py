@@ -154,6 +154,7 @@ def _load():
             lib.orc3_collide_site.argtypes = [p3, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, dp]
             lib.orc3_init.argtypes = [p3, dp, dp]
+            lib.orc3_fields.argtypes = [p3, dp, dp]
             lib.orc3_step.argtypes = [p3, dp, ctypes.c_int64]
             lib.orc3_phi.argtypes = [p3, dp, dp]
             lib.orc3_mass.argtypes = [p3, dp]
@@ -320,6 +321,14 @@ def step3(p: Params3, f: np.ndarray, nsteps: int) -> np.ndarray:
     assert g.shape == (15, p.nz, p.ny, p.nx)
     _check(_load().orc3_step(ctypes.byref(p.c()), _ptr(g), int(nsteps)), "step3")
     return g
+
+
+def fields3(p: Params3, f: np.ndarray) -> dict:
+    """phi, gamma, mu_alpha and mu_beta of a 3D state, each (nz, ny, nx)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros((4, p.nz, p.ny, p.nx))
+    _check(_load().orc3_fields(ctypes.byref(p.c()), _ptr(f), _ptr(out)), "fields3")
+    return {n: out[i] for i, n in enumerate(("phi", "gamma", "mu_alpha", "mu_beta"))}
 
 
 def phi3(p: Params3, f: np.ndarray) -> np.ndarray:

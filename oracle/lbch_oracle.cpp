@@ -834,6 +834,18 @@ int orc3_step(const orc3_params* p, double* f, int64_t nsteps) {
   return 0;
 }
 
+int orc3_fields(const orc3_params* p, const double* f, double* out4) {
+  Scheme3 sc;
+  if (make_scheme3(p, &sc) != 0) return -1;
+  const size_t N = size_t(sc.nx) * sc.ny * sc.nz;
+  Fields3 F(N);
+  compute_fields3(sc, f, F);
+  const std::vector<double>* src[4] = {&F.phi, &F.gamma, &F.mua, &F.mub};
+  for (int q = 0; q < 4; ++q)
+    for (size_t id = 0; id < N; ++id) out4[q * N + id] = (*src[q])[id];
+  return 0;
+}
+
 int orc3_phi(const orc3_params* p, const double* f, double* phi) {
   Scheme3 sc;
   if (make_scheme3(p, &sc) != 0) return -1;

@@ -113,7 +113,8 @@ int orc_set_threads(int n);
  * Pins: Eq. 21 and Eq. 24 printed values (with the two discrepancies named exactly),
  * Eq. 27 moment constraints, orthogonality, single-relaxation reduction, mass
  * conservation, energy decay, continuum linear dispersion along axis, face and body
- * diagonals, cube rotation equivariance, and a separate NumPy route. */
+ * diagonals, cube rotation equivariance, a separate NumPy route, and (orc3_fields) mu_beta
+ * on a spherical interface against the continuum value of Eqs. 3, 6, 15, 16. */
 typedef struct {
   int32_t nx, ny, nz;
   double M, sigma, D, eps, alpha;
@@ -128,6 +129,9 @@ void orc3_source(double gx, double gy, double gz, double F[15]);
 void orc3_collide_site(const orc3_params* p, const double f[15], double phi, double mu_alpha,
                        double gx, double gy, double gz, double out[15]);
 int orc3_init(const orc3_params* p, const double* phi0, double* f);
+/* phi, gamma, mu_alpha and mu_beta of the state f (4 planes of nx*ny*nz, in that order):
+ * the pointwise fields one step computes before the collision (Eqs. 3, 6, 13, 15, 16, 22). */
+int orc3_fields(const orc3_params* p, const double* f, double* out4);
 int orc3_step(const orc3_params* p, double* f, int64_t nsteps);
 int orc3_phi(const orc3_params* p, const double* f, double* phi);
 double orc3_mass(const orc3_params* p, const double* f);

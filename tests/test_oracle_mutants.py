@@ -77,12 +77,16 @@ MUTANTS = [
 
 # The same for the D3Q15 scheme (Eqs. 3, 6, 17-19, 21, 24, 26 with d = 3): each original text
 # occurs exactly once in the 3D part. Most are caught by the separately written NumPy step
-# (test_numpy_second_route_3d, alpha = 0.35), the rest by the dispersion and mass pins.
+# (test_numpy_second_route_3d, alpha = 0.35); the tangential-term readings also by the
+# spherical interface, which does not share the NumPy step's readings; the rest by the
+# dispersion and mass pins.
 MUTANTS3 = [
     ("grad_n_gamma_12_alpha_3d", "gn[d] = 16.0 * alpha * n[d] * n[d] * n[d];",
-     "gn[d] = 12.0 * alpha * n[d] * n[d] * n[d];", ["test_numpy_second_route_3d"]),
+     "gn[d] = 12.0 * alpha * n[d] * n[d] * n[d];",
+     ["test_numpy_second_route_3d", "test_tangential_term_spherical_interface"]),
     ("projector_sign_3d", "v += ((d == e ? 1.0 : 0.0) - n[d] * n[e]) * gn[e];  // P = I - n n^T",
-     "v += ((d == e ? 1.0 : 0.0) + n[d] * n[e]) * gn[e];", ["test_numpy_second_route_3d"]),
+     "v += ((d == e ? 1.0 : 0.0) + n[d] * n[e]) * gn[e];",
+     ["test_numpy_second_route_3d", "test_tangential_term_spherical_interface"]),
     ("gamma_alpha_sign_3d", "a.gamma = 1.0 + alpha * (4.0 * s4 - 3.0);  // Eq. 6, d = 3",
      "a.gamma = 1.0 - alpha * (4.0 * s4 - 3.0);", ["test_linear_dispersion_3d_axis"]),
     ("jz_rate_default_3d", "sc->s[3] = sc->s[5] = sc->s[7] = sj;",
@@ -92,7 +96,9 @@ MUTANTS3 = [
      "for (int i = 0; i < 15; ++i) s += W3[i] * (chi[idx3(sc, x + CX3[i], y + CY3[i], z + CZ3[i])] - c);",
      ["test_numpy_second_route_3d", "test_linear_dispersion_3d_axis"]),
     ("tangential_drops_k_3d", "const double kq = literal_q ? 1.0 : sc.k;",
-     "const double kq = 1.0;", ["test_numpy_second_route_3d"]),
+     "const double kq = 1.0;", ["test_numpy_second_route_3d", "test_tangential_term_spherical_interface"]),
+    ("literal_keeps_k_3d", "const double kq = literal_q ? 1.0 : sc.k;",
+     "const double kq = sc.k;", ["test_tangential_term_spherical_interface"]),
     ("willmore_drops_fprime_w_3d",
      "reg = sc.eps * (lap3(sc, F.w.data(), x, y, z) - fp * F.w[id]);  // Eq. 13",
      "reg = sc.eps * lap3(sc, F.w.data(), x, y, z);", ["test_numpy_second_route_3d"]),
