@@ -102,6 +102,12 @@ MUTANTS3 = [
     ("willmore_drops_fprime_w_3d",
      "reg = sc.eps * (lap3(sc, F.w.data(), x, y, z) - fp * F.w[id]);  // Eq. 13",
      "reg = sc.eps * lap3(sc, F.w.data(), x, y, z);", ["test_numpy_second_route_3d"]),
+    ("linear_regularisation_doubled_3d", "else if (sc.reg == 2) reg = sc.eps * F.lap2[id];",
+     "else if (sc.reg == 2) reg = 2.0 * sc.eps * F.lap2[id];", ["test_linear_dispersion_3d_linear_regularisation"]),
+    ("nested_as_split_3d", "const double iso = nested ? a.gamma : (a.gamma - 1.0);",
+     "const double iso = a.gamma - 1.0;", ["test_nested_minus_split_is_lattice_commutator_3d"]),
+    ("nested_minus_f_only_3d", "F.mub[id] = nested ? F.gamma[id] * fb - divQ + reg - F.mua[id]",
+     "F.mub[id] = nested ? F.gamma[id] * fb - divQ + reg - fb", ["test_nested_minus_split_is_lattice_commutator_3d"]),
     ("source_sign_3d", "F[i] = -W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);  // Eq. 19",
      "F[i] = W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);", ["test_numpy_second_route_3d"]),
     ("rest_equilibrium_3d", "feq[0] = phi + (W3[0] - 1.0) * mua;",
