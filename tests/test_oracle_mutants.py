@@ -108,6 +108,7 @@ MUTANTS3 = [
      "const double iso = a.gamma - 1.0;", ["test_nested_minus_split_is_lattice_commutator_3d"]),
     ("nested_minus_f_only_3d", "F.mub[id] = nested ? F.gamma[id] * fb - divQ + reg - F.mua[id]",
      "F.mub[id] = nested ? F.gamma[id] * fb - divQ + reg - fb", ["test_nested_minus_split_is_lattice_commutator_3d"]),
+    ("guard_too_high_3d", "  if (g2 < GUARD) {", "  if (g2 < 1e-6) {", ["test_guard_fires_only_in_the_bulk_3d"]),
     ("source_sign_3d", "F[i] = -W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);  // Eq. 19",
      "F[i] = W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);", ["test_numpy_second_route_3d"]),
     ("rest_equilibrium_3d", "feq[0] = phi + (W3[0] - 1.0) * mua;",
