@@ -72,6 +72,20 @@ MUTANTS = [
     # The n = 0 guard (reading C3) at a threshold that reaches interface nodes.
     ("guard_too_high", "const double GUARD = 1e-12;", "const double GUARD = 1e-6;",
      ["test_guard_fires_only_in_the_bulk"]),
+    # Parameters and collision (Eqs. 5, 17-19, the rate after Eq. 38).
+    ("k_without_half", "d->k = d->beta * p->D * p->D / 2.0;", "d->k = d->beta * p->D * p->D;",
+     ["test_parameters_eq5_inversion"]),
+    ("s35_without_cs2", "const double s35 = 1.0 / (p->M / CS2 + 0.5);", "const double s35 = 1.0 / (p->M + 0.5);",
+     ["test_parameters_eq5_inversion"]),
+    ("force_factor_one_minus_s", "b += sc->Minv[i][m] * (1.0 - sc->s[m] / 2.0) * MROWS[m][j];",
+     "b += sc->Minv[i][m] * (1.0 - sc->s[m]) * MROWS[m][j];", ["test_srt_reduction"]),
+    ("relaxation_squared", "a += sc->Minv[i][m] * sc->s[m] * MROWS[m][j];",
+     "a += sc->Minv[i][m] * sc->s[m] * sc->s[m] * MROWS[m][j];", ["test_srt_reduction"]),
+    ("rest_equilibrium", "feq[0] = phi + (WGT[0] - 1.0) * mua;", "feq[0] = phi - WGT[0] * mua;",
+     ["test_equilibrium_and_source_moments_eq27bc"]),
+    ("source_sign", "for (int i = 0; i < 9; ++i) F[i] = -WGT[i] * (CX[i] * gx + CY[i] * gy);",
+     "for (int i = 0; i < 9; ++i) F[i] = WGT[i] * (CX[i] * gx + CY[i] * gy);",
+     ["test_equilibrium_and_source_moments_eq27bc"]),
 ]
 
 
