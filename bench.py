@@ -24,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -544,6 +545,18 @@ def conv_with_roofline(c):
     return c
 
 
+def host_cpu() -> str:
+    """The host CPU's model name (lscpu), for the oracle timings; 'unknown' if unavailable."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:  # noqa: BLE001 - a label only, never fatal
+        pass
+    return platform.machine() or "unknown"
+
+
 def cpu_oracle_rate(target_s: float = 8.0, n_sample: int = 2048):
     """The FP64 oracle, as it stands, on the host cores: MLUPS on an n_sample^2 spinodal
     sample of the workload (alpha 0.3, noise 0.05, seed 0)."""
@@ -587,7 +600,7 @@ def reference_arm(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": f"{n_sample}x{n_sample}", "alpha": ALPHA, "noise": NOISE,
                    "seed": SEED, "lattice_steps_per_step": 1, "parallelism": "host cores (OpenMP)"},
-        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle", "host": host_cpu(),
                          "sample": f"each step: 1 FP64 oracle step on a {n_sample}x{n_sample} spinodal field"},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -718,6 +731,7 @@ def main():
             errors = o["errors"]
             cpu_rates = o["rates"]
             cpu_rates["cores"] = o["cores"]
+            cpu_rates["host"] = host_cpu()
             cfg2["energy_end_vs_oracle_rel"] = {
                 k: abs(float(c2[k]["log"][-1, 1]) - o["energy_oracle_spinodal256_end"]) /
                 abs(o["energy_oracle_spinodal256_end"]) for k in c2}
