@@ -198,6 +198,22 @@ def test_linear_dispersion_3d_linear_regularisation(phi0):
     assert abs(willmore - want) > 5e-2 * abs(want) and abs(no_reg - want) > 5e-2 * abs(want)
 
 
+def test_init_is_equilibrium_of_eq16_mu_alpha_3d():
+    """Reading C5 in 3D: f = f^eq (Eq. 18) of phi0 and mu_alpha = f(phi0) - k lap phi0 (Eq. 16,
+    the Eq. 26b Laplacian), recomputed with np.roll from the printed Eq. 21 tables."""
+    nx, ny, nz = 6, 5, 7
+    phi0 = np.random.default_rng(13).uniform(-0.9, 0.9, (nz, ny, nx))
+    f = oracle.init3(P3(nx, ny, nz, alpha=0.3), phi0)
+    beta = 3 * 0.01 / (4 * 5.0)
+    k = beta * 5.0 ** 2 / 2
+    at = lambda a, c: np.roll(a, shift=(-c[2], -c[1], -c[0]), axis=(0, 1, 2))
+    lap = 6 * sum(W3[i] * (at(phi0, C3[i]) - phi0) for i in range(15))
+    mua = 4 * beta * phi0 * (phi0 * phi0 - 1) - k * lap
+    want = W3[:, None, None, None] * mua[None]
+    want[0] = phi0 - (1 - W3[0]) * mua
+    assert np.abs(f - want).max() <= 1e-15
+
+
 # ---------------------------------------------------------------- curved interface
 
 def _sphere_mu_beta_error(scale, literal, alpha=0.3):

@@ -83,6 +83,9 @@ MUTANTS = [
      "a += sc->Minv[i][m] * sc->s[m] * sc->s[m] * MROWS[m][j];", ["test_srt_reduction"]),
     ("rest_equilibrium", "feq[0] = phi + (WGT[0] - 1.0) * mua;", "feq[0] = phi - WGT[0] * mua;",
      ["test_equilibrium_and_source_moments_eq27bc"]),
+    ("init_mu_alpha_sign", "const double mua = bulk_f(sc, phi0[id]) - sc.k * lap26(sc, phi0, x, y);  // Eq. 16",
+     "const double mua = bulk_f(sc, phi0[id]) + sc.k * lap26(sc, phi0, x, y);",
+     ["test_init_is_equilibrium_of_eq16_mu_alpha"]),
     ("source_sign", "for (int i = 0; i < 9; ++i) F[i] = -WGT[i] * (CX[i] * gx + CY[i] * gy);",
      "for (int i = 0; i < 9; ++i) F[i] = WGT[i] * (CX[i] * gx + CY[i] * gy);",
      ["test_equilibrium_and_source_moments_eq27bc"]),
@@ -123,6 +126,10 @@ MUTANTS3 = [
     ("nested_minus_f_only_3d", "F.mub[id] = nested ? F.gamma[id] * fb - divQ + reg - F.mua[id]",
      "F.mub[id] = nested ? F.gamma[id] * fb - divQ + reg - fb", ["test_nested_minus_split_is_lattice_commutator_3d"]),
     ("guard_too_high_3d", "  if (g2 < GUARD) {", "  if (g2 < 1e-6) {", ["test_guard_fires_only_in_the_bulk_3d"]),
+    ("init_mu_alpha_sign_3d",
+     "const double mua = 4.0 * sc.beta * ph * (ph + 1.0) * (ph - 1.0) - sc.k * lap3(sc, phi0, x, y, z);",
+     "const double mua = 4.0 * sc.beta * ph * (ph + 1.0) * (ph - 1.0) + sc.k * lap3(sc, phi0, x, y, z);",
+     ["test_init_is_equilibrium_of_eq16_mu_alpha_3d"]),
     ("source_sign_3d", "F[i] = -W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);  // Eq. 19",
      "F[i] = W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);", ["test_numpy_second_route_3d"]),
     ("rest_equilibrium_3d", "feq[0] = phi + (W3[0] - 1.0) * mua;",

@@ -123,6 +123,22 @@ def test_srt_reduction(s):
     assert np.abs(out - bgk).max() <= 1e-14
 
 
+def test_init_is_equilibrium_of_eq16_mu_alpha():
+    """Reading C5: the initial state is f^eq (Eq. 18) of phi0 and mu_alpha = f(phi0) - k lap phi0
+    (Eq. 16), the Laplacian that of Eq. 26b. Recomputed here with np.roll from the printed
+    Eq. 20 tables and the Eq. 39 parameters through Eq. 5."""
+    ny, nx = 9, 11
+    phi0 = np.random.default_rng(12).uniform(-0.9, 0.9, (ny, nx))
+    f = oracle.init(P(nx, ny, alpha=0.3), phi0)
+    beta = 3 * EQ39["sigma"] / (4 * EQ39["D"])
+    k = beta * EQ39["D"] ** 2 / 2
+    lap = 6 * sum(WT[i] * (np.roll(phi0, shift=(-C[i, 1], -C[i, 0]), axis=(0, 1)) - phi0) for i in range(9))
+    mua = 4 * beta * phi0 * (phi0 * phi0 - 1) - k * lap
+    want = WT[:, None, None] * mua[None]
+    want[0] = phi0 - (1 - WT[0]) * mua
+    assert np.abs(f - want).max() <= 1e-15
+
+
 # ---------------------------------------------------------------- P4 / P5: conservation and energy
 
 def test_mass_conserved_and_energy_decays_droplet():
