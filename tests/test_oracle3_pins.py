@@ -214,6 +214,29 @@ def test_init_is_equilibrium_of_eq16_mu_alpha_3d():
     assert np.abs(f - want).max() <= 1e-15
 
 
+@pytest.mark.parametrize("reg", [oracle.WILLMORE, oracle.LINEAR])
+def test_energy3_matches_numpy_route(reg):
+    """Reading C11 in 3D: E = sum_x [gamma(n) (k/2 |grad phi|^2 + F(phi)) + eps/2 G], F of Eq. 4,
+    G = (lap phi - f(phi))^2 (Eq. 9) or (lap phi)^2 (Eq. 8), the Eq. 26 stencils and the C3
+    guard, evaluated here by np.roll from the printed Eq. 21 tables."""
+    nx, ny, nz, alpha, eps = 7, 6, 5, 0.35, 0.03
+    phi = np.random.default_rng(14).uniform(-0.9, 0.9, (nz, ny, nx))
+    p = P3(nx, ny, nz, alpha=alpha, eps=eps, regularization=reg)
+    f = oracle.init3(p, phi)
+    beta = 3 * 0.01 / (4 * 5.0)
+    k = beta * 5.0 ** 2 / 2
+    at = lambda a, c: np.roll(a, shift=(-c[2], -c[1], -c[0]), axis=(0, 1, 2))
+    g = [3 * sum(W3[i] * C3[i, e] * at(phi, C3[i]) for i in range(15)) for e in range(3)]
+    lap = 6 * sum(W3[i] * (at(phi, C3[i]) - phi) for i in range(15))
+    g2 = sum(v * v for v in g)
+    ok = g2 >= 1e-12
+    s4 = sum(np.where(ok, v / np.sqrt(np.where(ok, g2, 1.0)), 0.0) ** 4 for v in g)
+    gamma = np.where(ok, 1 + alpha * (4 * s4 - 3), 1.0)
+    G = (lap - 4 * beta * phi * (phi * phi - 1)) ** 2 if reg == oracle.WILLMORE else lap ** 2
+    want = np.sum(gamma * (0.5 * k * g2 + beta * (phi * phi - 1) ** 2) + 0.5 * eps * G)
+    assert abs(oracle.energy3(p, f) - want) <= 1e-12 * abs(want)
+
+
 # ---------------------------------------------------------------- curved interface
 
 def _sphere_mu_beta_error(scale, literal, alpha=0.3):

@@ -130,6 +130,13 @@ MUTANTS3 = [
      "const double mua = 4.0 * sc.beta * ph * (ph + 1.0) * (ph - 1.0) - sc.k * lap3(sc, phi0, x, y, z);",
      "const double mua = 4.0 * sc.beta * ph * (ph + 1.0) * (ph - 1.0) + sc.k * lap3(sc, phi0, x, y, z);",
      ["test_init_is_equilibrium_of_eq16_mu_alpha_3d"]),
+    ("energy_without_gamma_3d",
+     "double e = a.gamma * (0.5 * sc.k * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) + F);  // Eq. 7",
+     "double e = (0.5 * sc.k * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) + F);", ["test_energy3_matches_numpy_route"]),
+    ("energy_willmore_factor_3d", "e += 0.5 * sc.eps * w * w;", "e += sc.eps * w * w;",
+     ["test_energy3_matches_numpy_route"]),
+    ("energy_linear_factor_3d", "e += 0.5 * sc.eps * lap * lap;  // Eq. 8", "e += sc.eps * lap * lap;",
+     ["test_energy3_matches_numpy_route"]),
     ("source_sign_3d", "F[i] = -W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);  // Eq. 19",
      "F[i] = W3[i] * (CX3[i] * gx + CY3[i] * gy + CZ3[i] * gz);", ["test_numpy_second_route_3d"]),
     ("rest_equilibrium_3d", "feq[0] = phi + (W3[0] - 1.0) * mua;",
