@@ -72,6 +72,11 @@ MUTANTS = [
     # The n = 0 guard (reading C3) at a threshold that reaches interface nodes.
     ("guard_too_high", "const double GUARD = 1e-12;", "const double GUARD = 1e-6;",
      ["test_guard_fires_only_in_the_bulk"]),
+    # The discrete energy (reading C11: Eq. 7 with Eq. 9).
+    ("energy_without_gamma", "double e = a.gamma * (0.5 * sc.k * (dx * dx + dy * dy) + bulkF(sc, phi[id]));",
+     "double e = (0.5 * sc.k * (dx * dx + dy * dy) + bulkF(sc, phi[id]));", ["test_energy_closed_form_cosines"]),
+    ("energy_willmore_factor", "        e += 0.5 * sc.eps * w * w;\n      } else if (sc.reg == 2) {",
+     "        e += sc.eps * w * w;\n      } else if (sc.reg == 2) {", ["test_energy_closed_form_cosines"]),
     # Parameters and collision (Eqs. 5, 17-19, the rate after Eq. 38).
     ("k_without_half", "d->k = d->beta * p->D * p->D / 2.0;", "d->k = d->beta * p->D * p->D;",
      ["test_parameters_eq5_inversion"]),
