@@ -65,13 +65,18 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-leap time-to-t measurement")
     ap.add_argument("--no-small-configs", action="store_true",
                     help="skip the 64^2 droplet and 256^2 spinodal legs and the oracle comparisons")
-    ap.add_argument("--config2-steps", type=int, default=20000, help="steps of the 256^2 spinodal run")
+    ap.add_argument("--config2-steps", type=int, default=20000,
+                    help="steps of the 256^2 spinodal run (a multiple of 100, at least 1000: the oracle "
+                         "comparison reads phi at step 1000)")
     ap.add_argument("--log-dir", default=os.environ.get("LBCH_LOG_DIR"),
                     help="write the 256^2 run's mass and energy every 100 steps as CSV into this folder "
                          "(default: $LBCH_LOG_DIR; none if unset)")
     ap.add_argument("--storage", choices=["f32", "bf16_dev", "f16_dev"], default="f32",
                     help="population storage of the main timed line")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.config2_steps < 1000 or args.config2_steps % 100:
+        ap.error("--config2-steps must be a multiple of 100 and at least 1000")
+    return args
 
 
 def dist_env():
